@@ -1,0 +1,206 @@
+"""FP64 CPU oracle of the reduced polyatomic ES-BGK lattice-Boltzmann step.
+
+TEST INFRASTRUCTURE. Only ``tests/``, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may import this package. The CUDA library in
+``paper_2201_05280_gb300`` never imports it and shares no code with it.
+
+The arithmetic lives in ``rpk_oracle.c`` (plain C, double precision, single
+thread, written in the order of the paper's Sec. 5); this module builds it with
+gcc, loads it with ctypes and marshals numpy arrays. ``params`` holds the
+host-side parameter mapping of Sec. 4 written out independently of the
+library's own.
+
+Functions whose result has no independent pin are marked "parity unpinned" in
+their docstring; at present there are none: every C entry point is pinned by a
+``-m "not gpu"`` test (see ``tests/test_oracle_*.py``).
+"""
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+from . import params  # noqa: F401  (re-exported)
+
+Q = 41
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "rpk_oracle.c")
+_BUILD_DIR = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD_DIR, "liboracle.so")
+
+
+def build(force=False):
+    """Compile the oracle with gcc (IEEE double, no FMA contraction, so that
+    x86-64 and aarch64 hosts give the same bits)."""
+    os.makedirs(_BUILD_DIR, exist_ok=True)
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+        return _LIB_PATH
+    tmp = _LIB_PATH + ".tmp%d" % os.getpid()
+    cmd = ["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-fno-fast-math",
+           "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
+    subprocess.check_call(cmd)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+class Params(ctypes.Structure):
+    """Mirror of ``ora_params`` in rpk_oracle.c."""
+    _fields_ = [("delta", ctypes.c_double), ("tau", ctypes.c_double),
+                ("tau1", ctypes.c_double), ("b", ctypes.c_double),
+                ("kr", ctypes.c_double), ("dt", ctypes.c_double),
+                ("nsub", ctypes.c_int), ("bcx", ctypes.c_int)]
+
+    def __repr__(self):
+        return ("Params(delta=%g, tau=%g, tau1=%g, b=%g, kr=%g, dt=%g, nsub=%d, bcx=%d)"
+                % (self.delta, self.tau, self.tau1, self.b, self.kr, self.dt,
+                   self.nsub, self.bcx))
+
+
+_lib = None
+_dp = ctypes.POINTER(ctypes.c_double)
+
+
+def _load():
+    global _lib
+    if _lib is not None:
+        return _lib
+    lib = ctypes.CDLL(build())
+    P = ctypes.POINTER(Params)
+    i, l, d = ctypes.c_int, ctypes.c_long, ctypes.c_double
+    sig = {
+        "ora_theta0": (d, []),
+        "ora_lattice": (None, [_dp, _dp]),
+        "ora_target": (None, [d, _dp, _dp, _dp]),
+        "ora_point_init": (None, [P, d, _dp, d, d, _dp, _dp]),
+        "ora_point_moments": (None, [P, _dp, d, _dp]),
+        "ora_point_collide": (None, [P, _dp, _dp]),
+        "ora_point_f": (None, [P, _dp, d, _dp]),
+        "ora_init": (i, [P, i, i, i, _dp, _dp, _dp, _dp, _dp, _dp]),
+        "ora_step": (i, [P, i, i, i, _dp, _dp, _dp, _dp, l]),
+        "ora_fields": (None, [P, i, i, i, _dp, _dp, _dp, _dp, _dp, _dp, _dp]),
+        "ora_diag": (None, [P, i, i, i, _dp, _dp, _dp]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _ptr(a):
+    assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(_dp)
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def theta0():
+    """Sec. 5, Table 1: lattice reference temperature."""
+    return _load().ora_theta0()
+
+
+THETA0 = 0.2948964908710633  # Sec. 5, Table 1 caption
+
+
+def lattice():
+    """(c, w): the 41 RD3Q41 velocities (41x3) and weights (Sec. 5, Table 1)."""
+    c = np.zeros((Q, 3))
+    w = np.zeros(Q)
+    _load().ora_lattice(_ptr(c), _ptr(w))
+    return c, w
+
+
+def target(rho, u, Lam):
+    """Discrete Gaussian f_i(rho, u, Lam), third-order Hermite expansion."""
+    f = np.zeros(Q)
+    _load().ora_target(float(rho), _ptr(_f64(u)), _ptr(_f64(np.asarray(Lam).reshape(9))), _ptr(f))
+    return f
+
+
+def make_params(delta, tau, tau1, b=0.0, kr=0.0, dt=1.0, nsub=1, bcx=0):
+    return Params(float(delta), float(tau), float(tau1), float(b), float(kr), float(dt),
+                  int(nsub), int(bcx))
+
+
+def point_init(P, rho, u, T, R):
+    g = np.zeros(Q)
+    Er = ctypes.c_double(0.0)
+    _load().ora_point_init(ctypes.byref(P), float(rho), _ptr(_f64(u)), float(T), float(R),
+                           _ptr(g), ctypes.cast(ctypes.byref(Er), _dp))
+    return g, Er.value
+
+
+def point_moments(P, g, Er):
+    """dict of rho, u, T, R, theta, thetaTg, sigma (3x3) of the f-level state."""
+    out = np.zeros(17)
+    _load().ora_point_moments(ctypes.byref(P), _ptr(_f64(g)), float(Er), _ptr(out))
+    return {"rho": out[0], "u": out[1:4].copy(), "T": out[4], "R": out[5],
+            "theta": out[6], "thetaTg": out[7], "sigma": out[8:17].reshape(3, 3).copy()}
+
+
+def point_collide(P, g, Er):
+    g = _f64(g).copy()
+    e = ctypes.c_double(float(Er))
+    _load().ora_point_collide(ctypes.byref(P), _ptr(g), ctypes.cast(ctypes.byref(e), _dp))
+    return g, e.value
+
+
+def point_f(P, g, Er):
+    f = np.zeros(Q)
+    _load().ora_point_f(ctypes.byref(P), _ptr(_f64(g)), float(Er), _ptr(f))
+    return f
+
+
+class State:
+    """Grid state of the oracle: g (npts x 41, point-major) and Er (npts)."""
+
+    def __init__(self, P, nx, ny, nz, reservoirs=None):
+        self.P = P
+        self.nx, self.ny, self.nz = int(nx), int(ny), int(nz)
+        self.npts = 2 * self.nx * self.ny * self.nz
+        self.g = np.zeros((self.npts, Q))
+        self.Er = np.zeros(self.npts)
+        self.uprev = np.zeros(3 * self.npts)  # u of the previous step (advection)
+        self.res = None if reservoirs is None else _f64(reservoirs).reshape(12).copy()
+        self.t = 0
+
+    def init_fields(self, rho, u, T, R):
+        n = self.npts
+        rho, T, R = _f64(rho).reshape(n), _f64(T).reshape(n), _f64(R).reshape(n)
+        u = _f64(u).reshape(3 * n)
+        _load().ora_init(ctypes.byref(self.P), self.nx, self.ny, self.nz, _ptr(rho), _ptr(u),
+                         _ptr(T), _ptr(R), _ptr(self.g), _ptr(self.Er))
+        self.uprev[:] = u  # the first step advects with u(0)
+        self.t = 0
+        return self
+
+    def step(self, n=1):
+        res = self.res if self.res is not None else np.zeros(12)
+        if self.P.bcx == 1 and self.res is None:
+            raise ValueError("bcx=1 needs reservoir states")
+        rc = _load().ora_step(ctypes.byref(self.P), self.nx, self.ny, self.nz, _ptr(res),
+                              _ptr(self.g), _ptr(self.Er), _ptr(self.uprev), int(n))
+        if rc != 0:
+            raise MemoryError("oracle step could not allocate its work arrays")
+        self.t += int(n)
+        return self
+
+    def fields(self):
+        """dict rho, u (3 x npts), T, R, Erot (each npts)."""
+        n = self.npts
+        rho, T, R, E = (np.zeros(n) for _ in range(4))
+        u = np.zeros(3 * n)
+        _load().ora_fields(ctypes.byref(self.P), self.nx, self.ny, self.nz, _ptr(self.g),
+                           _ptr(self.Er), _ptr(rho), _ptr(u), _ptr(T), _ptr(R), _ptr(E))
+        return {"rho": rho, "u": u.reshape(3, n), "T": T, "R": R, "Erot": E}
+
+    def diag(self):
+        """dict M, J (3), E, H1, min_g."""
+        out = np.zeros(7)
+        _load().ora_diag(ctypes.byref(self.P), self.nx, self.ny, self.nz, _ptr(self.g),
+                         _ptr(self.Er), _ptr(out))
+        return {"M": out[0], "J": out[1:4].copy(), "E": out[4], "H1": out[5], "min_g": out[6]}
