@@ -1,0 +1,334 @@
+"""Benchmark: MLUPS of the reduced polyatomic ES-BGK lattice-Boltzmann step on
+GB300, with the HBM roofline of the dominant kernel and the FP64 oracle timed
+on the host cores as a baseline.
+
+Workload: 3-D periodic decaying wave field on a 256^3 grid of each BCC
+sublattice (2 x 256^3 = 33,554,432 points), FP32, uniform rho = 1,
+theta = theta0 plus 8 seeded random Fourier modes (amplitude 1e-3 in rho, u,
+theta), diatomic gas (gamma = 7/5), nu = 0.02, eta_B/eta = 0.6, Pr = 0.71, b = 0.
+A step is one pass of the whole hot path: pull-stream + collide + rotational
+exchange, MacCormack advection and FTCS diffusion of E_R. The population
+arrays (2 x 11 GB) are far larger than L2, so no L2 flush is needed.
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl rpk|reference]
+Under torchrun (N > 1) every rank runs its own lattice (independent replicas,
+weak scaling, no collective in the data path); rank 0 prints one JSON line.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import rpk_inputs as I  # noqa: E402
+
+METRIC = "MLUPS & HBM GB/s vs peak; surrogate speedup vs plain LBM at <=1% L1 err"
+THETA0 = 0.2948964908710633
+GAS = dict(gamma=1.4, nu=0.02, lam=0.6, Pr=0.71, b=0.0)
+STORE_BYTES = {"f64": 8, "f32": 4, "f16dev": 2, "bf16dev": 2}
+FALLBACK_HBM_GBS = 6800.0
+
+
+def algorithmic_bytes_per_point(prec):
+    """Bytes one point must move per step (rows a1-a8 of the hot path):
+    41 populations read + 41 written, plus the moment/rotational fields
+    (read rho, u, theta, E_R: 24 B; write 24 B) in the field precision."""
+    sb = STORE_BYTES[prec]
+    fb = 8 if prec == "f64" else 4
+    return {"step": 41 * 2 * sb + 12 * fb,
+            # collide kernel alone: populations, e in, and e*, rho, u (3), kappa out
+            "collide": 41 * 2 * sb + 7 * fb}
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        for k in ("hbm_gbs", "hbm_copy_gbs", "hbm_GBs"):
+            if k in d:
+                return float(d[k]), "measured"
+    except (OSError, ValueError):
+        pass
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+def ncu_traffic(prec):
+    """DRAM bytes per point of the collide kernel from the committed ncu
+    summary, if the kernel source has not changed since it was captured."""
+    path = os.path.join(ROOT, "profiles", "ncu_collide_%s.txt" % prec)
+    src = os.path.join(ROOT, "paper_2201_05280_gb300", "csrc", "rpk_kernels.cuh")
+    try:
+        kv = {}
+        for line in open(path):
+            if ":" in line and not line.startswith("#"):
+                k, v = line.split(":", 1)
+                kv[k.strip()] = v.strip()
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+        if kv.get("kernel_source_sha256") != sha:
+            return None
+        return float(kv["dram_bytes_per_point"])
+    except (OSError, KeyError, ValueError):
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        self.out = ""
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out, _ = self.proc.communicate()
+
+    def summary(self):
+        rows = []
+        for line in (self.out or "").splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for name, v in zip(names, r[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(rows)}
+
+
+def make_fields(n, seed=I.SEED):
+    f, _ = I.fourier_modes(n, n, n, THETA0, nmodes=8, amp=1e-3, seed=seed)
+    return f
+
+
+def relax_params(rpk):
+    eta, etaB, kap = rpk.gas_from_nondim(GAS["gamma"], GAS["nu"], GAS["lam"], GAS["Pr"])
+    return rpk.map_gas(GAS["gamma"], eta, etaB, kap, GAS["b"])
+
+
+def oracle_mlups(n, steps, warmup=1):
+    """The FP64 oracle, as it stands, on an n^3 box of the same workload."""
+    import oracle as O
+    from oracle import params as PM
+    eta, etaB, kap = PM.gas_from_nondim(GAS["gamma"], GAS["nu"], GAS["lam"], GAS["Pr"])
+    d, tau, tau1, b, kr = PM.relax_from_gas(GAS["gamma"], eta, etaB, kap, GAS["b"])
+    f = make_fields(n)
+    thmax = float(np.max((3 * f["T"] + d * f["R"]) / (3 + d)))
+    P = O.make_params(d, tau, tau1, b, kr, 1.0, PM.nsub_for(d, tau, tau1, kr, thmax, 3), 0)
+    S = O.State(P, n, n, n).init_fields(f["rho"], f["u"], f["T"], f["R"])
+    if warmup:
+        S.step(warmup)
+    t = time.perf_counter()
+    S.step(steps)
+    dt = time.perf_counter() - t
+    return S.npts * steps / dt / 1e6, dt
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return 0
+    n = args.ref_n
+    value, dt = oracle_mlups(n, args.steps, args.warmup)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "MLUPS",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "3-D periodic decaying wave field (8 seeded Fourier modes), "
+                                   "oracle on a %d^3 sample of the 256^3 workload" % n,
+                       "grid": [n, n, n], "points": 2 * n ** 3, "gas": GAS},
+            "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+                             "sample": "%d^3 box (%d points) x %d steps" % (n, 2 * n ** 3, args.steps)},
+            "e2e": {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="rpk", choices=["rpk", "reference"])
+    ap.add_argument("--n", type=int, default=256, help="cells per axis of each sublattice")
+    ap.add_argument("--precision", default="f32", choices=list(STORE_BYTES))
+    ap.add_argument("--ref-n", type=int, default=16, help="oracle sample box for --impl reference")
+    ap.add_argument("--cpu-n", type=int, default=24, help="oracle sample box for cpu_baseline")
+    ap.add_argument("--cpu-steps", type=int, default=100)
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank)
+
+    import torch
+    import paper_2201_05280_gb300 as rpk
+    from paper_2201_05280_gb300 import build as B
+    if rank == 0 or world == 1:
+        B.build()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+        dist.barrier()
+        B.build()
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.cuda.current_device()
+
+    n = args.n
+    f = make_fields(n)
+    r = relax_params(rpk)
+    stream = torch.cuda.Stream()
+    lat = rpk.Lattice(n, n, n, precision=args.precision, stream=stream)
+    lat.set_relax(r["delta"], r["tau"], r["tau1"], r["b"], r["k_r"])
+    lat.init_fields(f["rho"], f["u"], f["T"], f["R"])
+    nsub = lat.info()["nsub"]
+    npts = lat.npts
+
+    lat.step(args.warmup)
+    torch.cuda.synchronize()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(dev) as clk:
+        lat.timing(True)
+        e0.record(stream)
+        lat.step(args.steps)
+        e1.record(stream)
+        barrier()
+    ktimes = lat.timing_read()
+    lat.timing(False)
+    ms = e0.elapsed_time(e1)
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    diag = lat.diagnostics()
+    value = world * npts * args.steps / (ms * 1e-3) / 1e6
+
+    # end to end through the public API with pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        pin = {k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory() for k, v in f.items()}
+        outs = {k: torch.empty(sz, dtype=torch.float64).pin_memory()
+                for k, sz in (("rho", npts), ("u", 3 * npts), ("T", npts), ("R", npts),
+                              ("Erot", npts))}
+        lat2 = rpk.Lattice(n, n, n, precision=args.precision, stream=stream)
+        lat2.set_relax(r["delta"], r["tau"], r["tau1"], r["b"], r["k_r"])
+        lat2.init_fields(pin["rho"], pin["u"], pin["T"], pin["R"])  # warm the staging path
+        lat2.step(3)
+        lat2.read_moments(outs)
+        barrier()
+        t0 = time.perf_counter()
+        lat2.init_fields(pin["rho"], pin["u"], pin["T"], pin["R"])
+        lat2.step(args.steps)
+        lat2.read_moments(outs)
+        barrier()
+        wall = time.perf_counter() - t0
+        if dist is not None:
+            t = torch.tensor([wall], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            wall = float(t.item())
+        lat2.close()
+        h2d = 6 * npts * 8
+        d2h = 7 * npts * 8
+        e2e = {"value": world * npts * args.steps / wall / 1e6, "unit": "MLUPS",
+               "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
+               "note": "per job of K steps: fields uploaded once from pinned host memory, "
+                       "moments read back once; bytes per step = job bytes / K"}
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return 0
+
+    ab = algorithmic_bytes_per_point(args.precision)
+    peak, peak_src = load_peaks()
+    coll_ms, coll_n = ktimes["collide"]
+    coll_avg_s = coll_ms / max(coll_n, 1) * 1e-3
+    achieved = ab["collide"] * npts / coll_avg_s / 1e9
+    traffic_pp = ncu_traffic(args.precision)
+    roofline = {"bound": "hbm", "kernel": "k_collide (pull-stream + collide + exchange)",
+                "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "peak_source": peak_src,
+                "algorithmic_bytes_per_point": ab["collide"],
+                "traffic": None if traffic_pp is None else traffic_pp * npts,
+                "kernel_ms": {k: v[0] / max(v[1], 1) for k, v in ktimes.items()},
+                "kernel_share": {k: v[0] / sum(x[0] for x in ktimes.values())
+                                 for k, v in ktimes.items()},
+                "step_gbs_at_376B": ab["step"] * npts * args.steps / (ms * 1e-3) / 1e9}
+    cpu_mlups, cpu_dt = oracle_mlups(args.cpu_n, args.cpu_steps, warmup=1)
+    launches = sum(v[1] for v in ktimes.values())
+    line = {"metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if args.precision == "f32" else args.precision, "data": "synthetic",
+            "config": {"workload": "3-D periodic %d^3 decaying wave field, %s" % (n, args.precision),
+                       "grid": [n, n, n], "points": npts, "gas": GAS, "nsub": nsub,
+                       "l2": "inputs larger than L2 (%.1f GB of populations)" %
+                             (2 * 41 * npts * STORE_BYTES[args.precision] / 1e9),
+                       "parallelism": "replicas x%d" % world},
+            "roofline": roofline,
+            "cpu_baseline": {"value": cpu_mlups, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+                             "sample": "%d^3 box (%d points) x %d steps, %.1f s" %
+                                       (args.cpu_n, 2 * args.cpu_n ** 3, args.cpu_steps, cpu_dt)},
+            "e2e": e2e, "gpu_launches": launches,
+            "clocks": clk.summary(),
+            "device_status": diag["status"]}
+    print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

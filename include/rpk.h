@@ -1,0 +1,193 @@
+/*
+ * rpk.h -- C interface of librpk, a single-GPU (sm_103a) implementation of the
+ * lattice-Boltzmann time step of the reduced polyatomic ES-BGK model of
+ * Kolluru, Atif & Ansumali, "Reduced kinetic model of polyatomic gases"
+ * (arXiv 2201.05280).
+ *
+ * What one step computes (Sec. 4, eq. kinEqBGK; Sec. 5):
+ *   - every point of the body-centred-cubic grid pulls its 41 RD3Q41
+ *     populations (Sec. 5, Table 1) from its neighbours,
+ *   - forms rho, rho u and the pressure tensor, recovers theta_T, theta_R and
+ *     sigma of the physical distribution from the auxiliary population
+ *     g = f - (dt/2) Omega (Sec. 5, g/f moment relations),
+ *   - relaxes toward tau*(f^ES/tau + f^Eq/tau1) with the explicit trapezoid
+ *     update g' = (1 - 2 beta*) g + 2 beta* tau*(f^ES/tau + f^Eq/tau1),
+ *   - moves the matching energy into the rotational energy density E_R, and
+ *   - advects (MacCormack) and diffuses (FTCS) E_R (Sec. 5, steps 2 and 3).
+ *
+ * Conventions for every call:
+ *   - Units are lattice units: sublattice spacing 1, dt = 1, reference
+ *     temperature theta0 = rpk_theta0() (Sec. 5, Table 1).
+ *   - A scalar field is 2*nx*ny*nz doubles indexed
+ *         p = ((s*nz + z)*ny + y)*nx + x,
+ *     s = 0 for the corner sublattice, s = 1 for the body-centre sublattice at
+ *     (x, y, z) + (1/2, 1/2, 1/2). A vector field (u) is three such planes, x
+ *     component first.
+ *   - Every call is made from the host. Kernels run on the CUDA stream given
+ *     to rpk_create (NULL = the legacy default stream) on the device that was
+ *     current at rpk_create; calls restore nothing else.
+ *   - Ownership: the library allocates and owns all device state of a lattice
+ *     and frees it in rpk_destroy. Caller arrays are only read or written
+ *     during the call that receives them; device pointers passed with
+ *     on_device = 1 must be device memory of the lattice's device.
+ *   - Errors: every call returns an rpk_status; nothing throws across the
+ *     interface. rpk_last_error() returns a message for the most recent failed
+ *     call of the calling thread. A failed call leaves the lattice usable
+ *     unless it reports RPK_ERR_CUDA (the CUDA context may then be broken).
+ */
+#ifndef RPK_H
+#define RPK_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define RPK_ABI_VERSION 1
+
+typedef enum {
+  RPK_OK = 0,
+  RPK_ERR_ARG = 1,     /* null pointer, bad size or bad enum */
+  RPK_ERR_PARAM = 2,   /* physically invalid parameter (see rpk_set_relax) */
+  RPK_ERR_CUDA = 3,    /* a CUDA call failed */
+  RPK_ERR_NUMERIC = 4, /* the device flagged a non-finite or non-positive moment */
+  RPK_ERR_STATE = 5,   /* call out of order (e.g. step before init) */
+  RPK_ERR_OOM = 6,     /* device or host allocation failed */
+  RPK_ERR_IO = 7       /* checkpoint file error */
+} rpk_status;
+
+/* Storage precision of the populations. Arithmetic is FP64 for RPK_F64 and
+ * FP32 otherwise. RPK_F32/F16DEV/BF16DEV store h_i = g_i/w_i - 1. */
+enum { RPK_F64 = 0, RPK_F32 = 1, RPK_F16DEV = 2, RPK_BF16DEV = 3 };
+
+/* Boundary in x: periodic, or fixed equilibrium reservoirs beyond both ends
+ * (rpk_set_reservoirs). y and z are always periodic. */
+enum { RPK_BC_PERIODIC = 0, RPK_BC_RESERVOIR = 1 };
+
+typedef struct {
+  int nx, ny, nz; /* cells per sublattice along each axis, each >= 1 */
+  int precision;  /* RPK_F64 ... RPK_BF16DEV */
+  int bc_x;       /* RPK_BC_PERIODIC or RPK_BC_RESERVOIR */
+} rpk_grid;
+
+/* Raw relaxation parameters, as in Sec. 4 eq. kinEqBGK and Sec. 5. */
+typedef struct {
+  double delta; /* rotational degrees of freedom, > 0 (Sec. 3, eq. thetadef) */
+  double tau;   /* ES-BGK relaxation time, > 0 */
+  double tau1;  /* relaxation time of the BGK term and of E_R, > 0 */
+  double b;     /* ES-BGK parameter (Sec. 2, eq. lambdaij), B - b > 0 */
+  double k_r;   /* kappa_R / kappa_T >= 0 (Sec. 4, conductivity paragraph) */
+  double dt;    /* time step; must be 1 (lattice units) */
+  int nsub;     /* FTCS sub-steps of the E_R diffusion per step; 0 = choose at
+                   rpk_init_fields from the initial fields (rpk_auto_nsub) */
+} rpk_relax;
+
+typedef struct {
+  double mass;      /* sum over points of rho */
+  double mom[3];    /* sum of rho u */
+  double energy;    /* sum of (sum_i g_i c_i^2 / 2 + auxiliary E_R), which
+                       equals the physical E_T + E_R (Sec. 4, ConservedMomEq) */
+  double H1;        /* sum of sum_i (f_i ln(f_i/w_i) - f_i) - (delta/2) rho ln theta_R
+                       (Sec. 4, H-theorem paragraph, k = -delta/2); NaN if
+                       some f_i <= 0 */
+  double min_g;     /* smallest auxiliary population g_i */
+  uint32_t status;  /* device flags since creation: 1 non-finite moment,
+                       2 rho <= 0, 4 theta_T <= 0 or theta_R <= 0 */
+  uint32_t pad;
+  int64_t steps;    /* steps taken since the last rpk_init_fields/rpk_load */
+} rpk_diag;
+
+typedef struct rpk_lattice rpk_lattice;
+
+/* Library facts. */
+int rpk_abi_version(void);
+double rpk_theta0(void); /* Sec. 5, Table 1 */
+const char* rpk_last_error(void);
+
+/* Parameter mapping of Sec. 4 (eq. viscosities and the conductivity
+ * paragraph) at the reference state p0 = rho0 * theta0; host only, needs no
+ * GPU. gamma -> delta = (5 - 3 gamma)/(gamma - 1); eta_b = c p0 tau1 with
+ * c = 2 delta/(3(3 + delta)); eta = p0 tau/(B - b), B = 1 + tau/tau1;
+ * kappa = 5 p0 tau (1 + k_r)/(2B). Writes out->{delta,tau,tau1,b,k_r},
+ * out->dt = 1, out->nsub = 0. RPK_ERR_PARAM when no tau > 0, tau1 > 0,
+ * k_r >= 0 realises the request (eta_B/eta < c needs b > 1). */
+rpk_status rpk_map_gas(double gamma, double eta, double eta_B, double kappa, double b,
+                       double rho0, rpk_relax* out);
+
+/* FTCS sub-steps for the E_R diffusion, host only: the diffusivity of
+ * theta_R = 2 E_R/(delta rho) is D = 5 k_r tau theta/(delta B); explicit
+ * stability in ndim dimensions needs 2 ndim D dt/nsub <= 1, kept at 0.9 with
+ * theta = 1.25 theta_max. Returns >= 1. */
+int rpk_auto_nsub(const rpk_relax* r, double theta_max, int ndim);
+
+/* Create a lattice on the current device. cuda_stream is a cudaStream_t (or
+ * NULL). Allocates 2 x 41 populations per point (ping-pong) plus ~12 scalar
+ * planes. */
+rpk_status rpk_create(const rpk_grid* grid, void* cuda_stream, rpk_lattice** out);
+void rpk_destroy(rpk_lattice* lat); /* NULL is allowed */
+
+/* Set the relaxation parameters (validated: delta > 0, tau > 0, tau1 > 0,
+ * B - b > 0, k_r >= 0, dt == 1, 0 <= nsub <= 4096). Takes effect at the next
+ * rpk_step; nsub = 0 is resolved at the next rpk_init_fields. */
+rpk_status rpk_set_relax(rpk_lattice* lat, const rpk_relax* r);
+/* rpk_map_gas with rho0 = 1, then rpk_set_relax. */
+rpk_status rpk_set_gas(rpk_lattice* lat, double gamma, double eta, double eta_B, double kappa,
+                       double b);
+
+/* RPK_BC_RESERVOIR only: the equilibrium states beyond the low-x and the
+ * high-x end, 12 doubles: rho, ux, uy, uz, theta_T, theta_R of the low end,
+ * then of the high end. Must be called after rpk_set_relax and before
+ * rpk_init_fields. */
+rpk_status rpk_set_reservoirs(rpk_lattice* lat, const double* states12);
+
+/* Initial state from hydrodynamic fields (layout above): rho > 0, u (3
+ * planes), theta_T > 0, theta_R > 0. f = f^Eq(rho, u, theta_T I), then
+ * g = f - (dt/2) Omega(f) and the auxiliary E_R (Sec. 5). Host arrays when
+ * on_device = 0, device arrays of this device when 1. Resets the step count.
+ * Synchronises the stream. */
+rpk_status rpk_init_fields(rpk_lattice* lat, const double* rho, const double* u,
+                           const double* theta_T, const double* theta_R, int on_device);
+
+/* Advance n >= 0 steps. Asynchronous: only enqueues kernels on the stream. */
+rpk_status rpk_step(rpk_lattice* lat, int64_t n);
+
+/* Hydrodynamic fields of the current state: rho, u (3 planes), theta_T and
+ * theta_R of the physical distribution, and E_R = delta rho theta_R / 2. Any
+ * output pointer may be NULL to skip it. Host arrays when on_device = 0,
+ * device arrays when 1. Synchronises the stream; returns RPK_ERR_NUMERIC if
+ * the device status flags are set (the arrays are still written). */
+rpk_status rpk_read_moments(rpk_lattice* lat, double* rho, double* u, double* theta_T,
+                            double* theta_R, double* E_rot, int on_device);
+
+/* FP64 global diagnostics of the current state (rpk_diag). Synchronises the
+ * stream; returns RPK_ERR_NUMERIC if status != 0 (out is still filled). */
+rpk_status rpk_diagnostics(rpk_lattice* lat, rpk_diag* out);
+
+/* Checkpoint: raw state (populations, auxiliary E_R, the last two velocity
+ * fields, step count, parameters) with a header. rpk_load requires a lattice
+ * created with the same grid. Bitwise restart. Synchronise the stream. */
+rpk_status rpk_save(rpk_lattice* lat, const char* path);
+rpk_status rpk_load(rpk_lattice* lat, const char* path);
+
+/* Facts about a lattice: out[0] nsub in use, out[1] steps, out[2] number of
+ * points, out[3] bytes of device memory held. */
+rpk_status rpk_get_info(rpk_lattice* lat, int64_t out[4]);
+
+/* Kernel timing (a tracing aid; the paper has no counterpart). While enabled,
+ * rpk_step brackets each kernel class with CUDA events recorded on the
+ * lattice's stream: RPK_KC_COLLIDE (pull-stream + collide + exchange),
+ * RPK_KC_ADVECT (MacCormack predictor and corrector) and RPK_KC_DIFFUSE (all
+ * FTCS sub-steps). rpk_timing(lat, 1) clears the counters and starts;
+ * rpk_timing(lat, 0) stops. rpk_timing_read synchronises the stream and
+ * returns the summed milliseconds and the number of kernel launches per class
+ * since the last start (arrays of RPK_KC_COUNT entries). */
+enum { RPK_KC_COLLIDE = 0, RPK_KC_ADVECT = 1, RPK_KC_DIFFUSE = 2, RPK_KC_COUNT = 3 };
+rpk_status rpk_timing(rpk_lattice* lat, int enable);
+rpk_status rpk_timing_read(rpk_lattice* lat, double* ms, int64_t* launches);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RPK_H */

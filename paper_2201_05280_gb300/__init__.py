@@ -1,0 +1,274 @@
+"""Python binding of librpk: the GB300 (sm_103a) lattice-Boltzmann step of the
+reduced polyatomic ES-BGK model (Kolluru, Atif & Ansumali, arXiv 2201.05280).
+
+This module only marshals arguments to the C interface declared in
+``include/rpk.h``; every step of the computation runs in the CUDA kernels of
+``librpk.so``. There is no CPU fallback: if the library is missing or cannot
+be loaded, ``load_library`` raises.
+
+Arrays: host numpy float64 arrays, or CUDA float64 torch tensors (then the
+device path of the C interface is used and nothing crosses PCIe/C2C). A scalar
+field has 2*nx*ny*nz entries indexed p = ((s*nz + z)*ny + y)*nx + x; u has
+shape (3, npts).
+"""
+import ctypes
+import os
+
+import numpy as np
+
+__all__ = ["Lattice", "RpkError", "load_library", "theta0", "map_gas", "auto_nsub",
+           "gas_from_nondim", "PRECISIONS", "library_path"]
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "librpk.so")
+
+PRECISIONS = {"f64": 0, "f32": 1, "f16dev": 2, "bf16dev": 3}
+_BC = {"periodic": 0, "reservoir": 1}
+_STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_PARAM", 3: "ERR_CUDA", 4: "ERR_NUMERIC",
+           5: "ERR_STATE", 6: "ERR_OOM", 7: "ERR_IO"}
+
+
+class RpkError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s: %s" % (_STATUS.get(code, code), msg))
+        self.code = code
+
+
+class Grid(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("precision", ctypes.c_int), ("bc_x", ctypes.c_int)]
+
+
+class Relax(ctypes.Structure):
+    _fields_ = [("delta", ctypes.c_double), ("tau", ctypes.c_double),
+                ("tau1", ctypes.c_double), ("b", ctypes.c_double), ("k_r", ctypes.c_double),
+                ("dt", ctypes.c_double), ("nsub", ctypes.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class Diag(ctypes.Structure):
+    _fields_ = [("mass", ctypes.c_double), ("mom", ctypes.c_double * 3),
+                ("energy", ctypes.c_double), ("H1", ctypes.c_double),
+                ("min_g", ctypes.c_double), ("status", ctypes.c_uint32),
+                ("pad", ctypes.c_uint32), ("steps", ctypes.c_int64)]
+
+
+_lib = None
+_dp = ctypes.POINTER(ctypes.c_double)
+
+
+def library_path():
+    return _LIB_PATH
+
+
+def load_library(path=None):
+    """Load librpk.so (built by ``build.build()``); raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or _LIB_PATH
+    if not os.path.exists(path):
+        raise ImportError("librpk.so not found at %s: build it with "
+                          "`python -c 'import __graft_entry__ as g; g.build()'`" % path)
+    lib = ctypes.CDLL(path)
+    vp, i, d, i64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_int64
+    sig = {
+        "rpk_abi_version": (i, []),
+        "rpk_theta0": (d, []),
+        "rpk_last_error": (ctypes.c_char_p, []),
+        "rpk_map_gas": (i, [d, d, d, d, d, d, ctypes.POINTER(Relax)]),
+        "rpk_auto_nsub": (i, [ctypes.POINTER(Relax), d, i]),
+        "rpk_create": (i, [ctypes.POINTER(Grid), vp, ctypes.POINTER(vp)]),
+        "rpk_destroy": (None, [vp]),
+        "rpk_set_relax": (i, [vp, ctypes.POINTER(Relax)]),
+        "rpk_set_gas": (i, [vp, d, d, d, d, d]),
+        "rpk_set_reservoirs": (i, [vp, _dp]),
+        "rpk_init_fields": (i, [vp, vp, vp, vp, vp, i]),
+        "rpk_step": (i, [vp, i64]),
+        "rpk_read_moments": (i, [vp, vp, vp, vp, vp, vp, i]),
+        "rpk_diagnostics": (i, [vp, ctypes.POINTER(Diag)]),
+        "rpk_save": (i, [vp, ctypes.c_char_p]),
+        "rpk_load": (i, [vp, ctypes.c_char_p]),
+        "rpk_get_info": (i, [vp, ctypes.POINTER(i64)]),
+        "rpk_timing": (i, [vp, i]),
+        "rpk_timing_read": (i, [vp, ctypes.POINTER(d), ctypes.POINTER(i64)]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    if lib.rpk_abi_version() != 1:
+        raise ImportError("librpk ABI version mismatch")
+    _lib = lib
+    return lib
+
+
+def _check(code):
+    if code != 0:
+        raise RpkError(code, load_library().rpk_last_error().decode())
+
+
+def theta0():
+    """Lattice reference temperature (Sec. 5, Table 1)."""
+    return load_library().rpk_theta0()
+
+
+def map_gas(gamma, eta, eta_B, kappa, b=0.0, rho0=1.0):
+    """(gamma, eta, eta_B, kappa, b) -> raw relaxation parameters (rpk_map_gas)."""
+    r = Relax()
+    _check(load_library().rpk_map_gas(gamma, eta, eta_B, kappa, b, rho0, ctypes.byref(r)))
+    return r.as_dict()
+
+
+def auto_nsub(relax, theta_max, ndim):
+    r = Relax(**{k: relax.get(k, 0) for k, _ in Relax._fields_})
+    return load_library().rpk_auto_nsub(ctypes.byref(r), float(theta_max), int(ndim))
+
+
+def gas_from_nondim(gamma, nu, lam, Pr, rho0=1.0):
+    """(eta, eta_B, kappa) from kinematic viscosity nu, eta_B/eta = lam and
+    Pr = eta c_p/kappa with c_p = (5 + delta)/2 (Sec. 4)."""
+    delta = (5.0 - 3.0 * gamma) / (gamma - 1.0)
+    eta = rho0 * nu
+    return eta, lam * eta, eta * (5.0 + delta) / 2.0 / Pr
+
+
+def _is_torch(a):
+    return type(a).__module__.startswith("torch")
+
+
+def _arg(a, n):
+    """(pointer, on_device, keepalive) for a float64 array of n values."""
+    if _is_torch(a):
+        import torch
+        if a.dtype != torch.float64 or not a.is_contiguous() or a.numel() != n:
+            raise ValueError("expected a contiguous float64 tensor of %d values" % n)
+        return ctypes.c_void_p(a.data_ptr()), 1 if a.is_cuda else 0, a
+    arr = np.ascontiguousarray(a, dtype=np.float64)
+    if arr.size != n:
+        raise ValueError("expected %d values, got %d" % (n, arr.size))
+    return arr.ctypes.data_as(ctypes.c_void_p), 0, arr
+
+
+def _stream_handle(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)  # torch.cuda.Stream
+
+
+class Lattice:
+    """One lattice on the current CUDA device, driven through librpk."""
+
+    def __init__(self, nx, ny, nz, precision="f32", bc_x="periodic", stream=None):
+        lib = load_library()
+        self.nx, self.ny, self.nz = int(nx), int(ny), int(nz)
+        self.npts = 2 * self.nx * self.ny * self.nz
+        self.precision = precision
+        g = Grid(self.nx, self.ny, self.nz, PRECISIONS[precision], _BC[bc_x])
+        h = ctypes.c_void_p()
+        _check(lib.rpk_create(ctypes.byref(g), _stream_handle(stream), ctypes.byref(h)))
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            load_library().rpk_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def set_relax(self, delta, tau, tau1, b=0.0, k_r=0.0, nsub=0, dt=1.0):
+        r = Relax(delta, tau, tau1, b, k_r, dt, int(nsub))
+        _check(load_library().rpk_set_relax(self._h, ctypes.byref(r)))
+        return self
+
+    def set_gas(self, gamma, eta, eta_B, kappa, b=0.0):
+        _check(load_library().rpk_set_gas(self._h, gamma, eta, eta_B, kappa, b))
+        return self
+
+    def set_reservoirs(self, states12):
+        s = np.ascontiguousarray(states12, dtype=np.float64).reshape(12)
+        _check(load_library().rpk_set_reservoirs(self._h, s.ctypes.data_as(_dp)))
+        return self
+
+    def init_fields(self, rho, u, T, R):
+        n = self.npts
+        args = [_arg(rho, n), _arg(u, 3 * n), _arg(T, n), _arg(R, n)]
+        dev = {a[1] for a in args}
+        if len(dev) != 1:
+            raise ValueError("all fields must be on the host or all on the device")
+        _check(load_library().rpk_init_fields(self._h, *[a[0] for a in args], dev.pop()))
+        return self
+
+    def step(self, n=1):
+        _check(load_library().rpk_step(self._h, int(n)))
+        return self
+
+    def read_moments(self, out=None, check=True):
+        """dict rho, u (3, npts), T, R, Erot. ``out`` may hold preallocated
+        numpy arrays or CUDA float64 tensors with those keys."""
+        n = self.npts
+        if out is None:
+            out = {"rho": np.empty(n), "u": np.empty((3, n)), "T": np.empty(n),
+                   "R": np.empty(n), "Erot": np.empty(n)}
+        sizes = {"rho": n, "u": 3 * n, "T": n, "R": n, "Erot": n}
+        args = {k: _arg(out[k], sizes[k]) if k in out else (None, None, None) for k in sizes}
+        dev = {a[1] for a in args.values() if a[1] is not None}
+        if len(dev) != 1:
+            raise ValueError("outputs must be all host or all device")
+        code = load_library().rpk_read_moments(self._h, args["rho"][0], args["u"][0],
+                                               args["T"][0], args["R"][0], args["Erot"][0],
+                                               dev.pop())
+        if check:
+            _check(code)
+        res = {}
+        for k in sizes:
+            if k in out:
+                a = args[k][2]
+                res[k] = a.reshape(3, n) if k == "u" else a
+        return res
+
+    def diagnostics(self, check=True):
+        d = Diag()
+        code = load_library().rpk_diagnostics(self._h, ctypes.byref(d))
+        if check:
+            _check(code)
+        return {"M": d.mass, "J": np.array(d.mom[:]), "E": d.energy, "H1": d.H1,
+                "min_g": d.min_g, "status": d.status, "steps": d.steps}
+
+    def save(self, path):
+        _check(load_library().rpk_save(self._h, os.fsencode(path)))
+
+    def load(self, path):
+        _check(load_library().rpk_load(self._h, os.fsencode(path)))
+        return self
+
+    def timing(self, enable=True):
+        """Start (clearing the counters) or stop per-kernel-class CUDA-event timing."""
+        _check(load_library().rpk_timing(self._h, 1 if enable else 0))
+        return self
+
+    def timing_read(self):
+        """{class: (ms, launches)} for 'collide', 'advect', 'diffuse' since the last start."""
+        ms = (ctypes.c_double * 3)()
+        n = (ctypes.c_int64 * 3)()
+        _check(load_library().rpk_timing_read(self._h, ms, n))
+        return {name: (ms[i], n[i]) for i, name in enumerate(("collide", "advect", "diffuse"))}
+
+    def info(self):
+        out = (ctypes.c_int64 * 4)()
+        _check(load_library().rpk_get_info(self._h, out))
+        return {"nsub": out[0], "steps": out[1], "npts": out[2], "bytes": out[3]}

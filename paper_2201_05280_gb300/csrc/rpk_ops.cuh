@@ -1,0 +1,183 @@
+// Kernel launch sequences of one precision (included by rpk_ops_<prec>.cu,
+// which instantiate Ops<Store, Real> for their storage type).
+#pragma once
+
+#include <algorithm>
+#include <cmath>
+
+#include "rpk_internal.h"
+#include "rpk_kernels.cuh"
+
+namespace rpk {
+
+template <typename Real>
+static StepConst<Real> make_const(const rpk_lattice* L) {
+  const rpk_relax& r = L->relax;
+  const double tau_s = 1.0 / (1.0 / r.tau + 1.0 / r.tau1);
+  const double beta = r.dt / (2.0 * tau_s + r.dt);
+  const double B = 1.0 + r.tau / r.tau1;
+  StepConst<Real> K;
+  K.nx = L->grid.nx;
+  K.ny = L->grid.ny;
+  K.nz = L->grid.nz;
+  K.n3 = L->n3;
+  K.theta0 = Real(kTheta0);
+  K.c_keep = Real(1.0 - 2.0 * beta);
+  K.c_relax = Real(2.0 * beta);
+  K.beta = Real(beta);
+  K.w_es = Real(tau_s / r.tau);
+  K.w_eq = Real(tau_s / r.tau1);
+  K.b = Real(r.b);
+  K.inv_sig = Real(1.0 / (1.0 + r.dt / (2.0 * tau_s) - r.b * r.dt / (2.0 * r.tau)));
+  K.inv_d = Real(1.0 / (1.0 + r.dt / (2.0 * r.tau1)));
+  K.delta = Real(r.delta);
+  K.inv_3pd = Real(1.0 / (3.0 + r.delta));
+  K.exc = Real(r.dt * r.delta / (2.0 * r.tau1));
+  K.kapc = Real(r.k_r * 5.0 * r.tau / (2.0 * B));
+  K.E0 = Real(0.5 * r.delta * kTheta0);
+  K.dt = Real(r.dt);
+  K.hsub = Real(r.dt / std::max(1, L->nsub));
+  return K;
+}
+
+static inline dim3 point_grid(const rpk_lattice* L, int bx) {
+  return dim3((unsigned)((L->grid.nx + bx - 1) / bx), (unsigned)L->grid.ny,
+              (unsigned)(2 * L->grid.nz));
+}
+
+static inline rpk_status check_launch(const char* what) {
+  cudaError_t err = cudaGetLastError();
+  if (err != cudaSuccess) return cuda_fail(err, what);
+  return RPK_OK;
+}
+
+template <typename Store, typename Real, bool kPull, int kBC>
+static rpk_status collide_launch(rpk_lattice* L, const StepConst<Real>& K) {
+  const Store* pin = static_cast<const Store*>(L->pop[L->cur]);
+  Store* pout = static_cast<Store*>(L->pop[L->cur ^ 1]);
+  Real* ucur = static_cast<Real*>(L->u[L->steps & 1]);
+  k_collide<Store, Real, kPull, kBC><<<point_grid(L, 128), 128, 0, L->stream>>>(
+      K, pin, pout, static_cast<const Real*>(L->e), static_cast<Real*>(L->e_star),
+      static_cast<Real*>(L->drho), ucur, static_cast<Real*>(L->kap),
+      static_cast<const Real*>(L->ghost), L->status);
+  return check_launch("k_collide");
+}
+
+template <typename Real, int kBC>
+static rpk_status transport_launch(rpk_lattice* L, const StepConst<Real>& K) {
+  const dim3 grid = point_grid(L, 128);
+  const Real* ucur = static_cast<const Real*>(L->u[L->steps & 1]);
+  const Real* uprev = static_cast<const Real*>(L->u[(L->steps + 1) & 1]);
+  const Real* gh = static_cast<const Real*>(L->ghost);
+  Real* es = static_cast<Real*>(L->e_star);
+  Real* ea = static_cast<Real*>(L->e_a);
+  Real* eb = static_cast<Real*>(L->e_b);
+  RPK_CUDA(timing_begin(L));
+  k_mac_pred<Real, kBC><<<grid, 128, 0, L->stream>>>(K, es, ucur, uprev, ea, gh);
+  k_mac_corr<Real, kBC><<<grid, 128, 0, L->stream>>>(K, es, ea, ucur, uprev, eb, gh);
+  RPK_CUDA(timing_end(L, RPK_KC_ADVECT, 2));
+  // FTCS sub-steps: eb -> ... -> e (state)
+  RPK_CUDA(timing_begin(L));
+  Real* src = eb;
+  for (int k = 0; k < L->nsub; ++k) {
+    Real* dst = (k == L->nsub - 1) ? static_cast<Real*>(L->e) : (src == eb ? ea : eb);
+    k_ftcs<Real, kBC><<<grid, 128, 0, L->stream>>>(K, src, static_cast<const Real*>(L->drho),
+                                                    static_cast<const Real*>(L->kap), dst, gh);
+    src = dst;
+  }
+  RPK_CUDA(timing_end(L, RPK_KC_DIFFUSE, L->nsub));
+  return check_launch("rotational transport");
+}
+
+template <typename Store, typename Real>
+rpk_status Ops<Store, Real>::step(rpk_lattice* L, int64_t n) {
+  const StepConst<Real> K = make_const<Real>(L);
+  const bool res = L->grid.bc_x == RPK_BC_RESERVOIR;
+  for (int64_t t = 0; t < n; ++t) {
+    rpk_status st;
+    RPK_CUDA(timing_begin(L));
+    if (L->streamed)
+      st = res ? collide_launch<Store, Real, false, 1>(L, K) : collide_launch<Store, Real, false, 0>(L, K);
+    else
+      st = res ? collide_launch<Store, Real, true, 1>(L, K) : collide_launch<Store, Real, true, 0>(L, K);
+    if (st != RPK_OK) return st;
+    RPK_CUDA(timing_end(L, RPK_KC_COLLIDE, 1));
+    st = res ? transport_launch<Real, 1>(L, K) : transport_launch<Real, 0>(L, K);
+    if (st != RPK_OK) return st;
+    L->cur ^= 1;
+    L->streamed = false;
+    L->steps += 1;
+  }
+  return RPK_OK;
+}
+
+template <typename Store, typename Real>
+rpk_status Ops<Store, Real>::init(rpk_lattice* L, const double* rho, const double* u,
+                                  const double* T, const double* R) {
+  const StepConst<Real> K = make_const<Real>(L);
+  const Real hdt = Real(0.5 * L->relax.dt / L->relax.tau1);
+  L->cur = 0;
+  k_init<Store, Real><<<point_grid(L, 128), 128, 0, L->stream>>>(
+      K, hdt, rho, u, T, R, static_cast<Store*>(L->pop[0]), static_cast<Real*>(L->e),
+      static_cast<Real*>(L->u[0]), static_cast<Real*>(L->u[1]));
+  return check_launch("k_init");
+}
+
+template <typename Store, typename Real>
+rpk_status Ops<Store, Real>::ghosts(rpk_lattice* L) {
+  const StepConst<Real> K = make_const<Real>(L);
+  const Real hdt = Real(0.5 * L->relax.dt / L->relax.tau1);
+  double* dst = L->diag_out;  // 12 doubles of staging (diag_out holds 16)
+  RPK_CUDA(cudaMemcpyAsync(dst, L->res, 12 * sizeof(double), cudaMemcpyHostToDevice, L->stream));
+  k_ghost<Real><<<1, 32, 0, L->stream>>>(K, hdt, dst, static_cast<Real*>(L->ghost));
+  rpk_status st = check_launch("k_ghost");
+  if (st != RPK_OK) return st;
+  RPK_CUDA(cudaStreamSynchronize(L->stream));
+  return RPK_OK;
+}
+
+template <typename Store, typename Real>
+rpk_status Ops<Store, Real>::moments(rpk_lattice* L, double* rho, double* u, double* T,
+                                     double* R, double* E) {
+  const StepConst<Real> K = make_const<Real>(L);
+  const Store* pin = static_cast<const Store*>(L->pop[L->cur]);
+  const Real* e = static_cast<const Real*>(L->e);
+  const Real* gh = static_cast<const Real*>(L->ghost);
+  const dim3 grid = point_grid(L, 128);
+  const bool res = L->grid.bc_x == RPK_BC_RESERVOIR;
+  if (L->streamed)
+    k_moments<Store, Real, false, 0><<<grid, 128, 0, L->stream>>>(K, pin, e, gh, rho, u, T, R, E);
+  else if (res)
+    k_moments<Store, Real, true, 1><<<grid, 128, 0, L->stream>>>(K, pin, e, gh, rho, u, T, R, E);
+  else
+    k_moments<Store, Real, true, 0><<<grid, 128, 0, L->stream>>>(K, pin, e, gh, rho, u, T, R, E);
+  return check_launch("k_moments");
+}
+
+template <typename Store, typename Real>
+rpk_status Ops<Store, Real>::diag(rpk_lattice* L, double out[8]) {
+  const StepConst<Real> K = make_const<Real>(L);
+  const Store* pin = static_cast<const Store*>(L->pop[L->cur]);
+  const Real* e = static_cast<const Real*>(L->e);
+  const Real* gh = static_cast<const Real*>(L->ghost);
+  const int64_t need = (L->npts + kDiagThreads - 1) / kDiagThreads;
+  const int nblk = (int)std::max<int64_t>(1, std::min<int64_t>(kDiagBlocks, need));
+  const bool res = L->grid.bc_x == RPK_BC_RESERVOIR;
+  if (L->streamed)
+    k_diag<Store, Real, false, 0><<<nblk, kDiagThreads, 0, L->stream>>>(K, pin, e, gh, L->diag_partial);
+  else if (res)
+    k_diag<Store, Real, true, 1><<<nblk, kDiagThreads, 0, L->stream>>>(K, pin, e, gh, L->diag_partial);
+  else
+    k_diag<Store, Real, true, 0><<<nblk, kDiagThreads, 0, L->stream>>>(K, pin, e, gh, L->diag_partial);
+  rpk_status st = check_launch("k_diag");
+  if (st != RPK_OK) return st;
+  k_diag_final<<<1, 1024, 0, L->stream>>>(L->diag_partial, nblk, L->diag_out);
+  st = check_launch("k_diag_final");
+  if (st != RPK_OK) return st;
+  RPK_CUDA(cudaMemcpyAsync(out, L->diag_out, kDiagVals * sizeof(double), cudaMemcpyDeviceToHost,
+                           L->stream));
+  RPK_CUDA(cudaStreamSynchronize(L->stream));
+  return RPK_OK;
+}
+
+}  // namespace rpk

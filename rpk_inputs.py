@@ -150,3 +150,16 @@ def random_smooth(nx, ny, nz, theta0, seed=SEED, amp=0.02, aniso_R=0.02):
     ph = rng.uniform(0, 2 * np.pi, 3)
     f["R"] = f["T"] * (1.0 + aniso_R * np.cos(k[0] * X[0] + ph[0]) * np.cos(k[1] * X[1] + ph[1]))
     return f
+
+
+def tile(fields, nx, ny, nz, reps):
+    """Repeat a periodic field set on an (nx, ny, nz) box reps = (rx, ry, rz)
+    times along each axis; the result lives on (rx nx, ry ny, rz nz)."""
+    rx, ry, rz = reps
+
+    def t(a, ncomp):
+        a = np.asarray(a).reshape(ncomp, 2, nz, ny, nx)
+        return np.tile(a, (1, 1, rz, ry, rx)).reshape(ncomp, -1)
+
+    return {"rho": t(fields["rho"], 1)[0], "u": t(fields["u"], 3),
+            "T": t(fields["T"], 1)[0], "R": t(fields["R"], 1)[0]}

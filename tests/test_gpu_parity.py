@@ -1,0 +1,233 @@
+"""GPU parity: librpk (CUDA, through the C interface) against the FP64 oracle
+on the same seeded inputs.
+
+Tolerances:
+  FP64 storage/arithmetic  relative L-inf <= 1e-12 per field (rounding order
+                           differs: the kernels work in deviation form and
+                           pair by pair).
+  FP32                     relative L-inf <= 1e-5 for rho, u, theta_T, E_rot
+                           after 1000 steps of a smooth flow.
+Relative L-inf of a field a against the oracle's b is max|a - b| / max|b|.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+import paper_2201_05280_gb300 as rpk
+import rpk_inputs as I
+from oracle import params as PM
+
+pytestmark = pytest.mark.gpu
+
+T0 = 0.2948964908710633
+FIELDS = ("rho", "u", "T", "R", "Erot")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2201_05280_gb300 import build as B
+    B.build()
+    import torch
+    assert torch.cuda.is_available()
+    torch.cuda.set_device(0)
+
+
+def rel_linf(a, b):
+    return float(np.abs(np.asarray(a) - np.asarray(b)).max() / max(np.abs(b).max(), 1e-300))
+
+
+def run_pair(nx, ny, nz, f, relax, nsteps, precision="f64", bcx=0, res=None, chunks=1):
+    """Run both sides; returns (gpu fields, oracle fields, gpu lattice, oracle state)."""
+    lat = rpk.Lattice(nx, ny, nz, precision=precision, bc_x="reservoir" if bcx else "periodic")
+    lat.set_relax(**relax)
+    if bcx:
+        lat.set_reservoirs(res)
+    lat.init_fields(f["rho"], f["u"], f["T"], f["R"])
+    nsub = lat.info()["nsub"]
+    P = O.make_params(relax["delta"], relax["tau"], relax["tau1"], relax.get("b", 0.0),
+                      relax.get("k_r", 0.0), 1.0, nsub, bcx)
+    S = O.State(P, nx, ny, nz, reservoirs=res).init_fields(f["rho"], f["u"], f["T"], f["R"])
+    for _ in range(chunks):
+        lat.step(nsteps // chunks)
+        S.step(nsteps // chunks)
+    return lat.read_moments(), S.fields(), lat, S
+
+
+def assert_fields(got, ref, tol, keys=FIELDS):
+    errs = {k: rel_linf(got[k], ref[k]) for k in keys}
+    assert all(v <= tol for v in errs.values()), errs
+    return errs
+
+
+RELAX = dict(delta=2.0, tau=0.6, tau1=0.8, b=0.3, k_r=0.9, nsub=2)
+
+
+@pytest.mark.parametrize("dims", [(150, 3, 2), (1, 1, 1), (2, 1, 1), (5, 4, 3), (129, 1, 1)])
+def test_f64_parity_small_and_ragged(dims):
+    nx, ny, nz = dims
+    f = I.random_smooth(nx, ny, nz, T0)
+    got, ref, lat, S = run_pair(nx, ny, nz, f, RELAX, 40)
+    assert_fields(got, ref, 1e-12)
+    d, dr = lat.diagnostics(), S.diag()
+    assert abs(d["M"] - dr["M"]) <= 1e-12 * dr["M"]
+    assert abs(d["E"] - dr["E"]) <= 1e-12 * dr["E"]
+    assert np.abs(d["J"] - dr["J"]).max() <= 1e-12 * dr["M"]
+    assert abs(d["H1"] - dr["H1"]) <= 1e-11 * abs(dr["H1"])
+    assert abs(d["min_g"] - dr["min_g"]) <= 1e-13
+    assert d["status"] == 0 and d["steps"] == 40
+
+
+@pytest.mark.parametrize("relax", [dict(delta=2.0, tau=0.3, tau1=0.38, b=0.0, k_r=0.97),
+                                   dict(delta=6.09, tau=2.0, tau1=1.2, b=-0.4, k_r=0.0, nsub=1),
+                                   dict(delta=0.03, tau=0.9, tau1=3.0, b=0.8, k_r=2.0)])
+def test_f64_parity_parameter_range(relax):
+    nx, ny, nz = 40, 6, 5
+    f = I.random_smooth(nx, ny, nz, T0, seed=7)
+    got, ref, lat, S = run_pair(nx, ny, nz, f, relax, 30)
+    assert_fields(got, ref, 1e-12)
+
+
+def _tube(weak):
+    nx = 2000
+    gamma, Kn, lam, Pr = 1.4, 1e-3, 0.6, 0.71
+    nu = Kn * np.sqrt(gamma * T0) * nx
+    eta, etaB, kap = rpk.gas_from_nondim(gamma, nu, lam, Pr)
+    r = rpk.map_gas(gamma, eta, etaB, kap, 0.0)
+    relax = {k: r[k] for k in ("delta", "tau", "tau1", "b", "k_r")}
+    if weak:
+        f, res = I.shock_tube(nx, T0, rho_r=1 / 1.5, p_r=0.5)
+    else:
+        f, res = I.shock_tube(nx, T0)
+    return nx, f, res, relax
+
+
+def test_f64_shock_tube_weak_1000_steps():
+    """Quasi-1-D diatomic tube, 2000 cells, Kn = 1e-3, Pr = 0.71, eta_B/eta = 0.6,
+    reservoirs at both x ends, pressure ratio 2 / density ratio 1.5, 1000 steps."""
+    nx, f, res, relax = _tube(weak=True)
+    got, ref, lat, S = run_pair(nx, 1, 1, f, relax, 1000, bcx=1, res=res)
+    assert_fields(got, ref, 1e-12)
+
+
+def test_f64_sod_400_steps():
+    """Full Sod ratios (rho 1/0.125, p 1/0.1), 400 steps: before the Hermite-3
+    equilibrium loses positivity at the shock (later steps blow up on both sides)."""
+    nx, f, res, relax = _tube(weak=False)
+    got, ref, lat, S = run_pair(nx, 1, 1, f, relax, 400, bcx=1, res=res)
+    assert_fields(got, ref, 1e-12)
+
+
+def test_f64_conservation_1000_steps():
+    nx, ny, nz = 16, 8, 6
+    f = I.random_smooth(nx, ny, nz, T0, seed=3)
+    lat = rpk.Lattice(nx, ny, nz, precision="f64").set_relax(**RELAX)
+    lat.init_fields(f["rho"], f["u"], f["T"], f["R"])
+    d0 = lat.diagnostics()
+    lat.step(1000)
+    d1 = lat.diagnostics()
+    assert abs(d1["M"] - d0["M"]) <= 1e-12 * d0["M"]
+    assert np.abs(d1["J"] - d0["J"]).max() <= 1e-12 * d0["M"]
+    assert abs(d1["E"] - d0["E"]) <= 1e-12 * d0["E"]
+
+
+def test_f32_smooth_flow_1000_steps():
+    """FP32 path on a smooth 3-D wave field: relative L-inf <= 1e-5 on rho, u,
+    theta_T and E_rot after 1000 steps against the FP64 oracle."""
+    nx, ny, nz = 24, 16, 8
+    f, _ = I.fourier_modes(nx, ny, nz, T0, amp=1e-3)
+    relax = dict(delta=2.0, tau=0.3, tau1=0.38, b=0.0, k_r=0.97)
+    got, ref, lat, S = run_pair(nx, ny, nz, f, relax, 1000, precision="f32")
+    errs = assert_fields(got, ref, 1e-5, keys=("rho", "u", "T", "Erot"))
+    print("f32 errors", errs)
+
+
+def test_full_size_256_cubed_f32_against_periodic_tile():
+    """The benchmark's 256^3 launch configuration: the input is the seeded
+    wave field of a 32^3 box tiled 8 x 8 x 8, so the exact answer is the
+    oracle's 32^3 run tiled back. 20 steps, FP32 vs FP64 oracle."""
+    small, reps, nsteps = 32, 8, 20
+    f, _ = I.fourier_modes(small, small, small, T0, amp=1e-3)
+    F = I.tile(f, small, small, small, (reps, reps, reps))
+    n = small * reps
+    relax = dict(delta=2.0, tau=0.3, tau1=0.38, b=0.0, k_r=0.97)
+    lat = rpk.Lattice(n, n, n, precision="f32").set_relax(**relax)
+    lat.init_fields(F["rho"], F["u"], F["T"], F["R"])
+    nsub = lat.info()["nsub"]
+    lat.step(nsteps)
+    got = lat.read_moments()
+    d = lat.diagnostics()
+    lat.close()
+    P = O.make_params(2.0, 0.3, 0.38, 0.0, 0.97, 1.0, nsub, 0)
+    S = O.State(P, small, small, small).init_fields(f["rho"], f["u"], f["T"], f["R"]).step(nsteps)
+    Fs = S.fields()
+    ref = I.tile(Fs, small, small, small, (reps, reps, reps))
+    ref["Erot"] = I.tile(dict(Fs, rho=Fs["Erot"]), small, small, small, (reps, reps, reps))["rho"]
+    assert_fields(got, ref, 1e-5, keys=("rho", "u", "T", "Erot"))
+    assert d["status"] == 0
+
+
+def test_checkpoint_restart_is_bitwise(tmp_path):
+    nx, ny, nz = 20, 6, 4
+    f = I.random_smooth(nx, ny, nz, T0, seed=11)
+    for prec in ("f64", "f32"):
+        a = rpk.Lattice(nx, ny, nz, precision=prec).set_relax(**RELAX)
+        a.init_fields(f["rho"], f["u"], f["T"], f["R"]).step(10)
+        path = str(tmp_path / ("ck_%s.bin" % prec))
+        a.save(path)
+        a.step(10)
+        ra = a.read_moments()
+        b = rpk.Lattice(nx, ny, nz, precision=prec).load(path)
+        assert b.info()["steps"] == 10
+        b.step(10)
+        rb = b.read_moments()
+        for k in FIELDS:
+            np.testing.assert_array_equal(ra[k], rb[k])
+
+
+def test_device_arrays_path():
+    import torch
+    nx, ny, nz = 30, 4, 3
+    f = I.random_smooth(nx, ny, nz, T0, seed=5)
+    dev = {k: torch.from_numpy(np.ascontiguousarray(v)).cuda() for k, v in f.items()}
+    a = rpk.Lattice(nx, ny, nz, precision="f64").set_relax(**RELAX)
+    a.init_fields(dev["rho"], dev["u"], dev["T"], dev["R"]).step(5)
+    n = a.npts
+    out = {"rho": torch.empty(n, dtype=torch.float64, device="cuda"),
+           "u": torch.empty(3 * n, dtype=torch.float64, device="cuda"),
+           "T": torch.empty(n, dtype=torch.float64, device="cuda"),
+           "R": torch.empty(n, dtype=torch.float64, device="cuda"),
+           "Erot": torch.empty(n, dtype=torch.float64, device="cuda")}
+    got = a.read_moments(out)
+    b = rpk.Lattice(nx, ny, nz, precision="f64").set_relax(**RELAX)
+    b.init_fields(f["rho"], f["u"], f["T"], f["R"]).step(5)
+    ref = b.read_moments()
+    for k in FIELDS:
+        np.testing.assert_array_equal(got[k].cpu().numpy().reshape(ref[k].shape), ref[k])
+
+
+def test_error_paths():
+    a = rpk.Lattice(4, 4, 4, precision="f32")
+    with pytest.raises(rpk.RpkError) as e:
+        a.step(1)
+    assert e.value.code == 5  # before init
+    with pytest.raises(rpk.RpkError) as e:
+        a.set_relax(delta=2.0, tau=-1.0, tau1=1.0)
+    assert e.value.code == 2
+    a.set_relax(**RELAX)
+    f = I.uniform(4, 4, 4, T0)
+    bad = dict(f)
+    bad["T"] = f["T"].copy()
+    bad["T"][3] = -1.0
+    with pytest.raises(rpk.RpkError) as e:
+        a.init_fields(bad["rho"], bad["u"], bad["T"], bad["R"])
+    assert e.value.code == 2
+    a.init_fields(f["rho"], f["u"], f["T"], f["R"])
+    with pytest.raises(rpk.RpkError) as e:
+        a.step(-1)
+    assert e.value.code == 1
+    b = rpk.Lattice(4, 4, 4, precision="f32", bc_x="reservoir").set_relax(**RELAX)
+    with pytest.raises(rpk.RpkError) as e:
+        b.init_fields(f["rho"], f["u"], f["T"], f["R"])
+    assert e.value.code == 5  # reservoirs missing
