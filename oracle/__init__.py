@@ -61,11 +61,7 @@ _lib = None
 _dp = ctypes.POINTER(ctypes.c_double)
 
 
-def _load():
-    global _lib
-    if _lib is not None:
-        return _lib
-    lib = ctypes.CDLL(build())
+def _configure(lib):
     P = ctypes.POINTER(Params)
     i, l, d = ctypes.c_int, ctypes.c_long, ctypes.c_double
     sig = {
@@ -85,8 +81,47 @@ def _load():
         fn = getattr(lib, name)
         fn.restype = res
         fn.argtypes = args
-    _lib = lib
     return lib
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        _lib = _configure(ctypes.CDLL(build()))
+    return _lib
+
+
+class using_library:
+    """Context manager that routes every oracle call to another build of the
+    oracle source (used by the mutation tests to plant mistakes on the CPU)."""
+
+    def __init__(self, path):
+        self.path = path
+
+    def __enter__(self):
+        global _lib
+        self.saved = _load()
+        _lib = _configure(ctypes.CDLL(self.path))
+        return self
+
+    def __exit__(self, *exc):
+        global _lib
+        _lib = self.saved
+
+
+def compile_variant(source_text, out_path):
+    """Compile a modified copy of the oracle source with the same flags."""
+    src = out_path + ".c"
+    with open(src, "w") as f:
+        f.write(source_text)
+    subprocess.check_call(["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-fno-fast-math",
+                           "-fPIC", "-shared", "-o", out_path, src, "-lm"])
+    return out_path
+
+
+def source():
+    with open(_SRC) as f:
+        return f.read()
 
 
 def _ptr(a):

@@ -153,3 +153,22 @@ def test_h1_non_increasing_in_homogeneous_relaxation(tau, tau1, b):
     assert np.all(np.isfinite(H))
     assert np.all(np.diff(H) <= 1e-13 * abs(H[0]))
     assert H[-1] < H[0]
+
+
+@pytest.mark.parametrize("rho,theta", [(1.0, T0), (1.3, T0), (0.7, 1.1 * T0)])
+def test_h1_value_at_rest_equilibrium(rho, theta):
+    """At rest with theta_T = theta_R = theta0 the discrete state is f = rho w,
+    so H1 = rho ln rho - rho - (delta/2) rho ln theta0 per point; away from
+    theta0 compare with the same sum taken over the target itself."""
+    P = _params()
+    S = O.State(P, 1, 1, 1)
+    u0 = np.zeros((3, 2))
+    S.init_fields(np.full(2, rho), u0, np.full(2, theta), np.full(2, theta))
+    H = S.diag()["H1"]
+    c, w = O.lattice()
+    feq = O.target(rho, np.zeros(3), theta * np.eye(3))
+    expect = 2 * ((feq * np.log(feq / w) - feq).sum() - 0.5 * P.delta * rho * np.log(theta))
+    assert abs(H - expect) < 1e-13 * max(1.0, abs(expect))
+    if theta == T0:
+        closed = 2 * (rho * np.log(rho) - rho - 0.5 * P.delta * rho * np.log(T0))
+        assert abs(H - closed) < 1e-13 * max(1.0, abs(closed))

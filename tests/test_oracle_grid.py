@@ -162,3 +162,11 @@ def test_reservoir_equilibrium_is_fixed():
     S.step(10)
     np.testing.assert_allclose(S.g, g0, atol=1e-16)
     np.testing.assert_allclose(S.Er, E0, atol=1e-16)
+
+
+def test_one_step_from_rest_is_mirror_symmetric():
+    """x -> -x symmetry of one step from a state at rest with varying rho,
+    theta_T and theta_R (no advection at u = 0): pins the streaming of the
+    half velocities and the symmetric face conductivity of the FTCS."""
+    from test_oracle_mutants import _pin_mirror
+    assert _pin_mirror()
