@@ -71,24 +71,30 @@ def fourier_modes(nx, ny, nz, theta0, nmodes=8, amp=1e-3, seed=SEED, nmax=3):
     """Uniform rho = 1, theta = theta0 plus ``nmodes`` seeded Fourier modes.
 
     Wave vectors n in [-nmax, nmax]^3 \\ {0}, distinct up to sign, restricted to
-    axes with more than one cell; each mode carries random-phase perturbations of
-    amplitude ``amp`` in rho, theta and in u (a random direction, so it has shear
-    and longitudinal parts). Returns (fields, list of mode dicts).
+    axes with more than one cell (fewer modes when fewer exist; none on a box of
+    one cell); each mode carries random-phase perturbations of amplitude ``amp``
+    in rho, theta and in u (a random direction, so it has shear and
+    longitudinal parts). Returns (fields, list of mode dicts).
     """
     rng = np.random.default_rng(seed)
     X = positions(nx, ny, nz)
     L = np.array([nx, ny, nz], float)
     f = uniform(nx, ny, nz, theta0)
     active = [d for d in range(3) if (nx, ny, nz)[d] > 1]
-    seen, modes = set(), []
-    while len(modes) < nmodes:
-        n = np.zeros(3, int)
-        for d in active:
-            n[d] = rng.integers(-nmax, nmax + 1)
-        key = tuple(n)
-        if not any(n) or key in seen or tuple(-n) in seen:
-            continue
-        seen.add(key)
+    # every admissible wave vector, one representative per +-pair
+    cands = []
+    rngs = [range(-nmax, nmax + 1) if d in active else range(1) for d in range(3)]
+    for a in rngs[0]:
+        for b in rngs[1]:
+            for c in rngs[2]:
+                n = (a, b, c)
+                if any(n) and (-a, -b, -c) not in cands:
+                    cands.append(n)
+    count = min(nmodes, len(cands))
+    picks = rng.permutation(len(cands))[:count]
+    modes = []
+    for idx in picks:
+        n = np.array(cands[idx], int)
         k = 2.0 * np.pi * n / L
         ph = k @ X
         a = amp * rng.uniform(0.5, 1.0, size=3)
@@ -97,7 +103,8 @@ def fourier_modes(nx, ny, nz, theta0, nmodes=8, amp=1e-3, seed=SEED, nmax=3):
         for dd in range(3):
             if dd not in active:
                 d[dd] = 0.0
-        d /= np.linalg.norm(d)
+        nd = np.linalg.norm(d)
+        d = d / nd if nd > 0 else d
         f["rho"] += a[0] * np.cos(ph + phi[0])
         f["T"] += theta0 * a[1] * np.cos(ph + phi[1])
         f["u"] += (a[2] * np.cos(ph + phi[2]))[None, :] * d[:, None]
