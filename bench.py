@@ -65,14 +65,19 @@ def ncu_traffic(prec):
     """DRAM bytes per point of the collide kernel from the committed ncu
     summary, if the kernel source has not changed since it was captured."""
     path = os.path.join(ROOT, "profiles", "ncu_collide_%s.txt" % prec)
-    src = os.path.join(ROOT, "paper_2201_05280_gb300", "csrc", "rpk_kernels.cuh")
+    csrc = os.path.join(ROOT, "paper_2201_05280_gb300", "csrc")
+    srcs = [os.path.join(csrc, f) for f in ("rpk_lattice.cuh", "rpk_device.cuh", "rpk_collide.cuh")]
     try:
         kv = {}
         for line in open(path):
             if ":" in line and not line.startswith("#"):
                 k, v = line.split(":", 1)
                 kv[k.strip()] = v.strip()
-        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+        h = hashlib.sha256()
+        for src in srcs:
+            with open(src, "rb") as f:
+                h.update(f.read())
+        sha = h.hexdigest()
         if kv.get("kernel_source_sha256") != sha:
             return None
         return float(kv["dram_bytes_per_point"])

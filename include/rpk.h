@@ -176,13 +176,12 @@ rpk_status rpk_get_info(rpk_lattice* lat, int64_t out[4]);
 
 /* Kernel timing (a tracing aid; the paper has no counterpart). While enabled,
  * rpk_step brackets each kernel class with CUDA events recorded on the
- * lattice's stream: RPK_KC_COLLIDE (pull-stream + collide + exchange),
- * RPK_KC_ADVECT (MacCormack predictor and corrector) and RPK_KC_DIFFUSE (all
- * FTCS sub-steps). rpk_timing(lat, 1) clears the counters and starts;
+ * lattice's stream: RPK_KC_COLLIDE (pull-stream + collide + exchange) and
+ * RPK_KC_TRANSPORT (MacCormack advection and all FTCS sub-steps of E_R). rpk_timing(lat, 1) clears the counters and starts;
  * rpk_timing(lat, 0) stops. rpk_timing_read synchronises the stream and
  * returns the summed milliseconds and the number of kernel launches per class
  * since the last start (arrays of RPK_KC_COUNT entries). */
-enum { RPK_KC_COLLIDE = 0, RPK_KC_ADVECT = 1, RPK_KC_DIFFUSE = 2, RPK_KC_COUNT = 3 };
+enum { RPK_KC_COLLIDE = 0, RPK_KC_TRANSPORT = 1, RPK_KC_COUNT = 2 };
 rpk_status rpk_timing(rpk_lattice* lat, int enable);
 rpk_status rpk_timing_read(rpk_lattice* lat, double* ms, int64_t* launches);
 

@@ -262,11 +262,11 @@ class Lattice:
         return self
 
     def timing_read(self):
-        """{class: (ms, launches)} for 'collide', 'advect', 'diffuse' since the last start."""
-        ms = (ctypes.c_double * 3)()
-        n = (ctypes.c_int64 * 3)()
+        """{class: (ms, launches)} for 'collide' and 'transport' since the last start."""
+        ms = (ctypes.c_double * 2)()
+        n = (ctypes.c_int64 * 2)()
         _check(load_library().rpk_timing_read(self._h, ms, n))
-        return {name: (ms[i], n[i]) for i, name in enumerate(("collide", "advect", "diffuse"))}
+        return {name: (ms[i], n[i]) for i, name in enumerate(("collide", "transport"))}
 
     def info(self):
         out = (ctypes.c_int64 * 4)()

@@ -1,0 +1,58 @@
+// The fused pull-stream + collide + rotational-exchange kernel (hot path,
+// rows a1-a6 of the step; Sec. 5).
+#pragma once
+
+#include "rpk_device.cuh"
+
+namespace rpk {
+
+// One collision per point after the pull (Sec. 5):
+//   g' = (1 - 2 beta*) g + 2 beta* f^mix,   in h form: h' = c_keep h + c_relax (f^mix/w - 1)
+//   Er' = Er + dt (delta rho/2)(theta - theta_R)/tau1   (rotational exchange)
+// Writes h', e', rho - 1, u (ring slot of this step) and kappa_R.
+template <typename Store, typename Real, bool kPull, int kBC>
+__global__ void __launch_bounds__(128)
+    k_collide(StepConst<Real> K, const Store* __restrict__ pin, Store* __restrict__ pout,
+              const Real* __restrict__ e_in, Real* __restrict__ e_out, Real* __restrict__ drho_out,
+              Real* __restrict__ u_out, Real* __restrict__ kap_out,
+              const Real* __restrict__ ghost, unsigned* __restrict__ status) {
+  PointIdx P;
+  if (!point_from_block(K, P)) return;
+  const int64_t p = (int64_t)P.s * K.n3 + P.cell;
+  Real h[kQ];
+  gather<Store, Real, kPull, kBC>(pin, ghost, K, P, h);
+  Mom<Real> m;
+  raw_moments(h, m);
+  const Real e = e_in[p];
+  recover(m, e, K);
+  Herm<Real> H;
+  mix_coeffs(m, K, H);
+  Store* out = pout + (int64_t)(P.s * kQ) * K.n3 + P.cell;
+  const int64_t n3 = K.n3;
+  out[0] = from_real<Store, Real>(K.c_keep * h[0] + K.c_relax * H.e0);
+  static_for<kPairs>([&](auto kc) {
+    constexpr int k = decltype(kc)::value;
+    constexpr Vel2 v = kPairVel2[k];
+    const Real ev = herm_even<v.x, v.y, v.z>(H);
+    const Real od = herm_odd<v.x, v.y, v.z>(H);
+    out[(int64_t)(2 * k + 1) * n3] = from_real<Store, Real>(K.c_keep * h[2 * k + 1] + K.c_relax * (ev + od));
+    out[(int64_t)(2 * k + 2) * n3] = from_real<Store, Real>(K.c_keep * h[2 * k + 2] + K.c_relax * (ev - od));
+  });
+  e_out[p] = e + K.exc * m.rho * (m.dth - m.dR);
+  drho_out[p] = m.drho;
+  const int64_t npts = 2 * K.n3;
+  u_out[p] = m.j[0] * m.inv_rho;
+  u_out[npts + p] = m.j[1] * m.inv_rho;
+  u_out[2 * npts + p] = m.j[2] * m.inv_rho;
+  kap_out[p] = K.kapc * m.rho * (K.theta0 + m.dth);
+  const bool ok = (m.rho > Real(0)) && (K.theta0 + m.dT > Real(0)) && (K.theta0 + m.dR > Real(0));
+  if (!ok) {
+    unsigned f = 0;
+    if (!(m.rho == m.rho) || !(m.dT == m.dT) || !(m.dR == m.dR)) f |= 1u;
+    if (!(m.rho > Real(0))) f |= 2u;
+    if (!(K.theta0 + m.dT > Real(0)) || !(K.theta0 + m.dR > Real(0))) f |= 4u;
+    atomicOr(status, f);
+  }
+}
+
+}  // namespace rpk

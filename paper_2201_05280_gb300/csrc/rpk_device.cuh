@@ -1,0 +1,357 @@
+// Device helpers of the reduced polyatomic ES-BGK lattice-Boltzmann step
+// (Kolluru, Atif & Ansumali, arXiv 2201.05280, Sec. 4 and Sec. 5): storage
+// conversions, per-launch constants, moments, the f-level recovery, Hermite
+// targets and the BCC pull gather.
+//
+// Data layout (HBM):
+//   populations  Store pop[2][41][nz][ny][nx] per buffer, i.e. element
+//                (s*41 + q)*n3 + (z*ny + y)*nx + x; two buffers ping-pong.
+//                Reduced-precision storage holds h_q = g_q/w_q - 1; FP64 too.
+//   scalar fields Real f[2][nz][ny][nx] (point index p = s*n3 + cell).
+//   e            auxiliary rotational energy minus delta*theta0/2 (deviation)
+//   drho         rho - 1 of the last collision
+//   u            two ring slots of 3 planes each: u(t) and u(t-1)
+//   kap          kappa_R of the last collision
+// The state between steps is "post-collision, pre-stream": the collide kernel
+// pulls g(x - c_q) from the previous buffer. Right after initialisation the
+// state is post-stream instead (kPull = false reads the point's own slot).
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+#include <utility>
+
+#include "rpk_lattice.cuh"
+
+namespace rpk {
+
+// ---------------------------------------------------------------------------
+// storage conversions
+
+template <typename S, typename R>
+__device__ __forceinline__ R to_real(S v) { return static_cast<R>(v); }
+template <>
+__device__ __forceinline__ float to_real<__half, float>(__half v) { return __half2float(v); }
+template <>
+__device__ __forceinline__ float to_real<__nv_bfloat16, float>(__nv_bfloat16 v) {
+  return __bfloat162float(v);
+}
+template <typename S, typename R>
+__device__ __forceinline__ S from_real(R v) { return static_cast<S>(v); }
+template <>
+__device__ __forceinline__ __half from_real<__half, float>(float v) { return __float2half_rn(v); }
+template <>
+__device__ __forceinline__ __nv_bfloat16 from_real<__nv_bfloat16, float>(float v) {
+  return __float2bfloat16_rn(v);
+}
+
+// compile-time loop: f(std::integral_constant<int, K>) for K = 0..N-1
+template <typename F, int... K>
+__device__ __forceinline__ void static_for_impl(F&& f, std::integer_sequence<int, K...>) {
+  (f(std::integral_constant<int, K>{}), ...);
+}
+template <int N, typename F>
+__device__ __forceinline__ void static_for(F&& f) {
+  static_for_impl(f, std::make_integer_sequence<int, N>{});
+}
+
+// ---------------------------------------------------------------------------
+// per-launch constants (host fills them in double, then casts)
+
+template <typename Real>
+struct StepConst {
+  int nx, ny, nz;
+  int64_t n3;     // nx*ny*nz
+  Real theta0;
+  Real c_keep;    // 1 - 2 beta*
+  Real c_relax;   // 2 beta*
+  Real beta;      // beta* = dt/(2 tau* + dt)
+  Real w_es;      // tau*/tau
+  Real w_eq;      // tau*/tau1
+  Real b;
+  Real inv_sig;   // 1 / (1 + dt/(2 tau*) - b dt/(2 tau))
+  Real inv_d;     // 1 / (1 + dt/(2 tau1))
+  Real delta;
+  Real inv_3pd;   // 1 / (3 + delta)
+  Real exc;       // dt delta / (2 tau1)
+  Real kapc;      // k_r 5 tau / (2 B), kappa_R = kapc * rho * theta
+  Real E0;        // delta theta0 / 2
+  Real dt;
+  Real hsub;      // dt / nsub
+};
+
+// Ghost (reservoir) values, one block of kGhostStride per x end.
+constexpr int kGhostStride = 48;
+enum { kGhE = 41, kGhDrho = 42, kGhU = 43, kGhKap = 46 };
+
+// ---------------------------------------------------------------------------
+// moments and Hermite targets (all in deviation form about rho = 1, theta0)
+
+template <typename Real>
+struct Mom {
+  Real drho, rho, inv_rho;
+  Real j[3];
+  Real dP[6];    // sum w h c_a c_b: xx yy zz xy xz yz
+  Real dTg;      // theta_T(g) - theta0
+  Real dth;      // theta - theta0 (eq. thetadef)
+  Real dT, dR;   // theta_T(f) - theta0, theta_R - theta0
+  Real sig[6];   // sigma(f), a density
+};
+
+// rho, j, P of g = w (1 + h), pair by pair.
+template <typename Real>
+__device__ __forceinline__ void raw_moments(const Real (&h)[kQ], Mom<Real>& m) {
+  Real d = Real(kWeightRest) * h[0];
+  Real jx = 0, jy = 0, jz = 0, pxx = 0, pyy = 0, pzz = 0, pxy = 0, pxz = 0, pyz = 0;
+  static_for<kPairs>([&](auto kc) {
+    constexpr int k = decltype(kc)::value;
+    constexpr Vel2 v = kPairVel2[k];
+    constexpr double w = pair_weight(k);
+    const Real ev = Real(w) * (h[2 * k + 1] + h[2 * k + 2]);
+    const Real od = Real(w) * (h[2 * k + 1] - h[2 * k + 2]);
+    d += ev;
+    if constexpr (v.x != 0) jx += Real(0.5 * v.x) * od;
+    if constexpr (v.y != 0) jy += Real(0.5 * v.y) * od;
+    if constexpr (v.z != 0) jz += Real(0.5 * v.z) * od;
+    if constexpr (v.x != 0) pxx += Real(0.25 * v.x * v.x) * ev;
+    if constexpr (v.y != 0) pyy += Real(0.25 * v.y * v.y) * ev;
+    if constexpr (v.z != 0) pzz += Real(0.25 * v.z * v.z) * ev;
+    if constexpr (v.x * v.y != 0) pxy += Real(0.25 * v.x * v.y) * ev;
+    if constexpr (v.x * v.z != 0) pxz += Real(0.25 * v.x * v.z) * ev;
+    if constexpr (v.y * v.z != 0) pyz += Real(0.25 * v.y * v.z) * ev;
+  });
+  m.drho = d;
+  m.rho = Real(1) + d;
+  m.inv_rho = Real(1) / m.rho;
+  m.j[0] = jx; m.j[1] = jy; m.j[2] = jz;
+  m.dP[0] = pxx; m.dP[1] = pyy; m.dP[2] = pzz;
+  m.dP[3] = pxy; m.dP[4] = pxz; m.dP[5] = pyz;
+}
+
+// f-level moments from g (Sec. 5, g/f relations) and the stored auxiliary
+// rotational energy e (deviation).
+//   theta_T(g) = (tr P - j^2/rho)/(3 rho)
+//   Rt = 2 Er/(delta rho)  (auxiliary rotational temperature)
+//   theta = (3 theta_T(g) + delta Rt)/(3 + delta)   (invariant of the transform)
+//   D = (theta_T(g) - Rt)/(1 + dt/(2 tau1)) = theta_T(f) - theta_R
+//   theta_T(f) = theta + delta D/(3 + delta),  theta_R = theta - 3 D/(3 + delta)
+//   sigma(f) = (P - jj/rho - rho theta_T(g) I)/(1 + dt/(2 tau*) - b dt/(2 tau))
+template <typename Real>
+__device__ __forceinline__ void recover(Mom<Real>& m, Real e, const StepConst<Real>& K) {
+  const Real t0 = K.theta0;
+  const Real jj = m.j[0] * m.j[0] + m.j[1] * m.j[1] + m.j[2] * m.j[2];
+  const Real trdP = m.dP[0] + m.dP[1] + m.dP[2];
+  m.dTg = (trdP - jj * m.inv_rho - Real(3) * t0 * m.drho) * m.inv_rho * Real(1.0 / 3.0);
+  const Real dRt = (Real(2) * e - K.delta * t0 * m.drho) * m.inv_rho / K.delta;
+  m.dth = (Real(3) * m.dTg + K.delta * dRt) * K.inv_3pd;
+  const Real D = (m.dTg - dRt) * K.inv_d;
+  m.dT = m.dth + K.delta * D * K.inv_3pd;
+  m.dR = m.dth - Real(3) * D * K.inv_3pd;
+  const Real iso = m.rho * m.dTg + t0 * m.drho;
+  const Real ir = m.inv_rho;
+  m.sig[0] = (m.dP[0] - m.j[0] * m.j[0] * ir - iso) * K.inv_sig;
+  m.sig[1] = (m.dP[1] - m.j[1] * m.j[1] * ir - iso) * K.inv_sig;
+  m.sig[2] = (m.dP[2] - m.j[2] * m.j[2] * ir - iso) * K.inv_sig;
+  m.sig[3] = (m.dP[3] - m.j[0] * m.j[1] * ir) * K.inv_sig;
+  m.sig[4] = (m.dP[4] - m.j[0] * m.j[2] * ir) * K.inv_sig;
+  m.sig[5] = (m.dP[5] - m.j[1] * m.j[2] * ir) * K.inv_sig;
+}
+
+// Coefficients of f_q/w_q - 1 for the third-order Hermite expansion of a
+// Gaussian (rho, u, Lambda) about the lattice weights; Dl = Lambda - theta0 I.
+//   f/w = rho + j.c/t0 + A2:(cc - t0 I)/(2 t0^2) + A3:H3(c)/(6 t0^3)
+//   A2 = jj/rho + rho Dl,  A3_abc = j_a j_b j_c/rho^2 + Dl_ab j_c + Dl_bc j_a + Dl_ca j_b
+// even part: e0 + sum E_ab c_a c_b ; odd part: sum O_a c_a + cubic terms.
+template <typename Real>
+struct Herm {
+  Real e0, exx, eyy, ezz, exy, exz, eyz;
+  Real ox, oy, oz;
+  Real oxxx, oyyy, ozzz, oxxy, oxxz, oyyx, oyyz, ozzx, ozzy, oxyz;
+};
+
+template <typename Real>
+__device__ __forceinline__ void hermite(Real drho, Real rho, Real inv_rho, const Real (&j)[3],
+                                        const Real (&Dl)[6], Real t0, Herm<Real>& H) {
+  const Real jx = j[0], jy = j[1], jz = j[2];
+  const Real a2xx = jx * jx * inv_rho + rho * Dl[0];
+  const Real a2yy = jy * jy * inv_rho + rho * Dl[1];
+  const Real a2zz = jz * jz * inv_rho + rho * Dl[2];
+  const Real a2xy = jx * jy * inv_rho + rho * Dl[3];
+  const Real a2xz = jx * jz * inv_rho + rho * Dl[4];
+  const Real a2yz = jy * jz * inv_rho + rho * Dl[5];
+  const Real ir2 = inv_rho * inv_rho;
+  const Real dxx = Dl[0], dyy = Dl[1], dzz = Dl[2], dxy = Dl[3], dxz = Dl[4], dyz = Dl[5];
+  const Real a3xxx = jx * jx * jx * ir2 + Real(3) * dxx * jx;
+  const Real a3yyy = jy * jy * jy * ir2 + Real(3) * dyy * jy;
+  const Real a3zzz = jz * jz * jz * ir2 + Real(3) * dzz * jz;
+  const Real a3xxy = jx * jx * jy * ir2 + dxx * jy + Real(2) * dxy * jx;
+  const Real a3xxz = jx * jx * jz * ir2 + dxx * jz + Real(2) * dxz * jx;
+  const Real a3yyx = jy * jy * jx * ir2 + dyy * jx + Real(2) * dxy * jy;
+  const Real a3yyz = jy * jy * jz * ir2 + dyy * jz + Real(2) * dyz * jy;
+  const Real a3zzx = jz * jz * jx * ir2 + dzz * jx + Real(2) * dxz * jz;
+  const Real a3zzy = jz * jz * jy * ir2 + dzz * jy + Real(2) * dyz * jz;
+  const Real a3xyz = jx * jy * jz * ir2 + dxy * jz + dyz * jx + dxz * jy;
+  const Real i1 = Real(1) / t0;
+  const Real i2 = i1 * i1;
+  const Real i3 = i2 * i1;
+  // even part
+  H.e0 = drho - Real(0.5) * i1 * (a2xx + a2yy + a2zz);
+  H.exx = Real(0.5) * i2 * a2xx;
+  H.eyy = Real(0.5) * i2 * a2yy;
+  H.ezz = Real(0.5) * i2 * a2zz;
+  H.exy = i2 * a2xy;
+  H.exz = i2 * a2xz;
+  H.eyz = i2 * a2yz;
+  // odd part: j.c/t0 - t0 * 3 V.c/(6 t0^3), V_a = sum_b A3_abb
+  const Real vx = a3xxx + a3yyx + a3zzx;
+  const Real vy = a3xxy + a3yyy + a3zzy;
+  const Real vz = a3xxz + a3yyz + a3zzz;
+  H.ox = jx * i1 - Real(0.5) * i2 * vx;
+  H.oy = jy * i1 - Real(0.5) * i2 * vy;
+  H.oz = jz * i1 - Real(0.5) * i2 * vz;
+  const Real s6 = i3 * Real(1.0 / 6.0), s2 = i3 * Real(0.5);
+  H.oxxx = s6 * a3xxx;
+  H.oyyy = s6 * a3yyy;
+  H.ozzz = s6 * a3zzz;
+  H.oxxy = s2 * a3xxy;
+  H.oxxz = s2 * a3xxz;
+  H.oyyx = s2 * a3yyx;
+  H.oyyz = s2 * a3yyz;
+  H.ozzx = s2 * a3zzx;
+  H.ozzy = s2 * a3zzy;
+  H.oxyz = i3 * a3xyz;
+}
+
+template <int VX, int VY, int VZ, typename Real>
+__device__ __forceinline__ Real herm_even(const Herm<Real>& H) {
+  constexpr double cx = 0.5 * VX, cy = 0.5 * VY, cz = 0.5 * VZ;
+  Real r = H.e0;
+  if constexpr (VX != 0) r += Real(cx * cx) * H.exx;
+  if constexpr (VY != 0) r += Real(cy * cy) * H.eyy;
+  if constexpr (VZ != 0) r += Real(cz * cz) * H.ezz;
+  if constexpr (VX * VY != 0) r += Real(cx * cy) * H.exy;
+  if constexpr (VX * VZ != 0) r += Real(cx * cz) * H.exz;
+  if constexpr (VY * VZ != 0) r += Real(cy * cz) * H.eyz;
+  return r;
+}
+
+template <int VX, int VY, int VZ, typename Real>
+__device__ __forceinline__ Real herm_odd(const Herm<Real>& H) {
+  constexpr double cx = 0.5 * VX, cy = 0.5 * VY, cz = 0.5 * VZ;
+  Real r = Real(0);
+  if constexpr (VX != 0) r += Real(cx) * H.ox + Real(cx * cx * cx) * H.oxxx;
+  if constexpr (VY != 0) r += Real(cy) * H.oy + Real(cy * cy * cy) * H.oyyy;
+  if constexpr (VZ != 0) r += Real(cz) * H.oz + Real(cz * cz * cz) * H.ozzz;
+  if constexpr (VX * VY != 0) r += Real(cx * cx * cy) * H.oxxy + Real(cy * cy * cx) * H.oyyx;
+  if constexpr (VX * VZ != 0) r += Real(cx * cx * cz) * H.oxxz + Real(cz * cz * cx) * H.ozzx;
+  if constexpr (VY * VZ != 0) r += Real(cy * cy * cz) * H.oyyz + Real(cz * cz * cy) * H.ozzy;
+  if constexpr (VX * VY * VZ != 0) r += Real(cx * cy * cz) * H.oxyz;
+  return r;
+}
+
+// Hermite coefficients of f^mix = tau*(f^ES/tau + f^Eq/tau1) (Sec. 5): both
+// targets share rho and u and are linear in Lambda, so
+//   Lambda_mix = (tau*/tau)(theta_T I + b sigma/rho) + (tau*/tau1) theta I.
+template <typename Real>
+__device__ __forceinline__ void mix_coeffs(const Mom<Real>& m, const StepConst<Real>& K,
+                                           Herm<Real>& H) {
+  const Real iso = K.w_es * m.dT + K.w_eq * m.dth;
+  const Real bs = K.w_es * K.b * m.inv_rho;
+  Real Dl[6] = {iso + bs * m.sig[0], iso + bs * m.sig[1], iso + bs * m.sig[2],
+                bs * m.sig[3], bs * m.sig[4], bs * m.sig[5]};
+  hermite(m.drho, m.rho, m.inv_rho, m.j, Dl, K.theta0, H);
+}
+
+// ---------------------------------------------------------------------------
+// geometry helpers
+
+__device__ __forceinline__ int wrap_near(int a, int n) {
+  // valid for |a - [0, n)| <= 2; n == 1 maps everything to 0
+  return n == 1 ? 0 : (a < 0 ? a + n : (a >= n ? a - n : a));
+}
+
+struct PointIdx {
+  int s, x, y, z;
+  int64_t cell;  // (z*ny + y)*nx + x
+};
+
+template <typename Real>
+__device__ __forceinline__ bool point_from_block(const StepConst<Real>& K, PointIdx& P) {
+  P.x = blockIdx.x * blockDim.x + threadIdx.x;
+  P.y = blockIdx.y;
+  P.s = blockIdx.z / K.nz;
+  P.z = blockIdx.z - P.s * K.nz;
+  if (P.x >= K.nx) return false;
+  P.cell = ((int64_t)P.z * K.ny + P.y) * K.nx + P.x;
+  return true;
+}
+
+// Gather the 41 populations of point P: from its own slots (kPull = false) or
+// pulled from x - c_q (kPull = true; Sec. 5, BCC layout: a half velocity
+// from sublattice 0 at index x comes from sublattice 1 at x - (c > 0 ? 1 : 0)
+// per axis, and from sublattice 1 it comes from sublattice 0 at
+// x + (c < 0 ? 1 : 0)). kBC = 1: sources beyond the x ends read the reservoir.
+template <typename Store, typename Real, bool kPull, int kBC>
+__device__ __forceinline__ void gather(const Store* __restrict__ pin,
+                                       const Real* __restrict__ ghost, const StepConst<Real>& K,
+                                       const PointIdx& P, Real (&h)[kQ]) {
+  const int64_t n3 = K.n3;
+  if constexpr (!kPull) {
+    const Store* base = pin + (int64_t)(P.s * kQ) * n3 + P.cell;
+#pragma unroll
+    for (int q = 0; q < kQ; ++q) h[q] = to_real<Store, Real>(base[(int64_t)q * n3]);
+  } else {
+    const int nx = K.nx, ny = K.ny, nz = K.nz;
+    int xw[5], yw[5], zw[5];
+    bool xin[5];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+      xw[k] = wrap_near(P.x + k - 2, nx);
+      yw[k] = wrap_near(P.y + k - 2, ny);
+      zw[k] = wrap_near(P.z + k - 2, nz);
+      xin[k] = (P.x + k - 2 >= 0) && (P.x + k - 2 < nx);
+    }
+    // half-velocity source offsets: c > 0 -> s - 1, c < 0 -> s
+    const int s = P.s;
+    const int xhp = s ? xw[2] : xw[1], xhm = s ? xw[3] : xw[2];
+    const int yhp = s ? yw[2] : yw[1], yhm = s ? yw[3] : yw[2];
+    const int zhp = s ? zw[2] : zw[1], zhm = s ? zw[3] : zw[2];
+    const bool xinhp = s ? xin[2] : xin[1], xinhm = s ? xin[3] : xin[2];
+    const Store* same = pin + (int64_t)(s * kQ) * n3;
+    const Store* other = pin + (int64_t)((1 - s) * kQ) * n3;
+    h[0] = to_real<Store, Real>(same[P.cell]);
+    static_for<kQ - 1>([&](auto qc) {
+      constexpr int q = decltype(qc)::value + 1;
+      constexpr Vel2 v = vel2(q);
+      constexpr bool half = (v.x & 1) != 0;
+      int xs, ys, zs;
+      [[maybe_unused]] bool inside = true;
+      const Store* base;
+      if constexpr (half) {
+        xs = v.x > 0 ? xhp : xhm;
+        ys = v.y > 0 ? yhp : yhm;
+        zs = v.z > 0 ? zhp : zhm;
+        if constexpr (kBC == 1) inside = v.x > 0 ? xinhp : xinhm;
+        base = other;
+      } else {
+        xs = xw[2 - v.x / 2];
+        ys = yw[2 - v.y / 2];
+        zs = zw[2 - v.z / 2];
+        if constexpr (kBC == 1) inside = xin[2 - v.x / 2];
+        base = same;
+      }
+      const int64_t cell = ((int64_t)zs * ny + ys) * nx + xs;
+      if constexpr (kBC == 1) {
+        if (!inside) {
+          h[q] = ghost[(v.x > 0 ? 0 : kGhostStride) + q];
+          return;
+        }
+      }
+      h[q] = to_real<Store, Real>(base[(int64_t)q * n3 + cell]);
+    });
+  }
+}
+
+}  // namespace rpk

@@ -3,6 +3,7 @@
 #pragma once
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 
 #include "rpk_internal.h"
@@ -65,27 +66,41 @@ static rpk_status collide_launch(rpk_lattice* L, const StepConst<Real>& K) {
 
 template <typename Real, int kBC>
 static rpk_status transport_launch(rpk_lattice* L, const StepConst<Real>& K) {
+  using TT = TransportTile<Real>;
+  // the dynamic shared memory limit is a per-device function attribute
+  static std::atomic<uint64_t> attr_set{0};
+  const size_t smem = TT::smem_bytes();
+  const uint64_t bit = 1ull << (L->device & 63);
+  if (!(attr_set.load() & bit)) {
+    RPK_CUDA(cudaFuncSetAttribute(k_transport_fused<Real, kBC>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    attr_set.fetch_or(bit);
+  }
+  const int nzb = (L->grid.nz + TT::TZ - 1) / TT::TZ;
+  const dim3 tgrid((unsigned)((L->grid.nx + TT::TX - 1) / TT::TX),
+                   (unsigned)((L->grid.ny + TT::TY - 1) / TT::TY), (unsigned)(2 * nzb));
   const dim3 grid = point_grid(L, 128);
   const Real* ucur = static_cast<const Real*>(L->u[L->steps & 1]);
   const Real* uprev = static_cast<const Real*>(L->u[(L->steps + 1) & 1]);
   const Real* gh = static_cast<const Real*>(L->ghost);
+  const Real* drho = static_cast<const Real*>(L->drho);
+  const Real* kap = static_cast<const Real*>(L->kap);
   Real* es = static_cast<Real*>(L->e_star);
   Real* ea = static_cast<Real*>(L->e_a);
   Real* eb = static_cast<Real*>(L->e_b);
+  Real* e = static_cast<Real*>(L->e);
+  // MacCormack + first FTCS sub-step; the remaining sub-steps end in e (state)
   RPK_CUDA(timing_begin(L));
-  k_mac_pred<Real, kBC><<<grid, 128, 0, L->stream>>>(K, es, ucur, uprev, ea, gh);
-  k_mac_corr<Real, kBC><<<grid, 128, 0, L->stream>>>(K, es, ea, ucur, uprev, eb, gh);
-  RPK_CUDA(timing_end(L, RPK_KC_ADVECT, 2));
-  // FTCS sub-steps: eb -> ... -> e (state)
-  RPK_CUDA(timing_begin(L));
-  Real* src = eb;
-  for (int k = 0; k < L->nsub; ++k) {
-    Real* dst = (k == L->nsub - 1) ? static_cast<Real*>(L->e) : (src == eb ? ea : eb);
-    k_ftcs<Real, kBC><<<grid, 128, 0, L->stream>>>(K, src, static_cast<const Real*>(L->drho),
-                                                    static_cast<const Real*>(L->kap), dst, gh);
+  Real* dst = L->nsub == 1 ? e : ea;
+  k_transport_fused<Real, kBC><<<tgrid, TT::kThreads, smem, L->stream>>>(K, es, ucur, uprev,
+                                                                          drho, kap, dst, gh);
+  Real* src = dst;
+  for (int k = 1; k < L->nsub; ++k) {
+    dst = (k == L->nsub - 1) ? e : (src == ea ? eb : ea);
+    k_ftcs<Real, kBC><<<grid, 128, 0, L->stream>>>(K, src, drho, kap, dst, gh);
     src = dst;
   }
-  RPK_CUDA(timing_end(L, RPK_KC_DIFFUSE, L->nsub));
+  RPK_CUDA(timing_end(L, RPK_KC_TRANSPORT, L->nsub));
   return check_launch("rotational transport");
 }
 
