@@ -185,6 +185,29 @@ enum { RPK_KC_COLLIDE = 0, RPK_KC_TRANSPORT = 1, RPK_KC_COUNT = 2 };
 rpk_status rpk_timing(rpk_lattice* lat, int enable);
 rpk_status rpk_timing_read(rpk_lattice* lat, double* ms, int64_t* launches);
 
+/* Conserved totals of hydrodynamic fields held by the caller in device memory,
+ * computed without allocating anything. The paper has no counterpart; this is
+ * for callers that cannot call cudaMalloc where they need the totals (a loop
+ * being recorded into a CUDA graph, where allocation is not allowed during
+ * stream capture, or an application whose memory manager owns all device
+ * memory). Inputs: rho, u (3 planes), theta_T, theta_R, npts values each, in
+ * the field layout above (e.g. written by rpk_read_moments with on_device = 1);
+ * delta as in rpk_relax. Output: out[0..4] in device memory =
+ *   sum rho, sum rho u_x, sum rho u_y, sum rho u_z,
+ *   sum (rho |u|^2/2 + 3 rho theta_T/2 + delta rho theta_R/2)   (E_T + E_R),
+ * which equal rpk_diagnostics' mass, mom and energy of the same state.
+ * Asynchronous on cuda_stream (NULL = legacy default stream); the device is
+ * the current one. The per-block partial sums live in a static 320 KiB device
+ * array that every GPU loading the library keeps until exit; npts is limited
+ * to 67,108,864 (8192 blocks of 8192 points), larger sizes return
+ * RPK_ERR_ARG. The first call on each device looks up that array's address;
+ * make that first call before any stream capture. All calls share the array,
+ * so calls whose kernels overlap on the GPU race: order them on one stream.
+ * No part of the array needs to start at zero. */
+rpk_status rpk_field_totals_noalloc(const double* rho, const double* u, const double* theta_T,
+                                    const double* theta_R, int64_t npts, double delta,
+                                    void* cuda_stream, double* out);
+
 #ifdef __cplusplus
 }
 #endif

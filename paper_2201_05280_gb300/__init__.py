@@ -17,7 +17,7 @@ import os
 import numpy as np
 
 __all__ = ["Lattice", "RpkError", "load_library", "theta0", "map_gas", "auto_nsub",
-           "gas_from_nondim", "PRECISIONS", "library_path"]
+           "gas_from_nondim", "field_totals_noalloc", "PRECISIONS", "library_path"]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB_PATH = os.path.join(_HERE, "librpk.so")
@@ -94,6 +94,7 @@ def load_library(path=None):
         "rpk_get_info": (i, [vp, ctypes.POINTER(i64)]),
         "rpk_timing": (i, [vp, i]),
         "rpk_timing_read": (i, [vp, ctypes.POINTER(d), ctypes.POINTER(i64)]),
+        "rpk_field_totals_noalloc": (i, [vp, vp, vp, vp, i64, d, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -133,6 +134,25 @@ def gas_from_nondim(gamma, nu, lam, Pr, rho0=1.0):
     delta = (5.0 - 3.0 * gamma) / (gamma - 1.0)
     eta = rho0 * nu
     return eta, lam * eta, eta * (5.0 + delta) / 2.0 / Pr
+
+
+def field_totals_noalloc(rho, u, T, R, delta, out, stream=None):
+    """Conserved totals (sum rho, sum rho u (3), E_T + E_R) of CUDA float64
+    tensors, written into the CUDA float64 tensor ``out`` (5 values) on
+    ``stream``; allocates nothing (rpk_field_totals_noalloc). For callers that
+    cannot allocate device memory at that point, e.g. while recording a CUDA
+    graph. Asynchronous: synchronise the stream before reading ``out``."""
+    n = rho.numel()
+    ptrs = []
+    for a, m in ((rho, n), (u, 3 * n), (T, n), (R, n), (out, 5)):
+        p, dev, _ = _arg(a, m)
+        if dev != 1:
+            raise ValueError("field_totals_noalloc takes CUDA tensors only")
+        ptrs.append(p)
+    _check(load_library().rpk_field_totals_noalloc(ptrs[0], ptrs[1], ptrs[2], ptrs[3], n,
+                                                   float(delta), _stream_handle(stream),
+                                                   ptrs[4]))
+    return out
 
 
 def _is_torch(a):

@@ -20,7 +20,8 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "-I" + INCLUDE, "--expt-relaxed-constexpr"]
-SOURCES = ["rpk_api.cu", "rpk_ops_f64.cu", "rpk_ops_f32.cu", "rpk_ops_f16.cu", "rpk_ops_bf16.cu"]
+SOURCES = ["rpk_api.cu", "rpk_ops_f64.cu", "rpk_ops_f32.cu", "rpk_ops_f16.cu", "rpk_ops_bf16.cu",
+           "rpk_noalloc.cu"]
 
 
 def nvcc():
