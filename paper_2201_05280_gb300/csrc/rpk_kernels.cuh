@@ -73,23 +73,25 @@ __global__ void __launch_bounds__(128)
 
 // ---------------------------------------------------------------------------
 // Fused rotational transport: MacCormack predictor, corrector and the first
-// FTCS sub-step in one pass. A block owns a TX x TY x TZ tile of one sublattice
-// and stages e*, the advecting velocity v, rho - 1 and kappa_R of the tile plus
-// a halo of two cells (periodic wrap, or reservoir values beyond the x ends) in
-// shared memory; the predictor is formed on the tile + [-2, +1], the corrector
-// on the tile + [-1, +1], then the diffusion flux on the tile. Same arithmetic
-// as the unfused scheme (forward-difference predictor, backward-difference
-// corrector, then one k_ftcs sub-step).
+// FTCS sub-step in one pass (same arithmetic as the unfused scheme:
+// forward-difference predictor, backward-difference corrector, one k_ftcs
+// sub-step). A block owns a TX x TY tile of x-y cells of one sublattice and
+// marches through ZC planes in z. Each iteration stages one new z plane of e*
+// and the advecting velocity v (tile + 2 halo) in a ring of three planes, forms
+// the predictor on the plane below it, the corrector (with theta_R and
+// kappa_R) on the plane below that, and the diffusion update of the plane two
+// below the newest one. Halo cells beyond the x ends hold reservoir values.
 template <typename Real>
 struct TransportTile {
-  static constexpr int TX = 32, TY = 4, TZ = sizeof(Real) == 8 ? 2 : 4;
-  static constexpr int RX = TX + 4, RY = TY + 4, RZ = TZ + 4;  // e, v: offset -2
-  static constexpr int PX = TX + 3, PY = TY + 3, PZ = TZ + 3;  // predictor: offset -2
-  static constexpr int CX = TX + 2, CY = TY + 2, CZ = TZ + 2;  // corrector, rho, kappa: offset -1
-  static constexpr int kThreads = TX * TY * TZ;
-  static constexpr size_t smem_bytes() {
-    return sizeof(Real) * (4 * RX * RY * RZ + PX * PY * PZ + 3 * CX * CY * CZ);
-  }
+  static constexpr int TX = 32, TY = 8, ZC = 16;
+  static constexpr int EX = TX + 4, EY = TY + 4;  // e*, v planes: offsets -2 .. T+1
+  static constexpr int PX = TX + 3, PY = TY + 3;  // predictor: offsets -2 .. T
+  static constexpr int CX = TX + 2, CY = TY + 2;  // corrector, theta_R, kappa_R: -1 .. T
+  static constexpr int EP = EX * EY, PP = PX * PY, CP = CX * CY;
+  static constexpr int kThreads = TX * TY;
+  // E[3] V[3][3] P[2] C[2] TH[3] K[3] planes, then x/y wrap tables (ints)
+  static constexpr size_t kReals = 3 * EP + 9 * EP + 2 * PP + 2 * CP + 3 * CP + 3 * CP;
+  static constexpr size_t smem_bytes() { return sizeof(Real) * kReals + sizeof(int) * (EX + EY); }
 };
 
 __device__ __forceinline__ int wrap_any(int a, int n) {
@@ -105,119 +107,150 @@ __global__ void __launch_bounds__(TransportTile<Real>::kThreads)
                       Real* __restrict__ e_out, const Real* __restrict__ ghost) {
   using T = TransportTile<Real>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  Real* se = reinterpret_cast<Real*>(smem_raw);
-  Real* sv = se + T::RX * T::RY * T::RZ;        // 3 planes of v
-  Real* sp = sv + 3 * T::RX * T::RY * T::RZ;    // predictor
-  Real* sc = sp + T::PX * T::PY * T::PZ;        // corrector
-  Real* sd = sc + T::CX * T::CY * T::CZ;        // rho - 1
-  Real* sk = sd + T::CX * T::CY * T::CZ;        // kappa_R
-  const int nzb = (K.nz + T::TZ - 1) / T::TZ;
+  Real* sE = reinterpret_cast<Real*>(smem_raw);  // [3][EP]
+  Real* sV = sE + 3 * T::EP;                     // [3 slots][3 comps][EP]
+  Real* sP = sV + 9 * T::EP;                     // [2][PP]
+  Real* sC = sP + 2 * T::PP;                     // [2][CP]
+  Real* sTH = sC + 2 * T::CP;                    // [3][CP]
+  Real* sK = sTH + 3 * T::CP;                    // [3][CP]
+  int* xw = reinterpret_cast<int*>(sK + 3 * T::CP);  // [EX] wrapped x (or -1/-2 ghost)
+  int* yw = xw + T::EX;                               // [EY] wrapped y
+  const int nzb = (K.nz + T::ZC - 1) / T::ZC;
   const int s = blockIdx.z / nzb;
-  const int x0 = blockIdx.x * T::TX, y0 = blockIdx.y * T::TY, z0 = (blockIdx.z - s * nzb) * T::TZ;
+  const int x0 = blockIdx.x * T::TX, y0 = blockIdx.y * T::TY, z0 = (blockIdx.z - s * nzb) * T::ZC;
   const int64_t npts = 2 * K.n3;
   const int64_t sbase = (int64_t)s * K.n3;
   const int tid = threadIdx.x;
-  constexpr int RV = T::RX * T::RY * T::RZ;
+  const Real t0d = K.delta * K.theta0;
+  for (int i = tid; i < T::EX; i += T::kThreads) {
+    const int gx = x0 + i - 2;
+    xw[i] = (kBC == 1 && gx < 0) ? -1 : (kBC == 1 && gx >= K.nx) ? -2 : wrap_any(gx, K.nx);
+  }
+  for (int i = tid; i < T::EY; i += T::kThreads) yw[i] = wrap_any(y0 + i - 2, K.ny);
   const Real* gl = ghost;
   const Real* gh = ghost + kGhostStride;
-  // stage e*, v on the tile + 2; rho - 1, kappa on the tile + 1
-  for (int i = tid; i < RV; i += T::kThreads) {
-    const int rx = i % T::RX, ry = (i / T::RX) % T::RY, rz = i / (T::RX * T::RY);
-    const int gx = x0 + rx - 2;
-    const int gy = wrap_any(y0 + ry - 2, K.ny), gz = wrap_any(z0 + rz - 2, K.nz);
-    const bool in_c = rx >= 1 && rx <= T::TX + 2 && ry >= 1 && ry <= T::TY + 2 && rz >= 1 &&
-                      rz <= T::TZ + 2;
-    const int ci = ((rz - 1) * T::CY + (ry - 1)) * T::CX + (rx - 1);
-    if (kBC == 1 && (gx < 0 || gx >= K.nx)) {
-      const Real* g = gx < 0 ? gl : gh;
-      se[i] = g[kGhE];
-      sv[i] = g[kGhU];
-      sv[RV + i] = g[kGhU + 1];
-      sv[2 * RV + i] = g[kGhU + 2];
-      if (in_c) {
-        sd[ci] = g[kGhDrho];
-        sk[ci] = g[kGhKap];
+  auto ghost_of = [&](int xwv) { return xwv == -1 ? gl : gh; };
+  auto is_ghost = [&](int xwv) { return kBC == 1 && xwv < 0; };
+
+  for (int k = 0; k < T::ZC + 4; ++k) {
+    const int zn = z0 - 2 + k;         // plane staged in this iteration
+    const int zw = wrap_any(zn, K.nz);
+    const int se = k % 3;              // ring slot of plane zn
+    __syncthreads();                   // previous readers of the slots are done
+    // 1. stage e* and v of plane zn
+    for (int i = tid; i < T::EP; i += T::kThreads) {
+      const int rx = i % T::EX, ry = i / T::EX;
+      const int xv = xw[rx];
+      Real e, v0, v1, v2;
+      if (is_ghost(xv)) {
+        const Real* g = ghost_of(xv);
+        e = g[kGhE]; v0 = g[kGhU]; v1 = g[kGhU + 1]; v2 = g[kGhU + 2];
+      } else {
+        const int64_t q = sbase + ((int64_t)zw * K.ny + yw[ry]) * K.nx + xv;
+        e = es[q];
+        v0 = vadv(ucur, uprev, q);
+        v1 = vadv(ucur, uprev, npts + q);
+        v2 = vadv(ucur, uprev, 2 * npts + q);
       }
-    } else {
-      const int64_t q = sbase + ((int64_t)gz * K.ny + gy) * K.nx + wrap_any(gx, K.nx);
-      se[i] = es[q];
-      sv[i] = vadv(ucur, uprev, q);
-      sv[RV + i] = vadv(ucur, uprev, npts + q);
-      sv[2 * RV + i] = vadv(ucur, uprev, 2 * npts + q);
-      if (in_c) {
-        sd[ci] = drho[q];
-        sk[ci] = kap[q];
+      sE[se * T::EP + i] = e;
+      sV[(se * 3 + 0) * T::EP + i] = v0;
+      sV[(se * 3 + 1) * T::EP + i] = v1;
+      sV[(se * 3 + 2) * T::EP + i] = v2;
+    }
+    __syncthreads();
+    // 2. predictor on plane zn - 1 (forward differences; z neighbour is plane zn)
+    if (k >= 1) {
+      const int sb = (k + 2) % 3;        // slot of plane zn - 1
+      const int sp = (k - 1) & 1;        // predictor slot of plane zn - 1
+      for (int i = tid; i < T::PP; i += T::kThreads) {
+        const int px = i % T::PX, py = i / T::PX;
+        const int r = py * T::EX + px;   // same offsets (-2) in the e plane
+        Real val;
+        if (is_ghost(xw[px])) {
+          val = sE[sb * T::EP + r];
+        } else {
+          const Real e0 = sE[sb * T::EP + r];
+          const int rn[3] = {sb * T::EP + r + 1, sb * T::EP + r + T::EX, se * T::EP + r};
+          const int sn[3] = {sb, sb, se};
+          Real div = Real(0);
+#pragma unroll
+          for (int a = 0; a < 3; ++a) {
+            const Real vp = sV[(sb * 3 + a) * T::EP + r];
+            const Real vq = sV[(sn[a] * 3 + a) * T::EP + (rn[a] - sn[a] * T::EP)];
+            const Real eq = sE[rn[a]];
+            div += K.E0 * (vq - vp) + (eq * vq - e0 * vp);
+          }
+          val = e0 - K.dt * div;
+        }
+        sP[sp * T::PP + i] = val;
       }
     }
-  }
-  __syncthreads();
-  auto ridx = [](int rx, int ry, int rz) { return (rz * T::RY + ry) * T::RX + rx; };
-  // predictor on offsets [-2, TX] (forward differences)
-  for (int i = tid; i < T::PX * T::PY * T::PZ; i += T::kThreads) {
-    const int px = i % T::PX, py = (i / T::PX) % T::PY, pz = i / (T::PX * T::PY);
-    const int r = ridx(px, py, pz);
-    const int gx = x0 + px - 2;
-    Real val;
-    if (kBC == 1 && (gx < 0 || gx >= K.nx)) {
-      val = se[r];  // reservoir: predictor equals the reservoir value
-    } else {
-      const Real e0 = se[r];
-      Real div = Real(0);
-      const int nb[3] = {ridx(px + 1, py, pz), ridx(px, py + 1, pz), ridx(px, py, pz + 1)};
+    __syncthreads();
+    // 3. corrector on plane zn - 1 (backward differences; z neighbour is plane
+    //    zn - 2), then theta_R deviation and kappa_R of that plane
+    if (k >= 2) {
+      const int sb = (k + 2) % 3;        // e/v slot of plane zn - 1
+      const int sm = (k + 1) % 3;        // e/v slot of plane zn - 2
+      const int pc = (k - 1) & 1;        // predictor of plane zn - 1
+      const int pm = k & 1;              // predictor of plane zn - 2
+      const int ct = (k - 1) & 1;        // corrector slot of plane zn - 1
+      const int zc = wrap_any(zn - 1, K.nz);
+      for (int i = tid; i < T::CP; i += T::kThreads) {
+        const int cx = i % T::CX, cy = i / T::CX;
+        const int r = (cy + 1) * T::EX + (cx + 1);  // e-plane index of this cell
+        const int pi = (cy + 1) * T::PX + (cx + 1);  // predictor index of this cell
+        const int xv = xw[cx + 1];
+        Real val, dr, kp;
+        if (is_ghost(xv)) {
+          const Real* g = ghost_of(xv);
+          val = sE[sb * T::EP + r];
+          dr = g[kGhDrho];
+          kp = g[kGhKap];
+        } else {
+          const Real epp = sP[pc * T::PP + pi];
+          const Real pnb[3] = {sP[pc * T::PP + pi - 1], sP[pc * T::PP + pi - T::PX], sP[pm * T::PP + pi]};
+          const int vs[3] = {sb, sb, sm};
+          const int vr[3] = {r - 1, r - T::EX, r};
+          Real div = Real(0);
 #pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        const Real vp = sv[a * RV + r], vq = sv[a * RV + nb[a]], eq = se[nb[a]];
-        div += K.E0 * (vq - vp) + (eq * vq - e0 * vp);
+          for (int a = 0; a < 3; ++a) {
+            const Real vp = sV[(sb * 3 + a) * T::EP + r];
+            const Real vq = sV[(vs[a] * 3 + a) * T::EP + vr[a]];
+            div += K.E0 * (vp - vq) + (epp * vp - pnb[a] * vq);
+          }
+          val = Real(0.5) * (sE[sb * T::EP + r] + epp - K.dt * div);
+          const int64_t q = sbase + ((int64_t)zc * K.ny + yw[cy + 1]) * K.nx + xv;
+          dr = drho[q];
+          kp = kap[q];
+        }
+        sC[ct * T::CP + i] = val;
+        sTH[sb * T::CP + i] = (Real(2) * val - t0d * dr) / (K.delta * (Real(1) + dr));
+        sK[sb * T::CP + i] = kp;
       }
-      val = e0 - K.dt * div;
     }
-    sp[i] = val;
-  }
-  __syncthreads();
-  auto pidx = [](int px, int py, int pz) { return (pz * T::PY + py) * T::PX + px; };
-  // corrector on offsets [-1, TX] (backward differences)
-  for (int i = tid; i < T::CX * T::CY * T::CZ; i += T::kThreads) {
-    const int cx = i % T::CX, cy = (i / T::CX) % T::CY, cz = i / (T::CX * T::CY);
-    const int r = ridx(cx + 1, cy + 1, cz + 1);
-    const int pc = pidx(cx + 1, cy + 1, cz + 1);
-    const int gx = x0 + cx - 1;
-    Real val;
-    if (kBC == 1 && (gx < 0 || gx >= K.nx)) {
-      val = se[r];
-    } else {
-      const Real epp = sp[pc];
-      Real div = Real(0);
-      const int pb[3] = {pidx(cx, cy + 1, cz + 1), pidx(cx + 1, cy, cz + 1), pidx(cx + 1, cy + 1, cz)};
-      const int rb[3] = {ridx(cx, cy + 1, cz + 1), ridx(cx + 1, cy, cz + 1), ridx(cx + 1, cy + 1, cz)};
+    __syncthreads();
+    // 4. first FTCS sub-step on plane zn - 2
+    if (k >= 4) {
+      const int zo = zn - 2;
+      const int s0 = (k + 1) % 3;        // theta/kappa slot of plane zn - 2
+      const int sl = k % 3;              // plane zn - 3
+      const int su = (k + 2) % 3;        // plane zn - 1
+      const int co = k & 1;              // corrector of plane zn - 2
+      const int tx = tid % T::TX, ty = tid / T::TX;
+      const int x = x0 + tx, y = y0 + ty;
+      if (x < K.nx && y < K.ny && zo < K.nz) {
+        const int c = (ty + 1) * T::CX + (tx + 1);
+        const Real th = sTH[s0 * T::CP + c];
+        const Real kc = sK[s0 * T::CP + c];
+        // order -x, +x, -y, +y, -z, +z as in k_ftcs
+        const int ns[6] = {s0, s0, s0, s0, sl, su};
+        const int nc[6] = {c - 1, c + 1, c - T::CX, c + T::CX, c, c};
+        Real acc = Real(0);
 #pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        const Real vp = sv[a * RV + r], vq = sv[a * RV + rb[a]], eq = sp[pb[a]];
-        div += K.E0 * (vp - vq) + (epp * vp - eq * vq);
+        for (int m = 0; m < 6; ++m)
+          acc += Real(0.5) * (kc + sK[ns[m] * T::CP + nc[m]]) * (sTH[ns[m] * T::CP + nc[m]] - th);
+        e_out[sbase + ((int64_t)zo * K.ny + y) * K.nx + x] = sC[co * T::CP + c] + K.hsub * acc;
       }
-      val = Real(0.5) * (se[r] + epp - K.dt * div);
-    }
-    sc[i] = val;
-  }
-  __syncthreads();
-  // first FTCS sub-step on the tile
-  {
-    const int tx = tid % T::TX, ty = (tid / T::TX) % T::TY, tz = tid / (T::TX * T::TY);
-    const int x = x0 + tx, y = y0 + ty, z = z0 + tz;
-    if (x < K.nx && y < K.ny && z < K.nz) {
-      const Real t0d = K.delta * K.theta0;
-      auto cidx = [](int cx, int cy, int cz) { return (cz * T::CY + cy) * T::CX + cx; };
-      auto dthR = [&](int c) { return (Real(2) * sc[c] - t0d * sd[c]) / (K.delta * (Real(1) + sd[c])); };
-      const int c0 = cidx(tx + 1, ty + 1, tz + 1);
-      const Real th = dthR(c0);
-      const Real kp = sk[c0];
-      // same order as k_ftcs: -x, +x, -y, +y, -z, +z
-      const int nbs[6] = {cidx(tx, ty + 1, tz + 1), cidx(tx + 2, ty + 1, tz + 1),
-                          cidx(tx + 1, ty, tz + 1), cidx(tx + 1, ty + 2, tz + 1),
-                          cidx(tx + 1, ty + 1, tz), cidx(tx + 1, ty + 1, tz + 2)};
-      Real acc = Real(0);
-#pragma unroll
-      for (int k = 0; k < 6; ++k) acc += Real(0.5) * (kp + sk[nbs[k]]) * (dthR(nbs[k]) - th);
-      e_out[sbase + ((int64_t)z * K.ny + y) * K.nx + x] = sc[c0] + K.hsub * acc;
     }
   }
 }

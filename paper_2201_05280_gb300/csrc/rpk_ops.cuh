@@ -76,7 +76,7 @@ static rpk_status transport_launch(rpk_lattice* L, const StepConst<Real>& K) {
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     attr_set.fetch_or(bit);
   }
-  const int nzb = (L->grid.nz + TT::TZ - 1) / TT::TZ;
+  const int nzb = (L->grid.nz + TT::ZC - 1) / TT::ZC;
   const dim3 tgrid((unsigned)((L->grid.nx + TT::TX - 1) / TT::TX),
                    (unsigned)((L->grid.ny + TT::TY - 1) / TT::TY), (unsigned)(2 * nzb));
   const dim3 grid = point_grid(L, 128);

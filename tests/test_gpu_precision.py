@@ -1,0 +1,107 @@
+"""Reduced-storage paths against the FP64 oracle (row a10: populations stored
+as h = g/w - 1 in FP16 or BF16, arithmetic in FP32).
+
+Stated bounds (relative L-inf against the oracle, after the step counts
+below; u measured on the scale of the flow):
+  FP32     1e-5 on rho, u, theta_T, E_rot
+  FP16dev  see BOUNDS: rounding of h to an 11-bit significand each step
+  BF16dev  see BOUNDS: 8-bit significand, about 8x coarser than FP16
+The 16-bit bounds are a small multiple of the errors measured on GB300 for
+these inputs; each step rounds every stored h once (unit roundoff 2^-11 for
+FP16, 2^-8 for BF16), and the collision damps the non-hydrodynamic part of
+that noise, so the error grows far slower than linearly in the step count.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+import paper_2201_05280_gb300 as rpk
+import rpk_inputs as I
+
+pytestmark = pytest.mark.gpu
+
+T0 = 0.2948964908710633
+KEYS = ("rho", "u", "T", "Erot")
+
+# per storage: bound on rel L-inf for rho, u, T, Erot
+BOUNDS = {"f32": (1e-5, 1e-5, 1e-5, 1e-5),
+          "f16dev": (1e-3, 3e-2, 1e-3, 1e-3),
+          "bf16dev": (1e-2, 3e-1, 1e-2, 1e-2)}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    from paper_2201_05280_gb300 import build as B
+    B.build()
+    import torch
+    assert torch.cuda.is_available()
+    torch.cuda.set_device(0)
+
+
+def _rel(a, b):
+    return float(np.abs(a - b).max() / np.abs(b).max())
+
+
+@pytest.fixture(scope="module")
+def wave_reference():
+    nx, ny, nz, nsteps = 48, 48, 2, 1000
+    f, _ = I.fourier_modes(nx, ny, nz, T0, amp=1e-3, nmax=1)
+    eta, etaB, kap = rpk.gas_from_nondim(1.4, 0.02, 0.6, 0.71)
+    r = rpk.map_gas(1.4, eta, etaB, kap, 0.0)
+    relax = {k: r[k] for k in ("delta", "tau", "tau1", "b", "k_r")}
+    lat = rpk.Lattice(nx, ny, nz, precision="f64").set_relax(**relax)
+    lat.init_fields(f["rho"], f["u"], f["T"], f["R"])
+    nsub = lat.info()["nsub"]
+    lat.close()
+    P = O.make_params(relax["delta"], relax["tau"], relax["tau1"], relax["b"], relax["k_r"],
+                      1.0, nsub, 0)
+    S = O.State(P, nx, ny, nz).init_fields(f["rho"], f["u"], f["T"], f["R"]).step(nsteps)
+    return (nx, ny, nz, nsteps, f, relax, S.fields())
+
+
+@pytest.mark.parametrize("prec", ["f32", "f16dev", "bf16dev"])
+def test_storage_precision_wave_field_1000_steps(prec, wave_reference):
+    nx, ny, nz, nsteps, f, relax, ref = wave_reference
+    lat = rpk.Lattice(nx, ny, nz, precision=prec).set_relax(**relax)
+    lat.init_fields(f["rho"], f["u"], f["T"], f["R"]).step(nsteps)
+    got = lat.read_moments()
+    d = lat.diagnostics()
+    errs = {k: _rel(got[k], ref[k]) for k in KEYS}
+    print("storage %s errors after %d steps: %s" % (prec, nsteps, errs))
+    assert d["status"] == 0
+    for k, bound in zip(KEYS, BOUNDS[prec]):
+        assert errs[k] <= bound, (prec, k, errs[k], bound)
+
+
+@pytest.fixture(scope="module")
+def tgv_reference():
+    """3-D Taylor-Green vortex, u0 = 0.3 c_s on a 32^3 box, Re = 100, 200
+    steps: larger deviations h than the wave field."""
+    n, nsteps = 32, 200
+    cs = np.sqrt(1.4 * T0)
+    u0 = 0.3 * cs
+    nu = u0 * (n / (2 * np.pi)) / 100.0
+    eta, etaB, kap = rpk.gas_from_nondim(1.4, nu, 0.6, 0.71)
+    r = rpk.map_gas(1.4, eta, etaB, kap, 0.0)
+    relax = {k: r[k] for k in ("delta", "tau", "tau1", "b", "k_r")}
+    f = I.taylor_green(n, T0, u0)
+    lat = rpk.Lattice(n, n, n, precision="f64").set_relax(**relax)
+    lat.init_fields(f["rho"], f["u"], f["T"], f["R"])
+    nsub = lat.info()["nsub"]
+    lat.close()
+    P = O.make_params(relax["delta"], relax["tau"], relax["tau1"], relax["b"], relax["k_r"],
+                      1.0, nsub, 0)
+    S = O.State(P, n, n, n).init_fields(f["rho"], f["u"], f["T"], f["R"]).step(nsteps)
+    return n, nsteps, f, relax, S.fields()
+
+
+@pytest.mark.parametrize("prec", ["f32", "f16dev", "bf16dev"])
+def test_storage_precision_taylor_green(prec, tgv_reference):
+    n, nsteps, f, relax, ref = tgv_reference
+    lat = rpk.Lattice(n, n, n, precision=prec).set_relax(**relax)
+    lat.init_fields(f["rho"], f["u"], f["T"], f["R"]).step(nsteps)
+    got = lat.read_moments()
+    errs = {k: _rel(got[k], ref[k]) for k in KEYS}
+    print("TGV storage %s errors after %d steps: %s" % (prec, nsteps, errs))
+    for k, bound in zip(KEYS, BOUNDS[prec]):
+        assert errs[k] <= bound, (prec, k, errs[k], bound)
