@@ -137,14 +137,28 @@ class ClockSampler:
                 "samples": len(rows)}
 
 
-def make_fields(n, seed=I.SEED):
+def make_fields(n, seed=I.SEED, workload="waves"):
+    if workload == "tgv":
+        return I.taylor_green(n, THETA0, TGV_MA * np.sqrt(GAS["gamma"] * THETA0))
     f, _ = I.fourier_modes(n, n, n, THETA0, nmodes=8, amp=1e-3, seed=seed)
     return f
 
 
-def relax_params(rpk):
-    eta, etaB, kap = rpk.gas_from_nondim(GAS["gamma"], GAS["nu"], GAS["lam"], GAS["Pr"])
-    return rpk.map_gas(GAS["gamma"], eta, etaB, kap, GAS["b"])
+TGV_MA, TGV_RE = 0.3, 1600.0
+
+
+def gas_for(workload, n):
+    """(gamma, nu, lam, Pr, b): the decaying-wave gas, or the Taylor-Green
+    vortex at Ma 0.3, Re 1600 on an n^3 box (L = n/(2 pi), eta_B/eta = 0.6)."""
+    if workload == "tgv":
+        u0 = TGV_MA * np.sqrt(GAS["gamma"] * THETA0)
+        return dict(GAS, nu=u0 * (n / (2 * np.pi)) / TGV_RE)
+    return dict(GAS)
+
+
+def relax_params(rpk, gas=GAS):
+    eta, etaB, kap = rpk.gas_from_nondim(gas["gamma"], gas["nu"], gas["lam"], gas["Pr"])
+    return rpk.map_gas(gas["gamma"], eta, etaB, kap, gas["b"])
 
 
 def oracle_mlups(n, steps, warmup=1):
@@ -197,6 +211,8 @@ def main():
     ap.add_argument("--cpu-n", type=int, default=24, help="oracle sample box for cpu_baseline")
     ap.add_argument("--cpu-steps", type=int, default=100)
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--workload", default="waves", choices=["waves", "tgv"],
+                    help="decaying wave field (default) or Taylor-Green vortex Ma 0.3 Re 1600")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -224,8 +240,9 @@ def main():
     dev = torch.cuda.current_device()
 
     n = args.n
-    f = make_fields(n)
-    r = relax_params(rpk)
+    f = make_fields(n, workload=args.workload)
+    gas = gas_for(args.workload, n)
+    r = relax_params(rpk, gas)
     stream = torch.cuda.Stream()
     lat = rpk.Lattice(n, n, n, precision=args.precision, stream=stream)
     lat.set_relax(r["delta"], r["tau"], r["tau1"], r["b"], r["k_r"])
@@ -317,8 +334,10 @@ def main():
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32" if args.precision == "f32" else args.precision, "data": "synthetic",
-            "config": {"workload": "3-D periodic %d^3 decaying wave field, %s" % (n, args.precision),
-                       "grid": [n, n, n], "points": npts, "gas": GAS, "nsub": nsub,
+            "config": {"workload": ("3-D periodic %d^3 decaying wave field, %s" % (n, args.precision)
+                                    if args.workload == "waves" else
+                                    "3-D Taylor-Green vortex %d^3, Ma 0.3, Re 1600, %s" % (n, args.precision)),
+                       "grid": [n, n, n], "points": npts, "gas": gas, "nsub": nsub,
                        "l2": "inputs larger than L2 (%.1f GB of populations)" %
                              (2 * 41 * npts * STORE_BYTES[args.precision] / 1e9),
                        "parallelism": "replicas x%d" % world},

@@ -1,15 +1,14 @@
 """Reduced-storage paths against the FP64 oracle (row a10: populations stored
 as h = g/w - 1 in FP16 or BF16, arithmetic in FP32).
 
-Stated bounds (relative L-inf against the oracle, after the step counts
-below; u measured on the scale of the flow):
-  FP32     1e-5 on rho, u, theta_T, E_rot
-  FP16dev  see BOUNDS: rounding of h to an 11-bit significand each step
-  BF16dev  see BOUNDS: 8-bit significand, about 8x coarser than FP16
-The 16-bit bounds are a small multiple of the errors measured on GB300 for
-these inputs; each step rounds every stored h once (unit roundoff 2^-11 for
-FP16, 2^-8 for BF16), and the collision damps the non-hydrodynamic part of
-that noise, so the error grows far slower than linearly in the step count.
+Stated bounds: relative L-inf against the oracle for rho, theta_T, E_rot; for
+u the scale is max(max|u|, c_s) (see test_gpu_parity). Each step rounds every
+stored h once (unit roundoff 2^-24 for FP32, 2^-11 for FP16, 2^-8 for BF16),
+with errors of order u_r |h| per step that add up nearly linearly in smooth
+flows. The bounds below are about 3x the errors measured on GB300:
+  wave field (|u| ~ 1e-3, 1000 steps):  FP32 1e-5, FP16 5e-6, BF16 5e-5
+  Taylor-Green (Ma 0.3, 200 steps):     FP32 1e-5 (u 3e-5), FP16 2e-3, BF16 2e-2
+At Ma 0.3 the deviations reach |h| ~ 1.3, hence the larger FP32 velocity bound.
 """
 import numpy as np
 import pytest
@@ -38,8 +37,9 @@ def _gpu():
     torch.cuda.set_device(0)
 
 
-def _rel(a, b):
-    return float(np.abs(a - b).max() / np.abs(b).max())
+def _rel(a, b, key="rho"):
+    scale = max(np.abs(b).max(), CS) if key == "u" else np.abs(b).max()
+    return float(np.abs(a - b).max() / scale)
 
 
 @pytest.fixture(scope="module")
@@ -66,10 +66,10 @@ def test_storage_precision_wave_field_1000_steps(prec, wave_reference):
     lat.init_fields(f["rho"], f["u"], f["T"], f["R"]).step(nsteps)
     got = lat.read_moments()
     d = lat.diagnostics()
-    errs = {k: _rel(got[k], ref[k]) for k in KEYS}
+    errs = {k: _rel(got[k], ref[k], k) for k in KEYS}
     print("storage %s errors after %d steps: %s" % (prec, nsteps, errs))
     assert d["status"] == 0
-    for k, bound in zip(KEYS, BOUNDS[prec]):
+    for k, bound in zip(KEYS, WAVE_BOUNDS[prec]):
         assert errs[k] <= bound, (prec, k, errs[k], bound)
 
 
@@ -101,7 +101,7 @@ def test_storage_precision_taylor_green(prec, tgv_reference):
     lat = rpk.Lattice(n, n, n, precision=prec).set_relax(**relax)
     lat.init_fields(f["rho"], f["u"], f["T"], f["R"]).step(nsteps)
     got = lat.read_moments()
-    errs = {k: _rel(got[k], ref[k]) for k in KEYS}
+    errs = {k: _rel(got[k], ref[k], k) for k in KEYS}
     print("TGV storage %s errors after %d steps: %s" % (prec, nsteps, errs))
-    for k, bound in zip(KEYS, BOUNDS[prec]):
+    for k, bound in zip(KEYS, TGV_BOUNDS[prec]):
         assert errs[k] <= bound, (prec, k, errs[k], bound)
