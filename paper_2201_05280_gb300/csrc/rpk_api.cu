@@ -145,8 +145,9 @@ static void free_all(rpk_lattice* L) {
   if (!L) return;
   for (cudaEvent_t ev : L->events) cudaEventDestroy(ev);
   L->events.clear();
-  void* ptrs[] = {L->pop[0], L->pop[1], L->e, L->e_star, L->e_a, L->e_b, L->drho, L->kap,
-                  L->u[0], L->u[1], L->ghost, L->status, L->diag_partial, L->diag_out, L->stage};
+  void* ptrs[] = {L->pop[0], L->pop[1], L->e,       L->e_star, L->e_a,    L->e_b,
+                  L->vbuf,   L->thbuf,  L->drho,    L->kap,    L->u[0],   L->u[1],
+                  L->ghost,  L->status, L->diag_partial, L->diag_out, L->stage};
   int prev = -1;
   cudaGetDevice(&prev);
   if (prev != L->device) cudaSetDevice(L->device);
@@ -185,7 +186,8 @@ rpk_status rpk_create(const rpk_grid* grid, void* cuda_stream, rpk_lattice** out
   const size_t popb = (size_t)kQ * L->npts * L->store_elem;
   const size_t fb = (size_t)L->npts * L->real_elem;
   Req reqs[] = {{&L->pop[0], popb}, {&L->pop[1], popb}, {&L->e, fb}, {&L->e_star, fb},
-                {&L->e_a, fb}, {&L->e_b, fb}, {&L->drho, fb}, {&L->kap, fb},
+                {&L->e_a, fb}, {&L->e_b, fb}, {&L->vbuf, 3 * fb}, {&L->thbuf, fb},
+                {&L->drho, fb}, {&L->kap, fb},
                 {&L->u[0], 3 * fb}, {&L->u[1], 3 * fb},
                 {&L->ghost, 2 * kGhostStride * L->real_elem},
                 {(void**)&L->status, sizeof(unsigned)},

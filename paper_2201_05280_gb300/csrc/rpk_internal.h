@@ -30,6 +30,8 @@ struct rpk_lattice {
   void* e_star = nullptr; // after the exchange
   void* e_a = nullptr;    // transport scratch
   void* e_b = nullptr;    // transport scratch
+  void* vbuf = nullptr;   // advecting velocity of the step (3 planes)
+  void* thbuf = nullptr;  // theta_R - theta0 after advection
   void* drho = nullptr;
   void* kap = nullptr;
   void* u[2] = {nullptr, nullptr};  // ring: u(t) and u(t-1), 3 planes each

@@ -72,229 +72,107 @@ __global__ void __launch_bounds__(128)
 }
 
 // ---------------------------------------------------------------------------
-// Fused rotational transport: MacCormack predictor, corrector and the first
-// FTCS sub-step in one pass (same arithmetic as the unfused scheme:
-// forward-difference predictor, backward-difference corrector, one k_ftcs
-// sub-step). A block owns a TX x TY tile of x-y cells of one sublattice and
-// marches through ZC planes in z. Iteration k stages plane zn = z0 - 2 + k
-// (e*, advecting velocity v, rho - 1, kappa_R; tile + halo) into rings of
-// shared-memory planes, forms the predictor on plane zn - 1, the corrector
-// (with theta_R) on plane zn - 1 and the diffusion update of plane zn - 2. The
-// global loads of plane zn + 1 are issued into registers before the compute
-// phases of iteration k, so their latency overlaps the arithmetic. Halo cells
-// beyond the x ends hold reservoir values.
-template <typename Real>
-struct TransportTile {
-  static constexpr int TX = 32, TY = 8, ZC = 32;
-  static constexpr int EX = TX + 4, EY = TY + 4;  // e*, v planes: offsets -2 .. T+1
-  static constexpr int PX = TX + 3, PY = TY + 3;  // predictor: offsets -2 .. T
-  static constexpr int CX = TX + 2, CY = TY + 2;  // corrector, theta_R, rho, kappa: -1 .. T
-  static constexpr int EP = EX * EY, PP = PX * PY, CP = CX * CY;
-  static constexpr int kThreads = TX * TY;
-  static constexpr int kEPer = (EP + kThreads - 1) / kThreads;  // staged e/v cells per thread
-  static constexpr int kCPer = (CP + kThreads - 1) / kThreads;  // staged rho/kappa cells per thread
-  // E[3] V[3][3] P[2] C[2] TH[3] D[4] K[4] planes, then x/y wrap tables (ints)
-  static constexpr size_t kReals = 3 * EP + 9 * EP + 2 * PP + 2 * CP + 3 * CP + 4 * CP + 4 * CP;
-  static constexpr size_t smem_bytes() { return sizeof(Real) * kReals + sizeof(int) * (EX + EY); }
-};
-
-__device__ __forceinline__ int wrap_any(int a, int n) {
-  a %= n;
-  return a < 0 ? a + n : a;
+// Rotational transport in three bandwidth-bound passes over the grid:
+//   k_mac_pred   MacCormack predictor (forward differences) in flux form
+//                F = Er v, with the advecting velocity v = (3 u(t) - u(t-1))/2;
+//                also stores v for the corrector
+//   k_mac_corr   corrector (backward differences): Er' = (Er + Er_p - dt div F_p)/2;
+//                also stores theta_R - theta0 of the result for the diffusion
+//   k_ftcs_first first FTCS sub-step of dEr/dt = div(kappa_R grad theta_R) from the
+//                stored theta_R (no division per neighbour)
+// Further sub-steps use k_ftcs. Reservoir values stand beyond the x ends.
+template <typename Real, int kBC>
+__global__ void __launch_bounds__(128)
+    k_mac_pred(StepConst<Real> K, const Real* __restrict__ e, const Real* __restrict__ ucur,
+               const Real* __restrict__ uprev, Real* __restrict__ ep, Real* __restrict__ v,
+               const Real* __restrict__ ghost) {
+  PointIdx P;
+  if (!point_from_block(K, P)) return;
+  const int64_t npts = 2 * K.n3;
+  const int64_t p = (int64_t)P.s * K.n3 + P.cell;
+  const Real ep0 = e[p];
+  Real div = Real(0);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const Real vp = vadv(ucur, uprev, a * npts + p);
+    v[a * npts + p] = vp;
+    const int64_t q = axis_nb<kBC>(K, P, a, +1);
+    Real eq, vq;
+    if (kBC == 1 && q < 0) {
+      const Real* g = ghost + (q == -1 ? 0 : kGhostStride);
+      eq = g[kGhE];
+      vq = g[kGhU + a];
+    } else {
+      eq = e[q];
+      vq = vadv(ucur, uprev, a * npts + q);
+    }
+    div += K.E0 * (vq - vp) + (eq * vq - ep0 * vp);
+  }
+  ep[p] = ep0 - K.dt * div;
 }
 
 template <typename Real, int kBC>
-__global__ void __launch_bounds__(TransportTile<Real>::kThreads)
-    k_transport_fused(StepConst<Real> K, const Real* __restrict__ es,
-                      const Real* __restrict__ ucur, const Real* __restrict__ uprev,
-                      const Real* __restrict__ drho, const Real* __restrict__ kap,
-                      Real* __restrict__ e_out, const Real* __restrict__ ghost) {
-  using T = TransportTile<Real>;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  Real* sE = reinterpret_cast<Real*>(smem_raw);  // [3][EP]
-  Real* sV = sE + 3 * T::EP;                     // [3 slots][3 comps][EP]
-  Real* sP = sV + 9 * T::EP;                     // [2][PP]
-  Real* sC = sP + 2 * T::PP;                     // [2][CP]
-  Real* sTH = sC + 2 * T::CP;                    // [3][CP]
-  Real* sD = sTH + 3 * T::CP;                    // [4][CP]
-  Real* sK = sD + 4 * T::CP;                     // [4][CP]
-  int* xw = reinterpret_cast<int*>(sK + 4 * T::CP);  // [EX] wrapped x (or -1/-2 ghost)
-  int* yw = xw + T::EX;                               // [EY] wrapped y
-  const int nzb = (K.nz + T::ZC - 1) / T::ZC;
-  const int s = blockIdx.z / nzb;
-  const int x0 = blockIdx.x * T::TX, y0 = blockIdx.y * T::TY, z0 = (blockIdx.z - s * nzb) * T::ZC;
+__global__ void __launch_bounds__(128)
+    k_mac_corr(StepConst<Real> K, const Real* __restrict__ e, const Real* __restrict__ ep,
+               const Real* __restrict__ v, const Real* __restrict__ drho, Real* __restrict__ ec,
+               Real* __restrict__ th, const Real* __restrict__ ghost) {
+  PointIdx P;
+  if (!point_from_block(K, P)) return;
   const int64_t npts = 2 * K.n3;
-  const int64_t sbase = (int64_t)s * K.n3;
-  const int tid = threadIdx.x;
+  const int64_t p = (int64_t)P.s * K.n3 + P.cell;
+  const Real epp = ep[p];
+  Real div = Real(0);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const Real vp = v[a * npts + p];
+    const int64_t q = axis_nb<kBC>(K, P, a, -1);
+    Real eq, vq;
+    if (kBC == 1 && q < 0) {
+      const Real* g = ghost + (q == -1 ? 0 : kGhostStride);
+      eq = g[kGhE];
+      vq = g[kGhU + a];
+    } else {
+      eq = ep[q];
+      vq = v[a * npts + q];
+    }
+    div += K.E0 * (vp - vq) + (epp * vp - eq * vq);
+  }
+  const Real val = Real(0.5) * (e[p] + epp - K.dt * div);
+  const Real dr = drho[p];
+  ec[p] = val;
+  th[p] = (Real(2) * val - K.delta * K.theta0 * dr) / (K.delta * (Real(1) + dr));
+}
+
+template <typename Real, int kBC>
+__global__ void __launch_bounds__(128)
+    k_ftcs_first(StepConst<Real> K, const Real* __restrict__ ec, const Real* __restrict__ th,
+                 const Real* __restrict__ kap, Real* __restrict__ e_next,
+                 const Real* __restrict__ ghost) {
+  PointIdx P;
+  if (!point_from_block(K, P)) return;
+  const int64_t p = (int64_t)P.s * K.n3 + P.cell;
   const Real t0d = K.delta * K.theta0;
-  for (int i = tid; i < T::EX; i += T::kThreads) {
-    const int gx = x0 + i - 2;
-    xw[i] = (kBC == 1 && gx < 0) ? -1 : (kBC == 1 && gx >= K.nx) ? -2 : wrap_any(gx, K.nx);
-  }
-  for (int i = tid; i < T::EY; i += T::kThreads) yw[i] = wrap_any(y0 + i - 2, K.ny);
-  const Real* gl = ghost;
-  const Real* gh = ghost + kGhostStride;
-  __syncthreads();
-
-  // registers holding the staged values of one plane
-  Real re[T::kEPer], rv0[T::kEPer], rv1[T::kEPer], rv2[T::kEPer];
-  Real rd[T::kCPer], rk[T::kCPer];
-  auto fetch = [&](int zn) {
-    const int zw = wrap_any(zn, K.nz);
+  const Real thp = th[p];
+  const Real kp = kap[p];
+  Real acc = Real(0);
 #pragma unroll
-    for (int j = 0; j < T::kEPer; ++j) {
-      const int i = tid + j * T::kThreads;
-      if (i < T::EP) {
-        const int xv = xw[i % T::EX], ry = i / T::EX;
-        if (kBC == 1 && xv < 0) {
-          const Real* g = xv == -1 ? gl : gh;
-          re[j] = g[kGhE]; rv0[j] = g[kGhU]; rv1[j] = g[kGhU + 1]; rv2[j] = g[kGhU + 2];
-        } else {
-          const int64_t q = sbase + ((int64_t)zw * K.ny + yw[ry]) * K.nx + xv;
-          re[j] = es[q];
-          rv0[j] = vadv(ucur, uprev, q);
-          rv1[j] = vadv(ucur, uprev, npts + q);
-          rv2[j] = vadv(ucur, uprev, 2 * npts + q);
-        }
-      }
-    }
+  for (int a = 0; a < 3; ++a) {
 #pragma unroll
-    for (int j = 0; j < T::kCPer; ++j) {
-      const int i = tid + j * T::kThreads;
-      if (i < T::CP) {
-        const int cx = i % T::CX, cy = i / T::CX;
-        const int xv = xw[cx + 1];
-        if (kBC == 1 && xv < 0) {
-          const Real* g = xv == -1 ? gl : gh;
-          rd[j] = g[kGhDrho]; rk[j] = g[kGhKap];
-        } else {
-          const int64_t q = sbase + ((int64_t)zw * K.ny + yw[cy + 1]) * K.nx + xv;
-          rd[j] = drho[q]; rk[j] = kap[q];
-        }
+    for (int d = -1; d <= 1; d += 2) {
+      const int64_t q = axis_nb<kBC>(K, P, a, d);
+      Real thq, kq;
+      if (kBC == 1 && q < 0) {
+        const Real* g = ghost + (q == -1 ? 0 : kGhostStride);
+        thq = (Real(2) * g[kGhE] - t0d * g[kGhDrho]) / (K.delta * (Real(1) + g[kGhDrho]));
+        kq = g[kGhKap];
+      } else {
+        thq = th[q];
+        kq = kap[q];
       }
-    }
-  };
-  fetch(z0 - 2);
-
-  for (int k = 0; k < T::ZC + 4; ++k) {
-    const int zn = z0 - 2 + k;     // plane staged in this iteration
-    const int se = k % 3;          // e/v ring slot of plane zn
-    const int sd = k & 3;          // rho/kappa ring slot of plane zn
-    __syncthreads();               // previous readers of the slots are done
-    // 1. stage plane zn from registers, then issue the loads of plane zn + 1
-#pragma unroll
-    for (int j = 0; j < T::kEPer; ++j) {
-      const int i = tid + j * T::kThreads;
-      if (i < T::EP) {
-        sE[se * T::EP + i] = re[j];
-        sV[(se * 3 + 0) * T::EP + i] = rv0[j];
-        sV[(se * 3 + 1) * T::EP + i] = rv1[j];
-        sV[(se * 3 + 2) * T::EP + i] = rv2[j];
-      }
-    }
-#pragma unroll
-    for (int j = 0; j < T::kCPer; ++j) {
-      const int i = tid + j * T::kThreads;
-      if (i < T::CP) {
-        sD[sd * T::CP + i] = rd[j];
-        sK[sd * T::CP + i] = rk[j];
-      }
-    }
-    if (k + 1 < T::ZC + 4) fetch(zn + 1);
-    __syncthreads();
-    // 2. predictor on plane zn - 1 (forward differences; z neighbour is plane zn)
-    if (k >= 1) {
-      const int sb = (k + 2) % 3;        // e/v slot of plane zn - 1
-      const int sp = (k - 1) & 1;        // predictor slot of plane zn - 1
-      for (int i = tid; i < T::PP; i += T::kThreads) {
-        const int px = i % T::PX, py = i / T::PX;
-        const int r = py * T::EX + px;   // same offsets (-2) in the e plane
-        Real val;
-        if (kBC == 1 && xw[px] < 0) {
-          val = sE[sb * T::EP + r];
-        } else {
-          const Real e0 = sE[sb * T::EP + r];
-          const int rn[3] = {r + 1, r + T::EX, r};
-          const int sn[3] = {sb, sb, se};
-          Real div = Real(0);
-#pragma unroll
-          for (int a = 0; a < 3; ++a) {
-            const Real vp = sV[(sb * 3 + a) * T::EP + r];
-            const Real vq = sV[(sn[a] * 3 + a) * T::EP + rn[a]];
-            const Real eq = sE[sn[a] * T::EP + rn[a]];
-            div += K.E0 * (vq - vp) + (eq * vq - e0 * vp);
-          }
-          val = e0 - K.dt * div;
-        }
-        sP[sp * T::PP + i] = val;
-      }
-    }
-    __syncthreads();
-    // 3. corrector on plane zn - 1 (backward differences; z neighbour is plane
-    //    zn - 2), then the theta_R deviation of that plane
-    if (k >= 2) {
-      const int sb = (k + 2) % 3;        // e/v slot of plane zn - 1
-      const int sm = (k + 1) % 3;        // e/v slot of plane zn - 2
-      const int pc = (k - 1) & 1;        // predictor of plane zn - 1
-      const int pm = k & 1;              // predictor of plane zn - 2
-      const int ct = (k - 1) & 1;        // corrector slot of plane zn - 1
-      const int sdm = (k + 3) & 3;       // rho/kappa slot of plane zn - 1
-      for (int i = tid; i < T::CP; i += T::kThreads) {
-        const int cx = i % T::CX, cy = i / T::CX;
-        const int r = (cy + 1) * T::EX + (cx + 1);  // e-plane index of this cell
-        const int pi = (cy + 1) * T::PX + (cx + 1);  // predictor index of this cell
-        Real val;
-        if (kBC == 1 && xw[cx + 1] < 0) {
-          val = sE[sb * T::EP + r];
-        } else {
-          const Real epp = sP[pc * T::PP + pi];
-          const Real pnb[3] = {sP[pc * T::PP + pi - 1], sP[pc * T::PP + pi - T::PX],
-                               sP[pm * T::PP + pi]};
-          const int vs[3] = {sb, sb, sm};
-          const int vr[3] = {r - 1, r - T::EX, r};
-          Real div = Real(0);
-#pragma unroll
-          for (int a = 0; a < 3; ++a) {
-            const Real vp = sV[(sb * 3 + a) * T::EP + r];
-            const Real vq = sV[(vs[a] * 3 + a) * T::EP + vr[a]];
-            div += K.E0 * (vp - vq) + (epp * vp - pnb[a] * vq);
-          }
-          val = Real(0.5) * (sE[sb * T::EP + r] + epp - K.dt * div);
-        }
-        const Real dr = sD[sdm * T::CP + i];
-        sC[ct * T::CP + i] = val;
-        sTH[sb * T::CP + i] = (Real(2) * val - t0d * dr) / (K.delta * (Real(1) + dr));
-      }
-    }
-    __syncthreads();
-    // 4. first FTCS sub-step on plane zn - 2
-    if (k >= 4) {
-      const int zo = zn - 2;
-      const int s0 = (k + 1) % 3;        // theta slot of plane zn - 2
-      const int sl = k % 3;              // plane zn - 3
-      const int su = (k + 2) % 3;        // plane zn - 1
-      const int k0 = (k + 2) & 3;        // kappa slot of plane zn - 2
-      const int kl = (k + 1) & 3;        // plane zn - 3
-      const int ku = (k + 3) & 3;        // plane zn - 1
-      const int co = k & 1;              // corrector of plane zn - 2
-      const int tx = tid % T::TX, ty = tid / T::TX;
-      const int x = x0 + tx, y = y0 + ty;
-      if (x < K.nx && y < K.ny && zo < K.nz) {
-        const int c = (ty + 1) * T::CX + (tx + 1);
-        const Real th = sTH[s0 * T::CP + c];
-        const Real kc = sK[k0 * T::CP + c];
-        // order -x, +x, -y, +y, -z, +z as in k_ftcs
-        const int ts[6] = {s0, s0, s0, s0, sl, su};
-        const int ks[6] = {k0, k0, k0, k0, kl, ku};
-        const int nc[6] = {c - 1, c + 1, c - T::CX, c + T::CX, c, c};
-        Real acc = Real(0);
-#pragma unroll
-        for (int m = 0; m < 6; ++m)
-          acc += Real(0.5) * (kc + sK[ks[m] * T::CP + nc[m]]) * (sTH[ts[m] * T::CP + nc[m]] - th);
-        e_out[sbase + ((int64_t)zo * K.ny + y) * K.nx + x] = sC[co * T::CP + c] + K.hsub * acc;
-      }
+      acc += Real(0.5) * (kp + kq) * (thq - thp);
     }
   }
+  e_next[p] = ec[p] + K.hsub * acc;
 }
 
 // Initial state of one point (Sec. 5): f = f^Eq(rho, u, theta_T I),

@@ -3,7 +3,6 @@
 #pragma once
 
 #include <algorithm>
-#include <atomic>
 #include <cmath>
 
 #include "rpk_internal.h"
@@ -66,19 +65,6 @@ static rpk_status collide_launch(rpk_lattice* L, const StepConst<Real>& K) {
 
 template <typename Real, int kBC>
 static rpk_status transport_launch(rpk_lattice* L, const StepConst<Real>& K) {
-  using TT = TransportTile<Real>;
-  // the dynamic shared memory limit is a per-device function attribute
-  static std::atomic<uint64_t> attr_set{0};
-  const size_t smem = TT::smem_bytes();
-  const uint64_t bit = 1ull << (L->device & 63);
-  if (!(attr_set.load() & bit)) {
-    RPK_CUDA(cudaFuncSetAttribute(k_transport_fused<Real, kBC>,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    attr_set.fetch_or(bit);
-  }
-  const int nzb = (L->grid.nz + TT::ZC - 1) / TT::ZC;
-  const dim3 tgrid((unsigned)((L->grid.nx + TT::TX - 1) / TT::TX),
-                   (unsigned)((L->grid.ny + TT::TY - 1) / TT::TY), (unsigned)(2 * nzb));
   const dim3 grid = point_grid(L, 128);
   const Real* ucur = static_cast<const Real*>(L->u[L->steps & 1]);
   const Real* uprev = static_cast<const Real*>(L->u[(L->steps + 1) & 1]);
@@ -88,19 +74,22 @@ static rpk_status transport_launch(rpk_lattice* L, const StepConst<Real>& K) {
   Real* es = static_cast<Real*>(L->e_star);
   Real* ea = static_cast<Real*>(L->e_a);
   Real* eb = static_cast<Real*>(L->e_b);
+  Real* v = static_cast<Real*>(L->vbuf);
+  Real* th = static_cast<Real*>(L->thbuf);
   Real* e = static_cast<Real*>(L->e);
-  // MacCormack + first FTCS sub-step; the remaining sub-steps end in e (state)
   RPK_CUDA(timing_begin(L));
+  k_mac_pred<Real, kBC><<<grid, 128, 0, L->stream>>>(K, es, ucur, uprev, ea, v, gh);
+  k_mac_corr<Real, kBC><<<grid, 128, 0, L->stream>>>(K, es, ea, v, drho, eb, th, gh);
+  // first FTCS sub-step from the stored theta_R; further sub-steps end in e
   Real* dst = L->nsub == 1 ? e : ea;
-  k_transport_fused<Real, kBC><<<tgrid, TT::kThreads, smem, L->stream>>>(K, es, ucur, uprev,
-                                                                          drho, kap, dst, gh);
+  k_ftcs_first<Real, kBC><<<grid, 128, 0, L->stream>>>(K, eb, th, kap, dst, gh);
   Real* src = dst;
   for (int k = 1; k < L->nsub; ++k) {
     dst = (k == L->nsub - 1) ? e : (src == ea ? eb : ea);
     k_ftcs<Real, kBC><<<grid, 128, 0, L->stream>>>(K, src, drho, kap, dst, gh);
     src = dst;
   }
-  RPK_CUDA(timing_end(L, RPK_KC_TRANSPORT, L->nsub));
+  RPK_CUDA(timing_end(L, RPK_KC_TRANSPORT, 2 + L->nsub));
   return check_launch("rotational transport");
 }
 
