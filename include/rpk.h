@@ -185,6 +185,68 @@ enum { RPK_KC_COLLIDE = 0, RPK_KC_TRANSPORT = 1, RPK_KC_COUNT = 2 };
 rpk_status rpk_timing(rpk_lattice* lat, int enable);
 rpk_status rpk_timing_read(rpk_lattice* lat, double* ms, int64_t* launches);
 
+/* ---- Batched quasi-1-D tubes (many independent shock tubes in one launch) ----
+ * Each tube is an nx x 1 x 1 lattice of the same model with its own relaxation
+ * parameters, x-reservoirs (RPK_BC_RESERVOIR semantics) and step count; the
+ * arithmetic per tube is the one of rpk_step on such a lattice. All tubes run
+ * in one persistent kernel launch (captured once into a CUDA graph): every CTA
+ * takes whole tubes from a work queue (longest work first) and runs their time
+ * loops itself, with the tube's rotational-energy and transport fields in
+ * shared memory and only the populations in device memory. The paper's
+ * shock-tube validations are single runs; batching is this library's.
+ * Field layout: tube b's 2*nx_b points (p = s*nx_b + x) follow tube b-1's in
+ * the concatenated arrays; u is three such concatenated planes. */
+typedef struct {
+  int nx;          /* cells per sublattice along x, 2 <= nx <= rpk_batch_max_nx() */
+  int nsteps;      /* steps that rpk_batch_run advances this tube, >= 0 */
+  rpk_relax relax; /* per-tube parameters (validated as in rpk_set_relax); nsub =
+                      0 is resolved at rpk_batch_init from the tube's fields */
+  double res[12];  /* reservoir states, as in rpk_set_reservoirs */
+} rpk_tube;
+
+typedef struct rpk_batch rpk_batch;
+
+/* Largest tube length the shared-memory layout supports for a precision. */
+int rpk_batch_max_nx(int precision);
+
+/* precision: RPK_F64 or RPK_F32. save_every >= 1: during rpk_batch_run, the
+ * moments (rho, u_x, theta_T, E_R) of every tube at steps 0, save_every,
+ * 2 save_every, ... (< nsteps) are stored as float snapshots. Copies the tube
+ * descriptions. */
+rpk_status rpk_batch_create(int precision, int ntubes, const rpk_tube* tubes, int save_every,
+                            void* cuda_stream, rpk_batch** out);
+void rpk_batch_destroy(rpk_batch* b);
+
+/* Initial state of every tube from concatenated host fields (rho, u (3 planes),
+ * theta_T, theta_R), as rpk_init_fields per tube. Synchronises. */
+rpk_status rpk_batch_init(rpk_batch* b, const double* rho, const double* u, const double* theta_T,
+                          const double* theta_R);
+
+/* Launch configuration of the persistent kernel: threads per CTA (a multiple
+ * of 32 in [64, 512]) and CTAs per SM (>= 1, limited by shared memory). */
+rpk_status rpk_batch_set_config(rpk_batch* b, int threads, int ctas_per_sm);
+
+/* Time every supported launch configuration on a sample of the batch's own
+ * tubes (a scratch copy; the batch state is untouched) and keep the fastest.
+ * out[0] = threads, out[1] = CTAs per SM, out[2] = sample milliseconds x 1000.
+ * Synchronises. */
+rpk_status rpk_batch_autotune(rpk_batch* b, int64_t out[3]);
+
+/* Advance every tube by its nsteps in one launch. Asynchronous. */
+rpk_status rpk_batch_run(rpk_batch* b);
+
+/* Moments of the current state of every tube (concatenated layout, host
+ * arrays; any may be NULL). Synchronises; RPK_ERR_NUMERIC if any tube flagged
+ * a non-finite or non-positive moment. */
+rpk_status rpk_batch_read_moments(rpk_batch* b, double* rho, double* u, double* theta_T,
+                                  double* theta_R, double* E_rot);
+
+/* Snapshots of the last rpk_batch_run: for tube b, nsnap_b = ceil(nsteps_b /
+ * save_every) records of 4 x 2 nx_b floats (rho, u_x, theta_T, E_R), tubes in
+ * order. Returns the total float count in *count; copies to host `out` when it
+ * is not NULL. Synchronises. */
+rpk_status rpk_batch_snapshots(rpk_batch* b, float* out, int64_t* count);
+
 /* Conserved totals of hydrodynamic fields held by the caller in device memory,
  * computed without allocating anything. The paper has no counterpart; this is
  * for callers that cannot call cudaMalloc where they need the totals (a loop

@@ -30,7 +30,7 @@ rpk_status cuda_fail(cudaError_t err, const char* what) {
   return RPK_ERR_CUDA;
 }
 
-static rpk_status fail(rpk_status st, const std::string& msg) {
+rpk_status fail(rpk_status st, const std::string& msg) {
   set_error(msg);
   return st;
 }
@@ -47,7 +47,7 @@ static rpk_status with_ops(int precision, F&& f) {
   }
 }
 
-static rpk_status validate_relax(const rpk_relax* r) {
+rpk_status validate_relax(const rpk_relax* r) {
   if (!r) return fail(RPK_ERR_ARG, "relax is NULL");
   if (!(r->delta > 0.0) || !std::isfinite(r->delta)) return fail(RPK_ERR_PARAM, "delta must be > 0");
   if (!(r->tau > 0.0) || !std::isfinite(r->tau)) return fail(RPK_ERR_PARAM, "tau must be > 0");

@@ -1,0 +1,746 @@
+// Batched quasi-1-D tubes: many independent nx x 1 x 1 lattices (shock tubes
+// with x reservoirs) advanced by one persistent kernel launch.
+//
+// Each CTA takes whole tubes from a work queue (an atomic counter over a
+// longest-work-first order) and runs every step of a tube itself: the pull +
+// collide pass over the tube's 2 nx points reads and writes the tube's
+// populations in device memory, while the auxiliary rotational energy, the
+// two velocity slots, rho - 1, kappa_R, the predictor and theta_R of the tube
+// live in shared memory for the whole time loop, so the transport (MacCormack
+// and the FTCS sub-steps) costs no device-memory traffic. Tubes need no
+// synchronisation with each other, so the launch has no grid-wide barrier. The
+// arithmetic is that of the lattice kernels (k_collide, k_mac_pred,
+// k_mac_corr, k_ftcs_first, k_ftcs) on an nx x 1 x 1 grid, where every y and z
+// neighbour is the point itself and contributes exact zeros.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <type_traits>
+#include <vector>
+
+#include "rpk_internal.h"
+#include "rpk_ops.cuh"
+
+namespace rpk {
+
+constexpr int kBatchArrays = 7;  // e, e*/theta, u slot 0, u slot 1, rho - 1, kappa, predictor
+constexpr size_t kBatchSmemLimit = 227 * 1024;
+
+template <typename Real>
+struct TubeDev {
+  StepConst<Real> K;  // nx, ny = nz = 1, n3 = nx and the relaxation constants
+  Real hdt;           // dt / (2 tau1), for the initial state
+  int nx, nsteps, nsub, cur;
+  int streamed, pad0, pad1, pad2;
+  int64_t pop_off;   // element offset of the tube in each population buffer
+  int64_t pt_off;    // point offset in the concatenated point arrays
+  int64_t snap_off;  // float offset of the tube's snapshots
+  Real ghost[2 * kGhostStride];
+};
+
+// Gathered point index of point p (0 <= p < 2 nx) of a tube.
+__device__ __forceinline__ PointIdx tube_point(int nx, int p) {
+  PointIdx P;
+  P.s = p >= nx;
+  P.x = p - P.s * nx;
+  P.y = 0;
+  P.z = 0;
+  P.cell = P.x;
+  return P;
+}
+
+template <typename Store, typename Real, int kThreads>
+__global__ void __launch_bounds__(kThreads)
+    k_batch(TubeDev<Real>* __restrict__ tubes, const int* __restrict__ order, int ntubes,
+            int* __restrict__ counter, Store* __restrict__ pop0, Store* __restrict__ pop1,
+            Real* __restrict__ e_state, Real* __restrict__ ux_state, float* __restrict__ snaps,
+            int save_every, int max_np, unsigned* __restrict__ status) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Real* sE = reinterpret_cast<Real*>(smem_raw);  // auxiliary E_R (state), then corrector
+  Real* sS = sE + max_np;                        // e* after exchange, then theta_R
+  Real* sU0 = sS + max_np;                       // u_x ring slot 0
+  Real* sU1 = sU0 + max_np;                      // u_x ring slot 1
+  Real* sD = sU1 + max_np;                       // rho - 1
+  Real* sK = sD + max_np;                        // kappa_R
+  Real* sP = sK + max_np;                        // predictor
+  __shared__ int s_slot;
+  const int tid = threadIdx.x;
+  for (;;) {
+    __syncthreads();
+    if (tid == 0) s_slot = atomicAdd(counter, 1);
+    __syncthreads();
+    const int slot = s_slot;
+    if (slot >= ntubes) break;
+    TubeDev<Real>* T = tubes + order[slot];
+    const StepConst<Real> K = T->K;
+    const int nx = T->nx, np = 2 * nx, nsteps = T->nsteps, nsub = T->nsub;
+    const Real* ghost = T->ghost;
+    const Real* gl = ghost;
+    const Real* gh = ghost + kGhostStride;
+    Real* gE = e_state + T->pt_off;
+    Real* gU = ux_state + T->pt_off;
+    for (int p = tid; p < np; p += kThreads) {
+      sE[p] = gE[p];
+      sU1[p] = gU[p];  // u(t-1) for the first step
+    }
+    int cur = T->cur;
+    bool streamed = T->streamed != 0;
+    Store* bufs[2] = {pop0 + T->pop_off, pop1 + T->pop_off};
+    const Real t0d = K.delta * K.theta0;
+    __syncthreads();
+    for (int t = 0; t < nsteps; ++t) {
+      Real* uc = (t & 1) ? sU1 : sU0;
+      const Real* up = (t & 1) ? sU0 : sU1;
+      const Store* pin = bufs[cur];
+      Store* pout = bufs[cur ^ 1];
+      const bool snap = (t % save_every) == 0;
+      float* sn = snaps + T->snap_off + (int64_t)(t / save_every) * 4 * np;
+      // 1. pull + collide + exchange of every point of the tube
+      for (int p = tid; p < np; p += kThreads) {
+        const PointIdx P = tube_point(nx, p);
+        Real h[kQ];
+        if (streamed)
+          gather<Store, Real, false, 1>(pin, ghost, K, P, h);
+        else
+          gather<Store, Real, true, 1>(pin, ghost, K, P, h);
+        Mom<Real> m;
+        const Real es = collide_point<Store, Real>(K, h, sE[p], pout + (int64_t)(P.s * kQ) * K.n3 + P.cell, m);
+        sS[p] = es;
+        sD[p] = m.drho;
+        uc[p] = m.j[0] * m.inv_rho;
+        sK[p] = K.kapc * m.rho * (K.theta0 + m.dth);
+        flag_moments(m, K.theta0, status);
+        if (snap) {
+          sn[p] = (float)(Real(1) + m.drho);
+          sn[np + p] = (float)(m.j[0] * m.inv_rho);
+          sn[2 * np + p] = (float)(K.theta0 + m.dT);
+          sn[3 * np + p] = (float)(Real(0.5) * K.delta * m.rho * (K.theta0 + m.dR));
+        }
+      }
+      __syncthreads();
+      // 2. MacCormack predictor (forward difference along x, same sublattice)
+      for (int p = tid; p < np; p += kThreads) {
+        const int s = p >= nx, x = p - s * nx;
+        const Real vp = Real(1.5) * uc[p] - Real(0.5) * up[p];
+        Real eq, vq;
+        if (x + 1 >= nx) {
+          eq = gh[kGhE];
+          vq = gh[kGhU];
+        } else {
+          eq = sS[p + 1];
+          vq = Real(1.5) * uc[p + 1] - Real(0.5) * up[p + 1];
+        }
+        const Real e0 = sS[p];
+        Real div = Real(0);
+        div += K.E0 * (vq - vp) + (eq * vq - e0 * vp);
+        sP[p] = e0 - K.dt * div;
+      }
+      __syncthreads();
+      // 3. corrector (backward difference), then theta_R of the result
+      for (int p = tid; p < np; p += kThreads) {
+        const int s = p >= nx, x = p - s * nx;
+        const Real vp = Real(1.5) * uc[p] - Real(0.5) * up[p];
+        Real eq, vq;
+        if (x == 0) {
+          eq = gl[kGhE];
+          vq = gl[kGhU];
+        } else {
+          eq = sP[p - 1];
+          vq = Real(1.5) * uc[p - 1] - Real(0.5) * up[p - 1];
+        }
+        const Real epp = sP[p];
+        Real div = Real(0);
+        div += K.E0 * (vp - vq) + (epp * vp - eq * vq);
+        const Real val = Real(0.5) * (sS[p] + epp - K.dt * div);
+        const Real dr = sD[p];
+        sE[p] = val;
+        sS[p] = (Real(2) * val - t0d * dr) / (K.delta * (Real(1) + dr));
+      }
+      __syncthreads();
+      // 4. FTCS sub-steps: e += h sum_faces K_face (theta_nb - theta)
+      for (int k = 0; k < nsub; ++k) {
+        for (int p = tid; p < np; p += kThreads) {
+          const int s = p >= nx, x = p - s * nx;
+          const Real thp = sS[p], kp = sK[p];
+          Real thm, km, thq, kq;
+          if (x == 0) {
+            thm = (Real(2) * gl[kGhE] - t0d * gl[kGhDrho]) / (K.delta * (Real(1) + gl[kGhDrho]));
+            km = gl[kGhKap];
+          } else {
+            thm = sS[p - 1];
+            km = sK[p - 1];
+          }
+          if (x + 1 >= nx) {
+            thq = (Real(2) * gh[kGhE] - t0d * gh[kGhDrho]) / (K.delta * (Real(1) + gh[kGhDrho]));
+            kq = gh[kGhKap];
+          } else {
+            thq = sS[p + 1];
+            kq = sK[p + 1];
+          }
+          Real acc = Real(0);
+          acc += Real(0.5) * (kp + km) * (thm - thp);
+          acc += Real(0.5) * (kp + kq) * (thq - thp);
+          sE[p] = sE[p] + K.hsub * acc;
+        }
+        __syncthreads();
+        if (k + 1 < nsub) {
+          for (int p = tid; p < np; p += kThreads)
+            sS[p] = (Real(2) * sE[p] - t0d * sD[p]) / (K.delta * (Real(1) + sD[p]));
+          __syncthreads();
+        }
+      }
+      cur ^= 1;
+      streamed = false;
+    }
+    // write the tube's state back
+    const Real* ulast = (nsteps == 0) ? sU1 : (((nsteps - 1) & 1) ? sU1 : sU0);
+    for (int p = tid; p < np; p += kThreads) {
+      gE[p] = sE[p];
+      gU[p] = ulast[p];
+    }
+    if (tid == 0) {
+      T->cur = cur;
+      T->streamed = streamed ? 1 : 0;
+    }
+  }
+}
+
+// Initial state and reservoir tables: one block per tube.
+template <typename Store, typename Real>
+__global__ void k_batch_init(TubeDev<Real>* __restrict__ tubes, const double* __restrict__ rho,
+                             const double* __restrict__ u, const double* __restrict__ T,
+                             const double* __restrict__ R, int64_t total_pts,
+                             const double* __restrict__ res, Store* __restrict__ pop0,
+                             Real* __restrict__ e_state, Real* __restrict__ ux_state) {
+  TubeDev<Real>* tb = tubes + blockIdx.x;
+  const StepConst<Real> K = tb->K;
+  const Real hdt = tb->hdt;
+  const int nx = tb->nx, np = 2 * nx;
+  const int64_t off = tb->pt_off;
+  Store* base = pop0 + tb->pop_off;
+  for (int p = threadIdx.x; p < np; p += blockDim.x) {
+    const PointIdx P = tube_point(nx, p);
+    const int64_t g = off + p;
+    Real h[kQ], e;
+    init_point(K, hdt, rho[g], u[g], u[total_pts + g], u[2 * total_pts + g], T[g], R[g], h, e);
+    Store* out = base + (int64_t)(P.s * kQ) * K.n3 + P.cell;
+#pragma unroll
+    for (int q = 0; q < kQ; ++q) out[(int64_t)q * K.n3] = from_real<Store, Real>(h[q]);
+    e_state[g] = e;
+    ux_state[g] = Real(u[g]);
+  }
+  if (threadIdx.x < 2) {
+    const int side = threadIdx.x;
+    const double* st = res + 12 * (int64_t)blockIdx.x + 6 * side;
+    Real h[kQ], e;
+    init_point(K, hdt, st[0], st[1], st[2], st[3], st[4], st[5], h, e);
+    Real* gg = tb->ghost + side * kGhostStride;
+    for (int q = 0; q < kQ; ++q) gg[q] = h[q];
+    gg[kGhE] = e;
+    gg[kGhDrho] = Real(st[0] - 1.0);
+    gg[kGhU] = Real(st[1]);
+    gg[kGhU + 1] = Real(st[2]);
+    gg[kGhU + 2] = Real(st[3]);
+    const double theta = (3.0 * st[4] + (double)K.delta * st[5]) / (3.0 + (double)K.delta);
+    gg[kGhKap] = Real((double)K.kapc * st[0] * theta);
+  }
+  if (threadIdx.x == 0) {
+    tb->cur = 0;
+    tb->streamed = 1;
+  }
+}
+
+// Moments of the current state, one block per tube (FP64 outputs).
+template <typename Store, typename Real>
+__global__ void k_batch_moments(const TubeDev<Real>* __restrict__ tubes, const Store* __restrict__ pop0,
+                                const Store* __restrict__ pop1, const Real* __restrict__ e_state,
+                                int64_t total_pts, double* __restrict__ out) {
+  const TubeDev<Real>* tb = tubes + blockIdx.x;
+  const StepConst<Real> K = tb->K;
+  const int nx = tb->nx, np = 2 * nx;
+  const Store* pin = (tb->cur ? pop1 : pop0) + tb->pop_off;
+  const int64_t off = tb->pt_off;
+  for (int p = threadIdx.x; p < np; p += blockDim.x) {
+    const PointIdx P = tube_point(nx, p);
+    Real h[kQ];
+    if (tb->streamed)
+      gather<Store, Real, false, 1>(pin, tb->ghost, K, P, h);
+    else
+      gather<Store, Real, true, 1>(pin, tb->ghost, K, P, h);
+    Mom<Real> m;
+    raw_moments(h, m);
+    recover(m, e_state[off + p], K);
+    const int64_t g = off + p;
+    out[g] = 1.0 + (double)m.drho;
+    out[total_pts + g] = (double)(m.j[0] * m.inv_rho);
+    out[2 * total_pts + g] = (double)(m.j[1] * m.inv_rho);
+    out[3 * total_pts + g] = (double)(m.j[2] * m.inv_rho);
+    out[4 * total_pts + g] = (double)K.theta0 + (double)m.dT;
+    out[5 * total_pts + g] = (double)K.theta0 + (double)m.dR;
+    out[6 * total_pts + g] =
+        0.5 * (double)K.delta * (1.0 + (double)m.drho) * ((double)K.theta0 + (double)m.dR);
+  }
+}
+
+}  // namespace rpk
+
+using namespace rpk;
+
+struct rpk_batch {
+  int precision = RPK_F32, ntubes = 0, save_every = 1, device = 0;
+  cudaStream_t stream = nullptr;
+  std::vector<rpk_tube> tubes;
+  std::vector<int> nsub;
+  std::vector<int64_t> pt_off, snap_off;
+  int64_t total_pts = 0, pop_elems = 0, snap_floats = 0;
+  int max_nx = 0;
+  size_t real_elem = 4, store_elem = 4;
+  void* pop[2] = {nullptr, nullptr};
+  void* e_state = nullptr;
+  void* ux_state = nullptr;
+  void* tubes_dev = nullptr;
+  int* order_dev = nullptr;
+  int* counter = nullptr;
+  float* snaps = nullptr;
+  unsigned* status = nullptr;
+  double* stage = nullptr;  // 7 x total_pts doubles, for init and reads
+  bool init_ok = false;
+  int threads = 256, ctas_per_sm = 1;
+  cudaGraphExec_t graph = nullptr;
+  int graph_threads = 0, graph_ctas = 0;
+};
+
+namespace {
+
+template <typename Store, typename Real>
+struct BatchOps {
+  static void* kernel(int threads) {
+    switch (threads) {
+      case 128: return (void*)k_batch<Store, Real, 128>;
+      case 256: return (void*)k_batch<Store, Real, 256>;
+      case 384: return (void*)k_batch<Store, Real, 384>;
+      case 512: return (void*)k_batch<Store, Real, 512>;
+      default: return nullptr;
+    }
+  }
+};
+
+bool supported_threads(int t) { return t == 128 || t == 256 || t == 384 || t == 512; }
+
+size_t batch_smem(const rpk_batch* B) {
+  return (size_t)kBatchArrays * 2 * B->max_nx * B->real_elem;
+}
+
+template <typename F>
+rpk_status with_batch_types(int precision, F&& f) {
+  if (precision == RPK_F64) return f(BatchOps<double, double>{}, (double*)nullptr);
+  return f(BatchOps<float, float>{}, (float*)nullptr);
+}
+
+void free_batch(rpk_batch* B) {
+  if (B->graph) cudaGraphExecDestroy(B->graph);
+  void* ptrs[] = {B->pop[0], B->pop[1], B->e_state, B->ux_state, B->tubes_dev, B->order_dev,
+                  B->counter, B->snaps, B->status, B->stage};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+}
+
+rpk_status dev_alloc(void** p, size_t bytes) {
+  cudaError_t err = cudaMalloc(p, bytes);
+  if (err != cudaSuccess) {
+    *p = nullptr;
+    cudaGetLastError();
+    return fail(err == cudaErrorMemoryAllocation ? RPK_ERR_OOM : RPK_ERR_CUDA,
+                std::string("batch allocation failed: ") + cudaGetErrorString(err));
+  }
+  return RPK_OK;
+}
+
+// Upload the tube descriptors (constants, offsets, nsub) and the work order.
+template <typename Real>
+rpk_status upload_tubes(rpk_batch* B) {
+  std::vector<TubeDev<Real>> td(B->ntubes);
+  int64_t pop_off = 0;
+  for (int i = 0; i < B->ntubes; ++i) {
+    const rpk_tube& t = B->tubes[i];
+    TubeDev<Real>& d = td[i];
+    std::memset(&d, 0, sizeof(d));
+    d.K = make_step_const<Real>(t.relax, B->nsub[i], t.nx, 1, 1);
+    d.hdt = Real(0.5 * t.relax.dt / t.relax.tau1);
+    d.nx = t.nx;
+    d.nsteps = t.nsteps;
+    d.nsub = B->nsub[i];
+    d.cur = 0;
+    d.streamed = 1;
+    d.pop_off = pop_off;
+    d.pt_off = B->pt_off[i];
+    d.snap_off = B->snap_off[i];
+    pop_off += (int64_t)2 * kQ * t.nx;
+  }
+  // longest work first: collide work ~ points x steps, diffusion ~ points x steps x nsub
+  std::vector<int> order(B->ntubes);
+  for (int i = 0; i < B->ntubes; ++i) order[i] = i;
+  std::vector<double> work(B->ntubes);
+  for (int i = 0; i < B->ntubes; ++i)
+    work[i] = 2.0 * B->tubes[i].nx * B->tubes[i].nsteps * (8.0 + B->nsub[i]);
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return work[a] > work[b]; });
+  RPK_CUDA(cudaMemcpyAsync(B->tubes_dev, td.data(), sizeof(TubeDev<Real>) * B->ntubes,
+                           cudaMemcpyHostToDevice, B->stream));
+  RPK_CUDA(cudaMemcpyAsync(B->order_dev, order.data(), sizeof(int) * B->ntubes,
+                           cudaMemcpyHostToDevice, B->stream));
+  RPK_CUDA(cudaStreamSynchronize(B->stream));
+  return RPK_OK;
+}
+
+// Shared-memory limit of the kernel variant (outside any stream capture).
+template <typename Store, typename Real>
+rpk_status prepare_batch(rpk_batch* B, int threads) {
+  void* kfn = BatchOps<Store, Real>::kernel(threads);
+  if (!kfn) return fail(RPK_ERR_ARG, "unsupported thread count");
+  RPK_CUDA(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)batch_smem(B)));
+  return RPK_OK;
+}
+
+template <typename Store, typename Real>
+rpk_status launch_batch(rpk_batch* B, cudaStream_t stream, int threads, int ctas_per_sm) {
+  int nsm = 0;
+  RPK_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, B->device));
+  const size_t smem = batch_smem(B);
+  const int grid = std::max(1, std::min(B->ntubes, nsm * ctas_per_sm));
+  RPK_CUDA(cudaMemsetAsync(B->counter, 0, sizeof(int), stream));
+  TubeDev<Real>* tubes = static_cast<TubeDev<Real>*>(B->tubes_dev);
+  Store* p0 = static_cast<Store*>(B->pop[0]);
+  Store* p1 = static_cast<Store*>(B->pop[1]);
+  Real* es = static_cast<Real*>(B->e_state);
+  Real* us = static_cast<Real*>(B->ux_state);
+  const int max_np = 2 * B->max_nx;
+  switch (threads) {
+#define RPK_LAUNCH(NT)                                                                         \
+  case NT:                                                                                     \
+    k_batch<Store, Real, NT><<<grid, NT, smem, stream>>>(tubes, B->order_dev, B->ntubes,       \
+                                                         B->counter, p0, p1, es, us, B->snaps, \
+                                                         B->save_every, max_np, B->status);    \
+    break;
+    RPK_LAUNCH(128)
+    RPK_LAUNCH(256)
+    RPK_LAUNCH(384)
+    RPK_LAUNCH(512)
+#undef RPK_LAUNCH
+  }
+  RPK_CUDA(cudaGetLastError());
+  return RPK_OK;
+}
+
+bool config_fits(const rpk_batch* B, int threads, int ctas) {
+  return supported_threads(threads) && ctas >= 1 && batch_smem(B) * ctas <= kBatchSmemLimit &&
+         threads * ctas <= 2048;
+}
+
+}  // namespace
+
+extern "C" {
+
+int rpk_batch_max_nx(int precision) {
+  const size_t real = precision == RPK_F64 ? 8 : 4;
+  return (int)((kBatchSmemLimit - 1024) / (kBatchArrays * 2 * real));
+}
+
+rpk_status rpk_batch_create(int precision, int ntubes, const rpk_tube* tubes, int save_every,
+                            void* cuda_stream, rpk_batch** out) {
+  if (!out || !tubes) return fail(RPK_ERR_ARG, "NULL argument");
+  *out = nullptr;
+  if (precision != RPK_F64 && precision != RPK_F32)
+    return fail(RPK_ERR_ARG, "batched tubes support RPK_F64 and RPK_F32");
+  if (ntubes < 1) return fail(RPK_ERR_ARG, "ntubes must be >= 1");
+  if (save_every < 1) return fail(RPK_ERR_ARG, "save_every must be >= 1");
+  const int max_nx = rpk_batch_max_nx(precision);
+  for (int i = 0; i < ntubes; ++i) {
+    const rpk_tube& t = tubes[i];
+    if (t.nx < 2 || t.nx > max_nx)
+      return fail(RPK_ERR_ARG, "tube " + std::to_string(i) + ": nx must lie in [2, " +
+                                   std::to_string(max_nx) + "] for this precision");
+    if (t.nsteps < 0) return fail(RPK_ERR_ARG, "tube " + std::to_string(i) + ": nsteps < 0");
+    rpk_status st = validate_relax(&t.relax);
+    if (st != RPK_OK) return fail(st, "tube " + std::to_string(i) + ": " + rpk_last_error());
+    for (int side = 0; side < 2; ++side) {
+      const double* r = t.res + 6 * side;
+      if (!(r[0] > 0.0) || !(r[4] > 0.0) || !(r[5] > 0.0))
+        return fail(RPK_ERR_PARAM, "tube " + std::to_string(i) + ": reservoir rho, theta must be > 0");
+    }
+  }
+  rpk_batch* B = new (std::nothrow) rpk_batch();
+  if (!B) return fail(RPK_ERR_OOM, "host allocation failed");
+  B->precision = precision;
+  B->ntubes = ntubes;
+  B->save_every = save_every;
+  B->stream = static_cast<cudaStream_t>(cuda_stream);
+  B->tubes.assign(tubes, tubes + ntubes);
+  B->nsub.assign(ntubes, 1);
+  B->real_elem = B->store_elem = precision == RPK_F64 ? 8 : 4;
+  cudaError_t err = cudaGetDevice(&B->device);
+  if (err != cudaSuccess) {
+    delete B;
+    return cuda_fail(err, "cudaGetDevice");
+  }
+  B->pt_off.resize(ntubes);
+  B->snap_off.resize(ntubes);
+  for (int i = 0; i < ntubes; ++i) {
+    B->pt_off[i] = B->total_pts;
+    B->snap_off[i] = B->snap_floats;
+    const int64_t np = 2 * (int64_t)tubes[i].nx;
+    const int64_t nsnap = (tubes[i].nsteps + save_every - 1) / save_every;
+    B->total_pts += np;
+    B->snap_floats += nsnap * 4 * np;
+    B->max_nx = std::max(B->max_nx, tubes[i].nx);
+  }
+  B->pop_elems = (int64_t)kQ * B->total_pts;
+  const size_t tube_bytes = precision == RPK_F64 ? sizeof(TubeDev<double>) : sizeof(TubeDev<float>);
+  rpk_status st = RPK_OK;
+  if (st == RPK_OK) st = dev_alloc(&B->pop[0], B->pop_elems * B->store_elem);
+  if (st == RPK_OK) st = dev_alloc(&B->pop[1], B->pop_elems * B->store_elem);
+  if (st == RPK_OK) st = dev_alloc(&B->e_state, B->total_pts * B->real_elem);
+  if (st == RPK_OK) st = dev_alloc(&B->ux_state, B->total_pts * B->real_elem);
+  if (st == RPK_OK) st = dev_alloc(&B->tubes_dev, tube_bytes * ntubes);
+  if (st == RPK_OK) st = dev_alloc((void**)&B->order_dev, sizeof(int) * ntubes);
+  if (st == RPK_OK) st = dev_alloc((void**)&B->counter, sizeof(int));
+  if (st == RPK_OK) st = dev_alloc((void**)&B->snaps, std::max<int64_t>(1, B->snap_floats) * sizeof(float));
+  if (st == RPK_OK) st = dev_alloc((void**)&B->status, sizeof(unsigned));
+  if (st == RPK_OK) st = dev_alloc((void**)&B->stage, sizeof(double) * 7 * B->total_pts);
+  if (st != RPK_OK) {
+    free_batch(B);
+    delete B;
+    return st;
+  }
+  *out = B;
+  return RPK_OK;
+}
+
+void rpk_batch_destroy(rpk_batch* B) {
+  if (!B) return;
+  cudaStreamSynchronize(B->stream);
+  free_batch(B);
+  delete B;
+}
+
+rpk_status rpk_batch_init(rpk_batch* B, const double* rho, const double* u, const double* T,
+                          const double* R) {
+  if (!B || !rho || !u || !T || !R) return fail(RPK_ERR_ARG, "NULL argument");
+  RPK_CUDA(cudaSetDevice(B->device));
+  const int64_t n = B->total_pts;
+  for (int64_t p = 0; p < n; ++p)
+    if (!(rho[p] > 0.0) || !(T[p] > 0.0) || !(R[p] > 0.0) || !std::isfinite(rho[p]) ||
+        !std::isfinite(T[p]) || !std::isfinite(R[p]))
+      return fail(RPK_ERR_PARAM, "fields need finite rho > 0, theta_T > 0, theta_R > 0");
+  for (int64_t p = 0; p < 3 * n; ++p)
+    if (!std::isfinite(u[p])) return fail(RPK_ERR_PARAM, "u not finite");
+  // FTCS sub-steps per tube (rpk_auto_nsub with one active axis when nsub = 0)
+  for (int i = 0; i < B->ntubes; ++i) {
+    const rpk_tube& t = B->tubes[i];
+    if (t.relax.nsub > 0) {
+      B->nsub[i] = t.relax.nsub;
+      continue;
+    }
+    double tmax = 0.0;
+    for (int64_t p = B->pt_off[i]; p < B->pt_off[i] + 2 * t.nx; ++p)
+      tmax = std::max(tmax, (3.0 * T[p] + t.relax.delta * R[p]) / (3.0 + t.relax.delta));
+    for (int side = 0; side < 2; ++side)
+      tmax = std::max(tmax, (3.0 * t.res[6 * side + 4] + t.relax.delta * t.res[6 * side + 5]) /
+                                (3.0 + t.relax.delta));
+    B->nsub[i] = rpk_auto_nsub(&t.relax, tmax, 1);
+  }
+  rpk_status st = with_batch_types(B->precision, [&](auto ops, auto* real_tag) {
+    using Real = std::remove_pointer_t<decltype(real_tag)>;
+    return upload_tubes<Real>(B);
+  });
+  if (st != RPK_OK) return st;
+  std::vector<double> res(12 * (size_t)B->ntubes);
+  for (int i = 0; i < B->ntubes; ++i) std::memcpy(&res[12 * (size_t)i], B->tubes[i].res, 12 * sizeof(double));
+  double* s = B->stage;
+  RPK_CUDA(cudaMemcpyAsync(s, rho, n * sizeof(double), cudaMemcpyHostToDevice, B->stream));
+  RPK_CUDA(cudaMemcpyAsync(s + n, u, 3 * n * sizeof(double), cudaMemcpyHostToDevice, B->stream));
+  RPK_CUDA(cudaMemcpyAsync(s + 4 * n, T, n * sizeof(double), cudaMemcpyHostToDevice, B->stream));
+  RPK_CUDA(cudaMemcpyAsync(s + 5 * n, R, n * sizeof(double), cudaMemcpyHostToDevice, B->stream));
+  double* dres = nullptr;
+  st = dev_alloc((void**)&dres, res.size() * sizeof(double));
+  if (st != RPK_OK) return st;
+  cudaError_t err = cudaMemcpyAsync(dres, res.data(), res.size() * sizeof(double),
+                                    cudaMemcpyHostToDevice, B->stream);
+  if (err == cudaSuccess) {
+    if (B->precision == RPK_F64)
+      k_batch_init<double, double><<<B->ntubes, 256, 0, B->stream>>>(
+          static_cast<TubeDev<double>*>(B->tubes_dev), s, s + n, s + 4 * n, s + 5 * n, n, dres,
+          static_cast<double*>(B->pop[0]), static_cast<double*>(B->e_state),
+          static_cast<double*>(B->ux_state));
+    else
+      k_batch_init<float, float><<<B->ntubes, 256, 0, B->stream>>>(
+          static_cast<TubeDev<float>*>(B->tubes_dev), s, s + n, s + 4 * n, s + 5 * n, n, dres,
+          static_cast<float*>(B->pop[0]), static_cast<float*>(B->e_state),
+          static_cast<float*>(B->ux_state));
+    err = cudaGetLastError();
+  }
+  if (err == cudaSuccess) err = cudaMemsetAsync(B->status, 0, sizeof(unsigned), B->stream);
+  if (err == cudaSuccess) err = cudaStreamSynchronize(B->stream);
+  cudaFree(dres);
+  if (err != cudaSuccess) return cuda_fail(err, "rpk_batch_init");
+  B->init_ok = true;
+  return RPK_OK;
+}
+
+rpk_status rpk_batch_set_config(rpk_batch* B, int threads, int ctas_per_sm) {
+  if (!B) return fail(RPK_ERR_ARG, "NULL batch");
+  if (!config_fits(B, threads, ctas_per_sm))
+    return fail(RPK_ERR_ARG, "unsupported configuration (threads in {128,256,384,512}; shared "
+                             "memory of the CTAs per SM must fit)");
+  B->threads = threads;
+  B->ctas_per_sm = ctas_per_sm;
+  return RPK_OK;
+}
+
+rpk_status rpk_batch_run(rpk_batch* B) {
+  if (!B) return fail(RPK_ERR_ARG, "NULL batch");
+  if (!B->init_ok) return fail(RPK_ERR_STATE, "initialise the batch first");
+  RPK_CUDA(cudaSetDevice(B->device));
+  if (!B->graph || B->graph_threads != B->threads || B->graph_ctas != B->ctas_per_sm) {
+    if (B->graph) {
+      cudaGraphExecDestroy(B->graph);
+      B->graph = nullptr;
+    }
+    rpk_status pst = with_batch_types(B->precision, [&](auto ops, auto* real_tag) {
+      using Real = std::remove_pointer_t<decltype(real_tag)>;
+      return prepare_batch<Real, Real>(B, B->threads);
+    });
+    if (pst != RPK_OK) return pst;
+    cudaStream_t cap = nullptr;
+    RPK_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+    cudaError_t err = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    rpk_status st = RPK_OK;
+    if (err == cudaSuccess) {
+      st = with_batch_types(B->precision, [&](auto ops, auto* real_tag) {
+        using Real = std::remove_pointer_t<decltype(real_tag)>;
+        return launch_batch<Real, Real>(B, cap, B->threads, B->ctas_per_sm);
+      });
+      cudaGraph_t g = nullptr;
+      cudaError_t e2 = cudaStreamEndCapture(cap, &g);
+      if (st == RPK_OK && e2 == cudaSuccess) e2 = cudaGraphInstantiate(&B->graph, g, 0);
+      if (g) cudaGraphDestroy(g);
+      err = e2;
+    }
+    cudaStreamDestroy(cap);
+    if (st != RPK_OK) return st;
+    if (err != cudaSuccess) return cuda_fail(err, "batch graph capture");
+    B->graph_threads = B->threads;
+    B->graph_ctas = B->ctas_per_sm;
+  }
+  RPK_CUDA(cudaGraphLaunch(B->graph, B->stream));
+  return RPK_OK;
+}
+
+rpk_status rpk_batch_read_moments(rpk_batch* B, double* rho, double* u, double* T, double* R,
+                                  double* E) {
+  if (!B) return fail(RPK_ERR_ARG, "NULL batch");
+  if (!B->init_ok) return fail(RPK_ERR_STATE, "initialise the batch first");
+  RPK_CUDA(cudaSetDevice(B->device));
+  const int64_t n = B->total_pts;
+  if (B->precision == RPK_F64)
+    k_batch_moments<double, double><<<B->ntubes, 256, 0, B->stream>>>(
+        static_cast<const TubeDev<double>*>(B->tubes_dev), static_cast<const double*>(B->pop[0]),
+        static_cast<const double*>(B->pop[1]), static_cast<const double*>(B->e_state), n, B->stage);
+  else
+    k_batch_moments<float, float><<<B->ntubes, 256, 0, B->stream>>>(
+        static_cast<const TubeDev<float>*>(B->tubes_dev), static_cast<const float*>(B->pop[0]),
+        static_cast<const float*>(B->pop[1]), static_cast<const float*>(B->e_state), n, B->stage);
+  RPK_CUDA(cudaGetLastError());
+  const size_t b = n * sizeof(double);
+  if (rho) RPK_CUDA(cudaMemcpyAsync(rho, B->stage, b, cudaMemcpyDeviceToHost, B->stream));
+  if (u) RPK_CUDA(cudaMemcpyAsync(u, B->stage + n, 3 * b, cudaMemcpyDeviceToHost, B->stream));
+  if (T) RPK_CUDA(cudaMemcpyAsync(T, B->stage + 4 * n, b, cudaMemcpyDeviceToHost, B->stream));
+  if (R) RPK_CUDA(cudaMemcpyAsync(R, B->stage + 5 * n, b, cudaMemcpyDeviceToHost, B->stream));
+  if (E) RPK_CUDA(cudaMemcpyAsync(E, B->stage + 6 * n, b, cudaMemcpyDeviceToHost, B->stream));
+  unsigned flags = 0;
+  RPK_CUDA(cudaMemcpyAsync(&flags, B->status, sizeof(unsigned), cudaMemcpyDeviceToHost, B->stream));
+  RPK_CUDA(cudaStreamSynchronize(B->stream));
+  if (flags) return fail(RPK_ERR_NUMERIC, "a tube flagged a non-finite or non-positive moment");
+  return RPK_OK;
+}
+
+rpk_status rpk_batch_snapshots(rpk_batch* B, float* out, int64_t* count) {
+  if (!B || !count) return fail(RPK_ERR_ARG, "NULL argument");
+  RPK_CUDA(cudaSetDevice(B->device));
+  *count = B->snap_floats;
+  if (out && B->snap_floats > 0) {
+    RPK_CUDA(cudaMemcpyAsync(out, B->snaps, B->snap_floats * sizeof(float), cudaMemcpyDeviceToHost,
+                             B->stream));
+    RPK_CUDA(cudaStreamSynchronize(B->stream));
+  }
+  return RPK_OK;
+}
+
+rpk_status rpk_batch_autotune(rpk_batch* B, int64_t out[3]) {
+  if (!B || !out) return fail(RPK_ERR_ARG, "NULL argument");
+  if (!B->init_ok) return fail(RPK_ERR_STATE, "initialise the batch first");
+  RPK_CUDA(cudaSetDevice(B->device));
+  int nsm = 0;
+  RPK_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, B->device));
+  // sample: up to 2 tubes per SM spread over the work order, 32 steps each, at rest
+  const int nsample = std::min(B->ntubes, 2 * nsm);
+  std::vector<rpk_tube> tv;
+  for (int i = 0; i < nsample; ++i) {
+    rpk_tube t = B->tubes[(int64_t)i * B->ntubes / nsample];
+    t.nsteps = std::min(t.nsteps, 32);
+    t.relax.nsub = B->nsub[(int64_t)i * B->ntubes / nsample];
+    tv.push_back(t);
+  }
+  rpk_batch* S = nullptr;
+  rpk_status st = rpk_batch_create(B->precision, nsample, tv.data(), 1 << 30, B->stream, &S);
+  if (st != RPK_OK) return st;
+  S->max_nx = B->max_nx;  // same shared-memory footprint as the real launch
+  std::vector<double> rho(S->total_pts, 1.0), u(3 * S->total_pts, 0.0), T(S->total_pts, kTheta0);
+  st = rpk_batch_init(S, rho.data(), u.data(), T.data(), T.data());
+  double best_ms = 1e300;
+  int best_t = B->threads, best_c = B->ctas_per_sm;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (st == RPK_OK) {
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const int cand_t[] = {128, 256, 384, 512};
+    for (int t : cand_t) {
+      for (int c = 1; c <= 4; ++c) {
+        if (!config_fits(S, t, c)) continue;
+        float ms = 0.f;
+        st = with_batch_types(B->precision, [&](auto ops, auto* real_tag) {
+          using Real = std::remove_pointer_t<decltype(real_tag)>;
+          return prepare_batch<Real, Real>(S, t);
+        });
+        for (int rep = 0; rep < 2 && st == RPK_OK; ++rep) {
+          cudaEventRecord(e0, B->stream);
+          st = with_batch_types(B->precision, [&](auto ops, auto* real_tag) {
+            using Real = std::remove_pointer_t<decltype(real_tag)>;
+            return launch_batch<Real, Real>(S, B->stream, t, c);
+          });
+          cudaEventRecord(e1, B->stream);
+          cudaEventSynchronize(e1);
+          cudaEventElapsedTime(&ms, e0, e1);
+        }
+        if (st != RPK_OK) break;
+        if (ms < best_ms) {
+          best_ms = ms;
+          best_t = t;
+          best_c = c;
+        }
+      }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+  }
+  rpk_batch_destroy(S);
+  if (st != RPK_OK) return st;
+  B->threads = best_t;
+  B->ctas_per_sm = best_c;
+  out[0] = best_t;
+  out[1] = best_c;
+  out[2] = (int64_t)(best_ms * 1000.0);
+  return RPK_OK;
+}
+
+}  // extern "C"

@@ -10,6 +10,47 @@ namespace rpk {
 //   g' = (1 - 2 beta*) g + 2 beta* f^mix,   in h form: h' = c_keep h + c_relax (f^mix/w - 1)
 //   Er' = Er + dt (delta rho/2)(theta - theta_R)/tau1   (rotational exchange)
 // Writes h', e', rho - 1, u (ring slot of this step) and kappa_R.
+// Collision of one gathered point, in place of the paper's explicit update:
+// writes the 41 relaxed populations through `out` (element q at out[q * n3]),
+// returns the moments in m and the exchanged auxiliary rotational energy.
+template <typename Store, typename Real>
+__device__ __forceinline__ Real collide_point(const StepConst<Real>& K, const Real (&h)[kQ], Real e,
+                                              Store* __restrict__ out, Mom<Real>& m) {
+  raw_moments(h, m);
+  recover(m, e, K);
+  Herm<Real> H;
+  mix_coeffs(m, K, H);
+  const int64_t n3 = K.n3;
+  out[0] = from_real<Store, Real>(K.c_keep * h[0] + K.c_relax * H.e0);
+  static_for<kPairs>([&](auto kc) {
+    constexpr int k = decltype(kc)::value;
+    constexpr Vel2 v = kPairVel2[k];
+    const Real ev = herm_even<v.x, v.y, v.z>(H);
+    const Real od = herm_odd<v.x, v.y, v.z>(H);
+    out[(int64_t)(2 * k + 1) * n3] = from_real<Store, Real>(K.c_keep * h[2 * k + 1] + K.c_relax * (ev + od));
+    out[(int64_t)(2 * k + 2) * n3] = from_real<Store, Real>(K.c_keep * h[2 * k + 2] + K.c_relax * (ev - od));
+  });
+  return e + K.exc * m.rho * (m.dth - m.dR);
+}
+
+// Device status flags: 1 non-finite moment, 2 rho <= 0, 4 theta_T or theta_R <= 0.
+template <typename Real>
+__device__ __forceinline__ void flag_moments(const Mom<Real>& m, Real theta0,
+                                             unsigned* __restrict__ status) {
+  const bool ok = (m.rho > Real(0)) && (theta0 + m.dT > Real(0)) && (theta0 + m.dR > Real(0));
+  if (!ok) {
+    unsigned f = 0;
+    if (!(m.rho == m.rho) || !(m.dT == m.dT) || !(m.dR == m.dR)) f |= 1u;
+    if (!(m.rho > Real(0))) f |= 2u;
+    if (!(theta0 + m.dT > Real(0)) || !(theta0 + m.dR > Real(0))) f |= 4u;
+    atomicOr(status, f);
+  }
+}
+
+// One collision per point after the pull (Sec. 5):
+//   g' = (1 - 2 beta*) g + 2 beta* f^mix,   in h form: h' = c_keep h + c_relax (f^mix/w - 1)
+//   Er' = Er + dt (delta rho/2)(theta - theta_R)/tau1   (rotational exchange)
+// Writes h', e', rho - 1, u (ring slot of this step) and kappa_R.
 template <typename Store, typename Real, bool kPull, int kBC>
 __global__ void __launch_bounds__(128)
     k_collide(StepConst<Real> K, const Store* __restrict__ pin, Store* __restrict__ pout,
@@ -22,37 +63,16 @@ __global__ void __launch_bounds__(128)
   Real h[kQ];
   gather<Store, Real, kPull, kBC>(pin, ghost, K, P, h);
   Mom<Real> m;
-  raw_moments(h, m);
-  const Real e = e_in[p];
-  recover(m, e, K);
-  Herm<Real> H;
-  mix_coeffs(m, K, H);
-  Store* out = pout + (int64_t)(P.s * kQ) * K.n3 + P.cell;
-  const int64_t n3 = K.n3;
-  out[0] = from_real<Store, Real>(K.c_keep * h[0] + K.c_relax * H.e0);
-  static_for<kPairs>([&](auto kc) {
-    constexpr int k = decltype(kc)::value;
-    constexpr Vel2 v = kPairVel2[k];
-    const Real ev = herm_even<v.x, v.y, v.z>(H);
-    const Real od = herm_odd<v.x, v.y, v.z>(H);
-    out[(int64_t)(2 * k + 1) * n3] = from_real<Store, Real>(K.c_keep * h[2 * k + 1] + K.c_relax * (ev + od));
-    out[(int64_t)(2 * k + 2) * n3] = from_real<Store, Real>(K.c_keep * h[2 * k + 2] + K.c_relax * (ev - od));
-  });
-  e_out[p] = e + K.exc * m.rho * (m.dth - m.dR);
+  const Real es = collide_point<Store, Real>(K, h, e_in[p],
+                                             pout + (int64_t)(P.s * kQ) * K.n3 + P.cell, m);
+  e_out[p] = es;
   drho_out[p] = m.drho;
   const int64_t npts = 2 * K.n3;
   u_out[p] = m.j[0] * m.inv_rho;
   u_out[npts + p] = m.j[1] * m.inv_rho;
   u_out[2 * npts + p] = m.j[2] * m.inv_rho;
   kap_out[p] = K.kapc * m.rho * (K.theta0 + m.dth);
-  const bool ok = (m.rho > Real(0)) && (K.theta0 + m.dT > Real(0)) && (K.theta0 + m.dR > Real(0));
-  if (!ok) {
-    unsigned f = 0;
-    if (!(m.rho == m.rho) || !(m.dT == m.dT) || !(m.dR == m.dR)) f |= 1u;
-    if (!(m.rho > Real(0))) f |= 2u;
-    if (!(K.theta0 + m.dT > Real(0)) || !(K.theta0 + m.dR > Real(0))) f |= 4u;
-    atomicOr(status, f);
-  }
+  flag_moments(m, K.theta0, status);
 }
 
 }  // namespace rpk

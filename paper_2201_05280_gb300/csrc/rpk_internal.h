@@ -60,7 +60,10 @@ namespace rpk {
 
 // Thread-local error message of the last failed call.
 void set_error(const std::string& msg);
+rpk_status fail(rpk_status st, const std::string& msg);
 rpk_status cuda_fail(cudaError_t err, const char* what);
+// Parameter checks of rpk_set_relax.
+rpk_status validate_relax(const rpk_relax* r);
 
 #define RPK_CUDA(call)                                      \
   do {                                                      \

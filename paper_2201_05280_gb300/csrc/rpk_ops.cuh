@@ -10,17 +10,18 @@
 
 namespace rpk {
 
+// Per-launch constants of the step (Sec. 5) for relaxation parameters r on an
+// nx x ny x nz grid with nsub FTCS sub-steps; computed in double, then cast.
 template <typename Real>
-static StepConst<Real> make_const(const rpk_lattice* L) {
-  const rpk_relax& r = L->relax;
+static StepConst<Real> make_step_const(const rpk_relax& r, int nsub, int nx, int ny, int nz) {
   const double tau_s = 1.0 / (1.0 / r.tau + 1.0 / r.tau1);
   const double beta = r.dt / (2.0 * tau_s + r.dt);
   const double B = 1.0 + r.tau / r.tau1;
   StepConst<Real> K;
-  K.nx = L->grid.nx;
-  K.ny = L->grid.ny;
-  K.nz = L->grid.nz;
-  K.n3 = L->n3;
+  K.nx = nx;
+  K.ny = ny;
+  K.nz = nz;
+  K.n3 = (int64_t)nx * ny * nz;
   K.theta0 = Real(kTheta0);
   K.c_keep = Real(1.0 - 2.0 * beta);
   K.c_relax = Real(2.0 * beta);
@@ -36,8 +37,13 @@ static StepConst<Real> make_const(const rpk_lattice* L) {
   K.kapc = Real(r.k_r * 5.0 * r.tau / (2.0 * B));
   K.E0 = Real(0.5 * r.delta * kTheta0);
   K.dt = Real(r.dt);
-  K.hsub = Real(r.dt / std::max(1, L->nsub));
+  K.hsub = Real(r.dt / std::max(1, nsub));
   return K;
+}
+
+template <typename Real>
+static StepConst<Real> make_const(const rpk_lattice* L) {
+  return make_step_const<Real>(L->relax, L->nsub, L->grid.nx, L->grid.ny, L->grid.nz);
 }
 
 static inline dim3 point_grid(const rpk_lattice* L, int bx) {
