@@ -199,6 +199,56 @@ def run_reference(args, rank):
     return 0
 
 
+def run_batch(args):
+    """Batched shock-tube sweep: --tubes quasi-1-D tubes, lengths U[500, 4000],
+    pressure ratio U[2, 20] (right state on the left isentrope), Kn log-U[1e-3,
+    1e-1], eta_B/eta U[0.3, 2], Pr 0.71, each run for 0.35 L/c_s steps, moments
+    saved every 32 steps; one persistent, graph-captured launch, configuration
+    chosen by the autotuner. Prints one JSON line (not the lattice line)."""
+    import torch
+    import paper_2201_05280_gb300 as rpk
+    from paper_2201_05280_gb300 import build as B
+    B.build()
+    torch.cuda.set_device(0)
+    specs, f = I.tube_sweep(args.tubes, THETA0)
+    cs = np.sqrt(GAS["gamma"] * THETA0)
+    tubes = []
+    for sp in specs:
+        nu = sp["kn"] * cs * sp["nx"]
+        eta, etaB, kap = rpk.gas_from_nondim(GAS["gamma"], nu, sp["lam"], sp["pr"])
+        r = rpk.map_gas(GAS["gamma"], eta, etaB, kap, 0.0)
+        tubes.append({"nx": sp["nx"], "nsteps": sp["nsteps"], "relax": r, "res": sp["res"]})
+    stream = torch.cuda.Stream()
+    bt = rpk.Batch(tubes, precision="f32", save_every=32, stream=stream)
+    bt.init_fields(f["rho"], f["u"], f["T"], f["R"])
+    tune = bt.autotune()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(0) as clk:
+        e0.record(stream)
+        bt.run()
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    m = bt.read_moments(check=False)
+    updates = sum(2 * t["nx"] * t["nsteps"] for t in tubes)
+    finite = bool(np.all(np.isfinite(m["rho"])))
+    line = {"metric": METRIC, "mode": "batch", "value": updates / (ms * 1e-3) / 1e6,
+            "unit": "MLUPS", "n_gpus": 1, "ms": ms, "higher_is_better": True, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "batched sweep: %d quasi-1-D shock tubes" % args.tubes,
+                       "points": int(sum(2 * t["nx"] for t in tubes)),
+                       "point_updates": int(updates), "save_every": 32,
+                       "lengths": [500, 4000], "pressure_ratio": [2, 20], "kn": [1e-3, 1e-1],
+                       "eta_B_over_eta": [0.3, 2.0]},
+            "autotune": tune, "gpu_launches": 1, "all_finite": finite,
+            "clocks": clk.summary()}
+    print(json.dumps(line))
+    bt.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -211,6 +261,9 @@ def main():
     ap.add_argument("--cpu-n", type=int, default=24, help="oracle sample box for cpu_baseline")
     ap.add_argument("--cpu-steps", type=int, default=100)
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--mode", default="lattice", choices=["lattice", "batch"],
+                    help="lattice: the 3-D step (default); batch: the shock-tube sweep")
+    ap.add_argument("--tubes", type=int, default=4096, help="tubes in --mode batch")
     ap.add_argument("--workload", default="waves", choices=["waves", "tgv"],
                     help="decaying wave field (default) or Taylor-Green vortex Ma 0.3 Re 1600")
     args = ap.parse_args()
@@ -222,6 +275,8 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         return run_reference(args, rank)
+    if args.mode == "batch":
+        return run_batch(args)
 
     import torch
     import paper_2201_05280_gb300 as rpk

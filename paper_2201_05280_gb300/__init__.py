@@ -17,7 +17,7 @@ import os
 import numpy as np
 
 __all__ = ["Lattice", "RpkError", "load_library", "theta0", "map_gas", "auto_nsub",
-           "gas_from_nondim", "field_totals_noalloc", "PRECISIONS", "library_path"]
+           "gas_from_nondim", "field_totals_noalloc", "Batch", "PRECISIONS", "library_path"]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB_PATH = os.path.join(_HERE, "librpk.so")
@@ -46,6 +46,11 @@ class Relax(ctypes.Structure):
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class Tube(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("nsteps", ctypes.c_int), ("relax", Relax),
+                ("res", ctypes.c_double * 12)]
 
 
 class Diag(ctypes.Structure):
@@ -95,6 +100,15 @@ def load_library(path=None):
         "rpk_timing": (i, [vp, i]),
         "rpk_timing_read": (i, [vp, ctypes.POINTER(d), ctypes.POINTER(i64)]),
         "rpk_field_totals_noalloc": (i, [vp, vp, vp, vp, i64, d, vp, vp]),
+        "rpk_batch_max_nx": (i, [i]),
+        "rpk_batch_create": (i, [i, i, ctypes.POINTER(Tube), i, vp, ctypes.POINTER(vp)]),
+        "rpk_batch_destroy": (None, [vp]),
+        "rpk_batch_init": (i, [vp, vp, vp, vp, vp]),
+        "rpk_batch_set_config": (i, [vp, i, i]),
+        "rpk_batch_autotune": (i, [vp, ctypes.POINTER(i64)]),
+        "rpk_batch_run": (i, [vp]),
+        "rpk_batch_read_moments": (i, [vp, vp, vp, vp, vp, vp]),
+        "rpk_batch_snapshots": (i, [vp, vp, ctypes.POINTER(i64)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -292,3 +306,93 @@ class Lattice:
         out = (ctypes.c_int64 * 4)()
         _check(load_library().rpk_get_info(self._h, out))
         return {"nsub": out[0], "steps": out[1], "npts": out[2], "bytes": out[3]}
+
+
+class Batch:
+    """Many quasi-1-D tubes (nx x 1 x 1 lattices with x reservoirs) advanced in
+    one persistent launch (rpk_batch_*). ``tubes`` is a sequence of dicts with
+    keys nx, nsteps, relax (dict of rpk_relax fields) and res (12 reservoir
+    values). Fields are concatenated tube after tube (2 nx points each)."""
+
+    def __init__(self, tubes, precision="f32", save_every=32, stream=None):
+        lib = load_library()
+        arr = (Tube * len(tubes))()
+        for t, d in zip(arr, tubes):
+            t.nx, t.nsteps = int(d["nx"]), int(d["nsteps"])
+            r = d["relax"]
+            t.relax = Relax(r["delta"], r["tau"], r["tau1"], r.get("b", 0.0), r.get("k_r", 0.0),
+                            r.get("dt", 1.0), int(r.get("nsub", 0)))
+            for k in range(12):
+                t.res[k] = float(d["res"][k])
+        self.tubes = [dict(d) for d in tubes]
+        self.save_every = int(save_every)
+        self.offsets = np.cumsum([0] + [2 * int(d["nx"]) for d in tubes])
+        self.total_pts = int(self.offsets[-1])
+        h = ctypes.c_void_p()
+        _check(lib.rpk_batch_create(PRECISIONS[precision], len(tubes), arr, self.save_every,
+                                    _stream_handle(stream), ctypes.byref(h)))
+        self._h = h
+
+    @staticmethod
+    def max_nx(precision="f32"):
+        return load_library().rpk_batch_max_nx(PRECISIONS[precision])
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            load_library().rpk_batch_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def init_fields(self, rho, u, T, R):
+        n = self.total_pts
+        a = [np.ascontiguousarray(x, dtype=np.float64).reshape(-1) for x in (rho, u, T, R)]
+        if [x.size for x in a] != [n, 3 * n, n, n]:
+            raise ValueError("concatenated fields of %d points expected" % n)
+        _check(load_library().rpk_batch_init(self._h, *[x.ctypes.data_as(ctypes.c_void_p)
+                                                        for x in a]))
+        self._keep = a
+        return self
+
+    def set_config(self, threads, ctas_per_sm=1):
+        _check(load_library().rpk_batch_set_config(self._h, int(threads), int(ctas_per_sm)))
+        return self
+
+    def autotune(self):
+        out = (ctypes.c_int64 * 3)()
+        _check(load_library().rpk_batch_autotune(self._h, out))
+        return {"threads": out[0], "ctas_per_sm": out[1], "sample_ms": out[2] / 1000.0}
+
+    def run(self):
+        _check(load_library().rpk_batch_run(self._h))
+        return self
+
+    def read_moments(self, check=True):
+        n = self.total_pts
+        out = {"rho": np.empty(n), "u": np.empty((3, n)), "T": np.empty(n), "R": np.empty(n),
+               "Erot": np.empty(n)}
+        code = load_library().rpk_batch_read_moments(
+            self._h, *[out[k].ctypes.data_as(ctypes.c_void_p) for k in ("rho", "u", "T", "R", "Erot")])
+        if check:
+            _check(code)
+        return out
+
+    def snapshots(self):
+        """List per tube of float32 arrays (nsnap, 4, 2 nx): rho, u_x, theta_T, E_R at
+        steps 0, save_every, ... of the last run."""
+        lib = load_library()
+        cnt = ctypes.c_int64()
+        _check(lib.rpk_batch_snapshots(self._h, None, ctypes.byref(cnt)))
+        buf = np.empty(cnt.value, dtype=np.float32)
+        _check(lib.rpk_batch_snapshots(self._h, buf.ctypes.data_as(ctypes.c_void_p), ctypes.byref(cnt)))
+        res, off = [], 0
+        for d in self.tubes:
+            np2 = 2 * int(d["nx"])
+            ns = (int(d["nsteps"]) + self.save_every - 1) // self.save_every
+            res.append(buf[off:off + ns * 4 * np2].reshape(ns, 4, np2))
+            off += ns * 4 * np2
+        return res

@@ -170,3 +170,32 @@ def tile(fields, nx, ny, nz, reps):
 
     return {"rho": t(fields["rho"], 1)[0], "u": t(fields["u"], 3),
             "T": t(fields["T"], 1)[0], "R": t(fields["R"], 1)[0]}
+
+
+def tube_sweep(ntubes, theta0, gamma=1.4, seed=SEED, L=(500, 4000), ratio=(2.0, 20.0),
+               kn=(1e-3, 1e-1), lam=(0.3, 2.0), pr=0.71, run_fraction=0.35):
+    """Seeded batch of quasi-1-D Riemann problems (the batched shock-tube
+    sweep): per tube a length nx ~ U[L], pressure ratio ~ U[ratio] with the
+    right state on the left state's isentrope (rho_R = ratio^(-1/gamma), left
+    rho = 1, p = 1), Knudsen number log-uniform in ``kn``, eta_B/eta ~ U[lam],
+    Prandtl number ``pr``, and a run of round(run_fraction * nx / c_s) steps
+    (c_s = sqrt(gamma theta0)). Returns (specs, fields) where specs is a list of
+    dicts (nx, nsteps, ratio, kn, lam, pr, res) and fields the concatenated
+    initial fields (tube after tube, 2 nx points each)."""
+    rng = np.random.default_rng(seed)
+    cs = np.sqrt(gamma * theta0)
+    specs, parts = [], []
+    for _ in range(ntubes):
+        nx = int(rng.integers(L[0], L[1] + 1))
+        r = float(rng.uniform(*ratio))
+        k = float(np.exp(rng.uniform(np.log(kn[0]), np.log(kn[1]))))
+        la = float(rng.uniform(*lam))
+        f, res = shock_tube(nx, theta0, rho_r=r ** (-1.0 / gamma), p_r=1.0 / r)
+        specs.append({"nx": nx, "nsteps": int(round(run_fraction * nx / cs)), "ratio": r,
+                      "kn": k, "lam": la, "pr": pr, "res": res})
+        parts.append(f)
+    fields = {"rho": np.concatenate([p["rho"] for p in parts]),
+              "u": np.concatenate([p["u"] for p in parts], axis=1),
+              "T": np.concatenate([p["T"] for p in parts]),
+              "R": np.concatenate([p["R"] for p in parts])}
+    return specs, fields
