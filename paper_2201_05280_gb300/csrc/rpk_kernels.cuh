@@ -7,6 +7,22 @@
 
 namespace rpk {
 
+// Point of a (32 x 8) thread block of the transport passes: threadIdx.x runs
+// along x and threadIdx.y along y, so the y neighbours of most threads are
+// loaded by the same block and served from L1.
+constexpr int kTBX = 32, kTBY = 8;
+
+template <typename Real>
+__device__ __forceinline__ bool point_from_block2d(const StepConst<Real>& K, PointIdx& P) {
+  P.x = blockIdx.x * kTBX + threadIdx.x;
+  P.y = blockIdx.y * kTBY + threadIdx.y;
+  P.s = blockIdx.z / K.nz;
+  P.z = blockIdx.z - P.s * K.nz;
+  if (P.x >= K.nx || P.y >= K.ny) return false;
+  P.cell = ((int64_t)P.z * K.ny + P.y) * K.nx + P.x;
+  return true;
+}
+
 // Axis neighbour on the same sublattice, or -1 / -2 for the low / high x
 // reservoir when kBC == 1.
 template <int kBC, typename Real>
@@ -82,12 +98,12 @@ __global__ void __launch_bounds__(128)
 //                stored theta_R (no division per neighbour)
 // Further sub-steps use k_ftcs. Reservoir values stand beyond the x ends.
 template <typename Real, int kBC>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(kTBX * kTBY)
     k_mac_pred(StepConst<Real> K, const Real* __restrict__ e, const Real* __restrict__ ucur,
                const Real* __restrict__ uprev, Real* __restrict__ ep, Real* __restrict__ v,
                const Real* __restrict__ ghost) {
   PointIdx P;
-  if (!point_from_block(K, P)) return;
+  if (!point_from_block2d(K, P)) return;
   const int64_t npts = 2 * K.n3;
   const int64_t p = (int64_t)P.s * K.n3 + P.cell;
   const Real ep0 = e[p];
@@ -112,12 +128,12 @@ __global__ void __launch_bounds__(128)
 }
 
 template <typename Real, int kBC>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(kTBX * kTBY)
     k_mac_corr(StepConst<Real> K, const Real* __restrict__ e, const Real* __restrict__ ep,
                const Real* __restrict__ v, const Real* __restrict__ drho, Real* __restrict__ ec,
                Real* __restrict__ th, const Real* __restrict__ ghost) {
   PointIdx P;
-  if (!point_from_block(K, P)) return;
+  if (!point_from_block2d(K, P)) return;
   const int64_t npts = 2 * K.n3;
   const int64_t p = (int64_t)P.s * K.n3 + P.cell;
   const Real epp = ep[p];
@@ -144,12 +160,12 @@ __global__ void __launch_bounds__(128)
 }
 
 template <typename Real, int kBC>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(kTBX * kTBY)
     k_ftcs_first(StepConst<Real> K, const Real* __restrict__ ec, const Real* __restrict__ th,
                  const Real* __restrict__ kap, Real* __restrict__ e_next,
                  const Real* __restrict__ ghost) {
   PointIdx P;
-  if (!point_from_block(K, P)) return;
+  if (!point_from_block2d(K, P)) return;
   const int64_t p = (int64_t)P.s * K.n3 + P.cell;
   const Real t0d = K.delta * K.theta0;
   const Real thp = th[p];

@@ -83,12 +83,15 @@ static rpk_status transport_launch(rpk_lattice* L, const StepConst<Real>& K) {
   Real* v = static_cast<Real*>(L->vbuf);
   Real* th = static_cast<Real*>(L->thbuf);
   Real* e = static_cast<Real*>(L->e);
+  const dim3 tb(kTBX, kTBY);
+  const dim3 tgrid((unsigned)((L->grid.nx + kTBX - 1) / kTBX),
+                   (unsigned)((L->grid.ny + kTBY - 1) / kTBY), (unsigned)(2 * L->grid.nz));
   RPK_CUDA(timing_begin(L));
-  k_mac_pred<Real, kBC><<<grid, 128, 0, L->stream>>>(K, es, ucur, uprev, ea, v, gh);
-  k_mac_corr<Real, kBC><<<grid, 128, 0, L->stream>>>(K, es, ea, v, drho, eb, th, gh);
+  k_mac_pred<Real, kBC><<<tgrid, tb, 0, L->stream>>>(K, es, ucur, uprev, ea, v, gh);
+  k_mac_corr<Real, kBC><<<tgrid, tb, 0, L->stream>>>(K, es, ea, v, drho, eb, th, gh);
   // first FTCS sub-step from the stored theta_R; further sub-steps end in e
   Real* dst = L->nsub == 1 ? e : ea;
-  k_ftcs_first<Real, kBC><<<grid, 128, 0, L->stream>>>(K, eb, th, kap, dst, gh);
+  k_ftcs_first<Real, kBC><<<tgrid, tb, 0, L->stream>>>(K, eb, th, kap, dst, gh);
   Real* src = dst;
   for (int k = 1; k < L->nsub; ++k) {
     dst = (k == L->nsub - 1) ? e : (src == ea ? eb : ea);

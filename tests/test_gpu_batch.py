@@ -1,8 +1,11 @@
 """GPU parity of the batched quasi-1-D tubes (rpk_batch_*): every tube of a
 batch must match the FP64 oracle run of the same nx x 1 x 1 lattice with x
 reservoirs, both the final state and the snapshots taken during the run.
-Tolerances as in test_gpu_parity (u on the scale max(|u|, c_s)); snapshots
-are stored as float32, so they are compared at 1e-6."""
+FP64 tolerance as in test_gpu_parity (u on the scale max(|u|, c_s)). FP32
+shock tubes have deviations |h| up to about 2 (density ratios up to 8), so the
+round-to-nearest of the stored h adds about 2^-24 * 2 per step and up to 1e-5
+over the 80 steps here; their bound is 5e-5. Snapshots are stored as float32
+and compared at 1e-6 (or the run's bound when larger)."""
 import numpy as np
 import pytest
 
@@ -78,7 +81,7 @@ def _cmp(got, ref, tol):
     return errs
 
 
-@pytest.mark.parametrize("prec,tol", [("f64", 1e-12), ("f32", 1e-5)])
+@pytest.mark.parametrize("prec,tol", [("f64", 1e-12), ("f32", 5e-5)])
 def test_batch_matches_oracle_per_tube(prec, tol):
     save_every = 8
     tubes, f = _setup(6, (24, 160), seed=5)
