@@ -87,6 +87,9 @@ __global__ void __launch_bounds__(kThreads)
     bool streamed = T->streamed != 0;
     Store* bufs[2] = {pop0 + T->pop_off, pop1 + T->pop_off};
     const Real t0d = K.delta * K.theta0;
+    // theta_R of the two reservoirs (constant)
+    const Real thGl = (Real(2) * gl[kGhE] - t0d * gl[kGhDrho]) / (K.delta * (Real(1) + gl[kGhDrho]));
+    const Real thGh = (Real(2) * gh[kGhE] - t0d * gh[kGhDrho]) / (K.delta * (Real(1) + gh[kGhDrho]));
     __syncthreads();
     for (int t = 0; t < nsteps; ++t) {
       Real* uc = (t & 1) ? sU1 : sU0;
@@ -157,35 +160,53 @@ __global__ void __launch_bounds__(kThreads)
         sS[p] = (Real(2) * val - t0d * dr) / (K.delta * (Real(1) + dr));
       }
       __syncthreads();
-      // 4. FTCS sub-steps: e += h sum_faces K_face (theta_nb - theta)
-      for (int k = 0; k < nsub; ++k) {
+      // 4. FTCS sub-steps: e += h sum_faces K_face (theta_nb - theta). The first
+      //    uses theta_R of the corrector (sS) and updates e in place; later ones
+      //    use theta_R = a e + c with a = 2/(delta(1 + D)), c = -delta theta0 D/(delta(1 + D))
+      //    (affine in e at fixed rho), ping-ponging e between sE and sS with one
+      //    barrier per sub-step.
+      for (int p = tid; p < np; p += kThreads) {
+        const int s = p >= nx, x = p - s * nx;
+        const Real thp = sS[p], kp = sK[p];
+        const Real thm = x == 0 ? thGl : sS[p - 1], km = x == 0 ? gl[kGhKap] : sK[p - 1];
+        const Real thq = x + 1 >= nx ? thGh : sS[p + 1], kq = x + 1 >= nx ? gh[kGhKap] : sK[p + 1];
+        Real acc = Real(0);
+        acc += Real(0.5) * (kp + km) * (thm - thp);
+        acc += Real(0.5) * (kp + kq) * (thq - thp);
+        sE[p] = sE[p] + K.hsub * acc;
+      }
+      __syncthreads();
+      if (nsub > 1) {
         for (int p = tid; p < np; p += kThreads) {
-          const int s = p >= nx, x = p - s * nx;
-          const Real thp = sS[p], kp = sK[p];
-          Real thm, km, thq, kq;
-          if (x == 0) {
-            thm = (Real(2) * gl[kGhE] - t0d * gl[kGhDrho]) / (K.delta * (Real(1) + gl[kGhDrho]));
-            km = gl[kGhKap];
-          } else {
-            thm = sS[p - 1];
-            km = sK[p - 1];
-          }
-          if (x + 1 >= nx) {
-            thq = (Real(2) * gh[kGhE] - t0d * gh[kGhDrho]) / (K.delta * (Real(1) + gh[kGhDrho]));
-            kq = gh[kGhKap];
-          } else {
-            thq = sS[p + 1];
-            kq = sK[p + 1];
-          }
-          Real acc = Real(0);
-          acc += Real(0.5) * (kp + km) * (thm - thp);
-          acc += Real(0.5) * (kp + kq) * (thq - thp);
-          sE[p] = sE[p] + K.hsub * acc;
+          const Real dr = sD[p];
+          const Real inv = Real(1) / (K.delta * (Real(1) + dr));
+          sP[p] = Real(2) * inv;    // a
+          sD[p] = -t0d * dr * inv;  // c
         }
         __syncthreads();
-        if (k + 1 < nsub) {
-          for (int p = tid; p < np; p += kThreads)
-            sS[p] = (Real(2) * sE[p] - t0d * sD[p]) / (K.delta * (Real(1) + sD[p]));
+        Real* ein = sE;
+        Real* eout = sS;
+        for (int k = 1; k < nsub; ++k) {
+          for (int p = tid; p < np; p += kThreads) {
+            const int s = p >= nx, x = p - s * nx;
+            const Real ep = ein[p];
+            const Real thp = sP[p] * ep + sD[p], kp = sK[p];
+            const Real thm = x == 0 ? thGl : sP[p - 1] * ein[p - 1] + sD[p - 1];
+            const Real km = x == 0 ? gl[kGhKap] : sK[p - 1];
+            const Real thq = x + 1 >= nx ? thGh : sP[p + 1] * ein[p + 1] + sD[p + 1];
+            const Real kq = x + 1 >= nx ? gh[kGhKap] : sK[p + 1];
+            Real acc = Real(0);
+            acc += Real(0.5) * (kp + km) * (thm - thp);
+            acc += Real(0.5) * (kp + kq) * (thq - thp);
+            eout[p] = ep + K.hsub * acc;
+          }
+          __syncthreads();
+          Real* tmp = ein;
+          ein = eout;
+          eout = tmp;
+        }
+        if (ein != sE) {
+          for (int p = tid; p < np; p += kThreads) sE[p] = ein[p];
           __syncthreads();
         }
       }
