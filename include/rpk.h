@@ -246,6 +246,55 @@ rpk_status rpk_batch_read_moments(rpk_batch* b, double* rho, double* u, double* 
  * order. Returns the total float count in *count; copies to host `out` when it
  * is not NULL. Synchronises. */
 rpk_status rpk_batch_snapshots(rpk_batch* b, float* out, int64_t* count);
+/* Moment blocks: per tube, in tube order, [4][2 nx] floats holding rho, u_x,
+ * theta_T and E_R = delta rho theta_R / 2 at the tube's 2 nx points (point
+ * order as in the fields), i.e. tube b's block starts at float 8 sum_{b'<b}
+ * nx_b' -- the layout of one snapshot. Device pointers. */
+/* Initialise every tube from moment blocks (u_y = u_z = 0; theta_R from E_R).
+ * Needs every tube's FTCS sub-step count: relax.nsub > 0, or an earlier
+ * rpk_batch_init from host fields. Invalid values (non-positive or non-finite)
+ * are reported by the next rpk_batch_read_moments. Synchronises. */
+rpk_status rpk_batch_init_device(rpk_batch* b, const float* state);
+/* Steps of the next rpk_batch_run per tube (host array), each in [0, the count
+ * given at creation]; snapshots keep their creation-time offsets. Synchronises. */
+rpk_status rpk_batch_set_steps(rpk_batch* b, const int* nsteps);
+/* Current moments into device moment blocks. Asynchronous (the batch's stream). */
+rpk_status rpk_batch_moments_device(rpk_batch* b, float* state);
+
+/* ---- Learned surrogate network (a 1-D convolutional operator) --------------
+ * Maps the moment fields of quasi-1-D tubes at step t to step t + 32 (the
+ * paper has no learned component). Architecture on a sequence of L fine points
+ * (L a multiple of 4), position-major tensors [sequence][point][channel]:
+ * unshuffle by 4 -> conv k=1 (4 cin -> width) -> nblocks residual blocks
+ * h + conv5(relu(conv5(relu(h)))) -> conv k=1 of relu(h) (width -> 4 cout) ->
+ * shuffle. Every contraction runs on the tensor cores with BF16 operands and
+ * FP32 accumulation; parameters are FP32 master copies with Adam state.
+ * Parameter vector: per layer (lift, block convs, head) the weights W[o][t][i]
+ * then the biases. All pointers to tensors are device pointers on the
+ * network's device; calls on the network's stream. */
+typedef struct rpk_net rpk_net;
+rpk_status rpk_net_create(int cin, int cout, int width, int nblocks, uint64_t seed,
+                          void* cuda_stream, rpk_net** out);
+void rpk_net_destroy(rpk_net* net);
+int64_t rpk_net_num_params(const rpk_net* net);
+/* which = 0: parameters, 1: gradients of the last rpk_net_loss_grad (host
+ * array of rpk_net_num_params floats). Synchronises. */
+rpk_status rpk_net_get_params(rpk_net* net, float* host, int which);
+rpk_status rpk_net_set_params(rpk_net* net, const float* host);
+/* y[nseq][len][cout] = network(x[nseq][len][cin]). Asynchronous. */
+rpk_status rpk_net_forward(rpk_net* net, const float* x, int nseq, int len, float* y);
+/* The same network over nseq sequences of different lengths lens[s] (host
+ * array, each a positive multiple of 4), concatenated position-major in x
+ * [sum lens][cin] and y [sum lens][cout]; zero padding at every sequence's ends.
+ * Synchronises the network's stream. */
+rpk_status rpk_net_forward_ragged(rpk_net* net, const float* x, int nseq, const int* lens, float* y);
+/* Masked mean-squared error sum(mask (y - target)^2)/(sum(mask) cout) of the
+ * network output against target[nseq][len][cout], mask[nseq][len]; writes the
+ * loss to *loss and the gradients to the network. Synchronises. */
+rpk_status rpk_net_loss_grad(rpk_net* net, const float* x, const float* target,
+                             const float* mask, int nseq, int len, double* loss);
+/* One Adam step (bias-corrected) with the stored gradients. Asynchronous. */
+rpk_status rpk_net_adam(rpk_net* net, float lr, float beta1, float beta2, float eps);
 
 /* Conserved totals of hydrodynamic fields held by the caller in device memory,
  * computed without allocating anything. The paper has no counterpart; this is

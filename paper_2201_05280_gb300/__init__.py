@@ -17,7 +17,7 @@ import os
 import numpy as np
 
 __all__ = ["Lattice", "RpkError", "load_library", "theta0", "map_gas", "auto_nsub",
-           "gas_from_nondim", "field_totals_noalloc", "Batch", "PRECISIONS", "library_path"]
+           "gas_from_nondim", "field_totals_noalloc", "Batch", "Net", "PRECISIONS", "library_path"]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB_PATH = os.path.join(_HERE, "librpk.so")
@@ -109,6 +109,15 @@ def load_library(path=None):
         "rpk_batch_run": (i, [vp]),
         "rpk_batch_read_moments": (i, [vp, vp, vp, vp, vp, vp]),
         "rpk_batch_snapshots": (i, [vp, vp, ctypes.POINTER(i64)]),
+        "rpk_net_create": (i, [i, i, i, i, ctypes.c_uint64, vp, ctypes.POINTER(vp)]),
+        "rpk_net_destroy": (None, [vp]),
+        "rpk_net_num_params": (i64, [vp]),
+        "rpk_net_get_params": (i, [vp, vp, i]),
+        "rpk_net_set_params": (i, [vp, vp]),
+        "rpk_net_forward": (i, [vp, vp, i, i, vp]),
+        "rpk_net_forward_ragged": (i, [vp, vp, i, ctypes.POINTER(i), vp]),
+        "rpk_net_loss_grad": (i, [vp, vp, vp, vp, i, i, ctypes.POINTER(d)]),
+        "rpk_net_adam": (i, [vp, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -396,3 +405,91 @@ class Batch:
             res.append(buf[off:off + ns * 4 * np2].reshape(ns, 4, np2))
             off += ns * 4 * np2
         return res
+
+
+def _dev_f32(t, shape=None, name="tensor"):
+    """Device pointer of a contiguous CUDA float32 torch tensor."""
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float32
+            and t.is_contiguous()):
+        raise TypeError("%s must be a contiguous CUDA float32 tensor" % name)
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError("%s has shape %s, expected %s" % (name, tuple(t.shape), tuple(shape)))
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Net:
+    """The surrogate network of the C interface (rpk_net_*): a 1-D convolutional
+    operator on position-major tensors [sequence][point][channel], trained and
+    evaluated by the library's BF16 tensor-core kernels. Tensors are contiguous
+    CUDA float32 torch tensors; parameters cross as host numpy float32 vectors."""
+
+    def __init__(self, cin, cout, width=128, nblocks=6, seed=0, stream=None):
+        h = ctypes.c_void_p()
+        _check(load_library().rpk_net_create(int(cin), int(cout), int(width), int(nblocks),
+                                             int(seed), _stream_handle(stream), ctypes.byref(h)))
+        self._h = h
+        self.cin, self.cout, self.width, self.nblocks = int(cin), int(cout), int(width), int(nblocks)
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            load_library().rpk_net_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def num_params(self):
+        return int(load_library().rpk_net_num_params(self._h))
+
+    def params(self, grads=False):
+        out = np.empty(self.num_params, dtype=np.float32)
+        _check(load_library().rpk_net_get_params(self._h, out.ctypes.data_as(ctypes.c_void_p),
+                                                 1 if grads else 0))
+        return out
+
+    def set_params(self, v):
+        v = np.ascontiguousarray(v, dtype=np.float32)
+        if v.size != self.num_params:
+            raise ValueError("expected %d parameters" % self.num_params)
+        _check(load_library().rpk_net_set_params(self._h, v.ctypes.data_as(ctypes.c_void_p)))
+
+    def forward(self, x, out=None):
+        import torch
+        nseq, length, cin = x.shape
+        if cin != self.cin:
+            raise ValueError("expected %d input channels" % self.cin)
+        if out is None:
+            out = torch.empty((nseq, length, self.cout), device=x.device, dtype=torch.float32)
+        _check(load_library().rpk_net_forward(self._h, _dev_f32(x, name="x"), nseq, length,
+                                              _dev_f32(out, (nseq, length, self.cout), "out")))
+        return out
+
+    def forward_ragged(self, x, lens, out=None):
+        """x [sum(lens)][cin]: sequences of the given lengths (multiples of 4) back to back."""
+        import torch
+        lens = [int(v) for v in lens]
+        n = sum(lens)
+        if out is None:
+            out = torch.empty((n, self.cout), device=x.device, dtype=torch.float32)
+        arr = (ctypes.c_int * len(lens))(*lens)
+        _check(load_library().rpk_net_forward_ragged(self._h, _dev_f32(x, (n, self.cin), "x"),
+                                                     len(lens), arr,
+                                                     _dev_f32(out, (n, self.cout), "out")))
+        return out
+
+    def loss_grad(self, x, target, mask):
+        nseq, length, _ = x.shape
+        loss = ctypes.c_double()
+        _check(load_library().rpk_net_loss_grad(
+            self._h, _dev_f32(x, (nseq, length, self.cin), "x"),
+            _dev_f32(target, (nseq, length, self.cout), "target"),
+            _dev_f32(mask, (nseq, length), "mask"), nseq, length, ctypes.byref(loss)))
+        return loss.value
+
+    def adam(self, lr, beta1=0.9, beta2=0.999, eps=1e-8):
+        _check(load_library().rpk_net_adam(self._h, lr, beta1, beta2, eps))

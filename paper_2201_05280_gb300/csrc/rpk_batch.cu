@@ -303,6 +303,56 @@ __global__ void k_batch_moments(const TubeDev<Real>* __restrict__ tubes, const S
   }
 }
 
+// Moment blocks (per tube [4][2 nx] floats: rho, u_x, theta_T, E_R, at float
+// offset 4 pt_off) -> the FP64 staging rows read by k_batch_init (rho, u (3
+// rows), theta_T, theta_R). theta_R = 2 E_R / (delta rho); theta_T when delta = 0.
+// Non-positive or non-finite values set bit 2 of the status word.
+template <typename Real>
+__global__ void k_state_to_stage(const TubeDev<Real>* __restrict__ tubes, const float* __restrict__ state,
+                                 int64_t n, double* __restrict__ stage, unsigned* __restrict__ status) {
+  const TubeDev<Real>* tb = tubes + blockIdx.x;
+  const int np = 2 * tb->nx;
+  const int64_t off = tb->pt_off;
+  const float* s = state + 4 * off;
+  const double delta = (double)tb->K.delta;
+  bool bad = false;
+  for (int p = threadIdx.x; p < np; p += blockDim.x) {
+    const double rho = s[p], ux = s[np + p], T = s[2 * np + p], er = s[3 * np + p];
+    const double R = delta > 0.0 ? 2.0 * er / (delta * rho) : T;
+    bad |= !(rho > 0.0) || !(T > 0.0) || !(R > 0.0) || !isfinite(rho) || !isfinite(ux) ||
+           !isfinite(T) || !isfinite(R);
+    stage[off + p] = rho;
+    stage[n + off + p] = ux;
+    stage[2 * n + off + p] = 0.0;
+    stage[3 * n + off + p] = 0.0;
+    stage[4 * n + off + p] = T;
+    stage[5 * n + off + p] = R;
+  }
+  if (bad) atomicOr(status, 4u);
+}
+
+// FP64 moment rows of k_batch_moments -> moment blocks (rho, u_x, theta_T, E_R).
+template <typename Real>
+__global__ void k_stage_to_state(const TubeDev<Real>* __restrict__ tubes, const double* __restrict__ stage,
+                                 int64_t n, float* __restrict__ state) {
+  const TubeDev<Real>* tb = tubes + blockIdx.x;
+  const int np = 2 * tb->nx;
+  const int64_t off = tb->pt_off;
+  float* s = state + 4 * off;
+  for (int p = threadIdx.x; p < np; p += blockDim.x) {
+    s[p] = (float)stage[off + p];
+    s[np + p] = (float)stage[n + off + p];
+    s[2 * np + p] = (float)stage[4 * n + off + p];
+    s[3 * np + p] = (float)stage[6 * n + off + p];
+  }
+}
+
+template <typename Real>
+__global__ void k_set_steps(TubeDev<Real>* __restrict__ tubes, const int* __restrict__ nsteps, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) tubes[i].nsteps = nsteps[i];
+}
+
 }  // namespace rpk
 
 using namespace rpk;
@@ -325,6 +375,10 @@ struct rpk_batch {
   float* snaps = nullptr;
   unsigned* status = nullptr;
   double* stage = nullptr;  // 7 x total_pts doubles, for init and reads
+  double* res_dev = nullptr;  // 12 reservoir values per tube
+  int* steps_dev = nullptr;   // per-tube step counts for rpk_batch_set_steps
+  std::vector<int> max_steps; // step counts given at creation (bound the snapshot storage)
+  bool nsub_ok = false;       // every tube's FTCS sub-step count is resolved
   bool init_ok = false;
   int threads = 256, ctas_per_sm = 1;
   cudaGraphExec_t graph = nullptr;
@@ -361,7 +415,7 @@ rpk_status with_batch_types(int precision, F&& f) {
 void free_batch(rpk_batch* B) {
   if (B->graph) cudaGraphExecDestroy(B->graph);
   void* ptrs[] = {B->pop[0], B->pop[1], B->e_state, B->ux_state, B->tubes_dev, B->order_dev,
-                  B->counter, B->snaps, B->status, B->stage};
+                  B->counter, B->snaps,  B->status, B->stage,    B->res_dev,   B->steps_dev};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -374,6 +428,21 @@ rpk_status dev_alloc(void** p, size_t bytes) {
     return fail(err == cudaErrorMemoryAllocation ? RPK_ERR_OOM : RPK_ERR_CUDA,
                 std::string("batch allocation failed: ") + cudaGetErrorString(err));
   }
+  return RPK_OK;
+}
+
+// Work order of the queue: longest work first (collide work ~ points x steps,
+// diffusion ~ points x steps x nsub).
+rpk_status upload_order(rpk_batch* B) {
+  std::vector<int> order(B->ntubes);
+  for (int i = 0; i < B->ntubes; ++i) order[i] = i;
+  std::vector<double> work(B->ntubes);
+  for (int i = 0; i < B->ntubes; ++i)
+    work[i] = 2.0 * B->tubes[i].nx * B->tubes[i].nsteps * (8.0 + B->nsub[i]);
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return work[a] > work[b]; });
+  RPK_CUDA(cudaMemcpyAsync(B->order_dev, order.data(), sizeof(int) * B->ntubes,
+                           cudaMemcpyHostToDevice, B->stream));
+  RPK_CUDA(cudaStreamSynchronize(B->stream));
   return RPK_OK;
 }
 
@@ -398,19 +467,10 @@ rpk_status upload_tubes(rpk_batch* B) {
     d.snap_off = B->snap_off[i];
     pop_off += (int64_t)2 * kQ * t.nx;
   }
-  // longest work first: collide work ~ points x steps, diffusion ~ points x steps x nsub
-  std::vector<int> order(B->ntubes);
-  for (int i = 0; i < B->ntubes; ++i) order[i] = i;
-  std::vector<double> work(B->ntubes);
-  for (int i = 0; i < B->ntubes; ++i)
-    work[i] = 2.0 * B->tubes[i].nx * B->tubes[i].nsteps * (8.0 + B->nsub[i]);
-  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return work[a] > work[b]; });
   RPK_CUDA(cudaMemcpyAsync(B->tubes_dev, td.data(), sizeof(TubeDev<Real>) * B->ntubes,
                            cudaMemcpyHostToDevice, B->stream));
-  RPK_CUDA(cudaMemcpyAsync(B->order_dev, order.data(), sizeof(int) * B->ntubes,
-                           cudaMemcpyHostToDevice, B->stream));
   RPK_CUDA(cudaStreamSynchronize(B->stream));
-  return RPK_OK;
+  return upload_order(B);
 }
 
 // Shared-memory limit of the kernel variant (outside any stream capture).
@@ -450,6 +510,36 @@ rpk_status launch_batch(rpk_batch* B, cudaStream_t stream, int threads, int ctas
 #undef RPK_LAUNCH
   }
   RPK_CUDA(cudaGetLastError());
+  return RPK_OK;
+}
+
+// Tube descriptors, then the initial state from the staging rows (filled from
+// host fields before the call, or from device moment blocks here).
+rpk_status init_from_stage(rpk_batch* B, const float* state) {
+  const int64_t n = B->total_pts;
+  double* s = B->stage;
+  rpk_status st = with_batch_types(B->precision, [&](auto ops, auto* real_tag) {
+    using Real = std::remove_pointer_t<decltype(real_tag)>;
+    return upload_tubes<Real>(B);
+  });
+  if (st != RPK_OK) return st;
+  RPK_CUDA(cudaMemsetAsync(B->status, 0, sizeof(unsigned), B->stream));
+  if (B->precision == RPK_F64) {
+    auto* td = static_cast<TubeDev<double>*>(B->tubes_dev);
+    if (state) k_state_to_stage<double><<<B->ntubes, 256, 0, B->stream>>>(td, state, n, s, B->status);
+    k_batch_init<double, double><<<B->ntubes, 256, 0, B->stream>>>(
+        td, s, s + n, s + 4 * n, s + 5 * n, n, B->res_dev, static_cast<double*>(B->pop[0]),
+        static_cast<double*>(B->e_state), static_cast<double*>(B->ux_state));
+  } else {
+    auto* td = static_cast<TubeDev<float>*>(B->tubes_dev);
+    if (state) k_state_to_stage<float><<<B->ntubes, 256, 0, B->stream>>>(td, state, n, s, B->status);
+    k_batch_init<float, float><<<B->ntubes, 256, 0, B->stream>>>(
+        td, s, s + n, s + 4 * n, s + 5 * n, n, B->res_dev, static_cast<float*>(B->pop[0]),
+        static_cast<float*>(B->e_state), static_cast<float*>(B->ux_state));
+  }
+  RPK_CUDA(cudaGetLastError());
+  RPK_CUDA(cudaStreamSynchronize(B->stream));
+  B->init_ok = true;
   return RPK_OK;
 }
 
@@ -528,10 +618,29 @@ rpk_status rpk_batch_create(int precision, int ntubes, const rpk_tube* tubes, in
   if (st == RPK_OK) st = dev_alloc((void**)&B->snaps, std::max<int64_t>(1, B->snap_floats) * sizeof(float));
   if (st == RPK_OK) st = dev_alloc((void**)&B->status, sizeof(unsigned));
   if (st == RPK_OK) st = dev_alloc((void**)&B->stage, sizeof(double) * 7 * B->total_pts);
+  if (st == RPK_OK) st = dev_alloc((void**)&B->res_dev, sizeof(double) * 12 * ntubes);
+  if (st == RPK_OK) st = dev_alloc((void**)&B->steps_dev, sizeof(int) * ntubes);
+  if (st == RPK_OK) {
+    std::vector<double> res(12 * (size_t)ntubes);
+    for (int i = 0; i < ntubes; ++i) std::memcpy(&res[12 * (size_t)i], tubes[i].res, 12 * sizeof(double));
+    cudaError_t e = cudaMemcpyAsync(B->res_dev, res.data(), res.size() * sizeof(double),
+                                    cudaMemcpyHostToDevice, B->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(B->stream);
+    if (e != cudaSuccess) st = cuda_fail(e, "rpk_batch_create");
+  }
   if (st != RPK_OK) {
     free_batch(B);
     delete B;
     return st;
+  }
+  B->max_steps.resize(ntubes);
+  B->nsub_ok = true;
+  for (int i = 0; i < ntubes; ++i) {
+    B->max_steps[i] = tubes[i].nsteps;
+    if (tubes[i].relax.nsub > 0)
+      B->nsub[i] = tubes[i].relax.nsub;
+    else
+      B->nsub_ok = false;
   }
   *out = B;
   return RPK_OK;
@@ -570,41 +679,65 @@ rpk_status rpk_batch_init(rpk_batch* B, const double* rho, const double* u, cons
                                 (3.0 + t.relax.delta));
     B->nsub[i] = rpk_auto_nsub(&t.relax, tmax, 1);
   }
-  rpk_status st = with_batch_types(B->precision, [&](auto ops, auto* real_tag) {
-    using Real = std::remove_pointer_t<decltype(real_tag)>;
-    return upload_tubes<Real>(B);
-  });
-  if (st != RPK_OK) return st;
-  std::vector<double> res(12 * (size_t)B->ntubes);
-  for (int i = 0; i < B->ntubes; ++i) std::memcpy(&res[12 * (size_t)i], B->tubes[i].res, 12 * sizeof(double));
+  B->nsub_ok = true;
   double* s = B->stage;
   RPK_CUDA(cudaMemcpyAsync(s, rho, n * sizeof(double), cudaMemcpyHostToDevice, B->stream));
   RPK_CUDA(cudaMemcpyAsync(s + n, u, 3 * n * sizeof(double), cudaMemcpyHostToDevice, B->stream));
   RPK_CUDA(cudaMemcpyAsync(s + 4 * n, T, n * sizeof(double), cudaMemcpyHostToDevice, B->stream));
   RPK_CUDA(cudaMemcpyAsync(s + 5 * n, R, n * sizeof(double), cudaMemcpyHostToDevice, B->stream));
-  double* dres = nullptr;
-  st = dev_alloc((void**)&dres, res.size() * sizeof(double));
-  if (st != RPK_OK) return st;
-  cudaError_t err = cudaMemcpyAsync(dres, res.data(), res.size() * sizeof(double),
-                                    cudaMemcpyHostToDevice, B->stream);
-  if (err == cudaSuccess) {
-    if (B->precision == RPK_F64)
-      k_batch_init<double, double><<<B->ntubes, 256, 0, B->stream>>>(
-          static_cast<TubeDev<double>*>(B->tubes_dev), s, s + n, s + 4 * n, s + 5 * n, n, dres,
-          static_cast<double*>(B->pop[0]), static_cast<double*>(B->e_state),
-          static_cast<double*>(B->ux_state));
-    else
-      k_batch_init<float, float><<<B->ntubes, 256, 0, B->stream>>>(
-          static_cast<TubeDev<float>*>(B->tubes_dev), s, s + n, s + 4 * n, s + 5 * n, n, dres,
-          static_cast<float*>(B->pop[0]), static_cast<float*>(B->e_state),
-          static_cast<float*>(B->ux_state));
-    err = cudaGetLastError();
+  return init_from_stage(B, nullptr);
+}
+
+rpk_status rpk_batch_init_device(rpk_batch* B, const float* state) {
+  if (!B || !state) return fail(RPK_ERR_ARG, "NULL argument");
+  if (!B->nsub_ok)
+    return fail(RPK_ERR_STATE, "FTCS sub-step counts unresolved: give relax.nsub > 0 for every "
+                               "tube or initialise once from host fields");
+  RPK_CUDA(cudaSetDevice(B->device));
+  return init_from_stage(B, state);
+}
+
+rpk_status rpk_batch_set_steps(rpk_batch* B, const int* nsteps) {
+  if (!B || !nsteps) return fail(RPK_ERR_ARG, "NULL argument");
+  for (int i = 0; i < B->ntubes; ++i)
+    if (nsteps[i] < 0 || nsteps[i] > B->max_steps[i])
+      return fail(RPK_ERR_ARG, "tube " + std::to_string(i) + ": nsteps must lie in [0, " +
+                                   std::to_string(B->max_steps[i]) + "] (its count at creation)");
+  RPK_CUDA(cudaSetDevice(B->device));
+  for (int i = 0; i < B->ntubes; ++i) B->tubes[i].nsteps = nsteps[i];
+  if (!B->init_ok) return RPK_OK;  // uploaded with the tube descriptors at initialisation
+  RPK_CUDA(cudaMemcpyAsync(B->steps_dev, nsteps, sizeof(int) * B->ntubes, cudaMemcpyHostToDevice,
+                           B->stream));
+  const int blocks = (B->ntubes + 255) / 256;
+  if (B->precision == RPK_F64)
+    k_set_steps<double><<<blocks, 256, 0, B->stream>>>(static_cast<TubeDev<double>*>(B->tubes_dev),
+                                                        B->steps_dev, B->ntubes);
+  else
+    k_set_steps<float><<<blocks, 256, 0, B->stream>>>(static_cast<TubeDev<float>*>(B->tubes_dev),
+                                                       B->steps_dev, B->ntubes);
+  RPK_CUDA(cudaGetLastError());
+  return upload_order(B);  // synchronises the stream
+}
+
+rpk_status rpk_batch_moments_device(rpk_batch* B, float* state) {
+  if (!B || !state) return fail(RPK_ERR_ARG, "NULL argument");
+  if (!B->init_ok) return fail(RPK_ERR_STATE, "initialise the batch first");
+  RPK_CUDA(cudaSetDevice(B->device));
+  const int64_t n = B->total_pts;
+  if (B->precision == RPK_F64) {
+    const auto* td = static_cast<const TubeDev<double>*>(B->tubes_dev);
+    k_batch_moments<double, double><<<B->ntubes, 256, 0, B->stream>>>(
+        td, static_cast<const double*>(B->pop[0]), static_cast<const double*>(B->pop[1]),
+        static_cast<const double*>(B->e_state), n, B->stage);
+    k_stage_to_state<double><<<B->ntubes, 256, 0, B->stream>>>(td, B->stage, n, state);
+  } else {
+    const auto* td = static_cast<const TubeDev<float>*>(B->tubes_dev);
+    k_batch_moments<float, float><<<B->ntubes, 256, 0, B->stream>>>(
+        td, static_cast<const float*>(B->pop[0]), static_cast<const float*>(B->pop[1]),
+        static_cast<const float*>(B->e_state), n, B->stage);
+    k_stage_to_state<float><<<B->ntubes, 256, 0, B->stream>>>(td, B->stage, n, state);
   }
-  if (err == cudaSuccess) err = cudaMemsetAsync(B->status, 0, sizeof(unsigned), B->stream);
-  if (err == cudaSuccess) err = cudaStreamSynchronize(B->stream);
-  cudaFree(dres);
-  if (err != cudaSuccess) return cuda_fail(err, "rpk_batch_init");
-  B->init_ok = true;
+  RPK_CUDA(cudaGetLastError());
   return RPK_OK;
 }
 

@@ -1,0 +1,146 @@
+"""GPU parity of the surrogate network kernels (rpk_net_*) against the FP64
+numpy network of the oracle.
+
+Two bars. Against the oracle evaluated with BF16-rounded contraction operands
+(the tensor cores' input rounding) the GPU differs only by FP32 accumulation
+and FP32 storage of activations. Those differ from FP64 by ~sqrt(K) 2^-24
+~ 1.5e-6 relative (K <= 640 terms), which flips the BF16 rounding of a
+fraction ~1.5e-6 / 2^-9 ~ 1e-3 of the operands by one BF16 step (2^-8), a
+relative L2 change of ~sqrt(1e-3) 2^-8 ~ 1e-4 per contraction: the forward
+pass (up to 6 contractions in series) is held to 1e-3, the gradients (up to
+11 in series, the last ones fed by all earlier ones) to 3e-3. Against the exact
+FP64 network the BF16 rounding itself (2^-9 relative per operand, amplified
+where a contraction cancels) is measured at up to 1e-2 on outputs and 3e-2 on
+the deepest gradient (the lift weights); the bars are 3e-2 and 6e-2. Sizes span
+several 64 x 64 tiles with ragged tails in positions, channels and the
+reduction dimension (5 taps x 80 channels = 400 = 12.5 k-tiles)."""
+import numpy as np
+import pytest
+
+from oracle import surrogate as S
+import paper_2201_05280_gb300 as rpk
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    from paper_2201_05280_gb300 import build as B
+    B.build()
+    import torch
+    assert torch.cuda.is_available()
+    torch.cuda.set_device(0)
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(np.ravel(a) - np.ravel(b)) / max(np.linalg.norm(np.ravel(b)), 1e-300))
+
+
+def _case(cin, cout, width, nb, nseq, L, seed):
+    import torch
+    rng = np.random.default_rng(seed)
+    p = S.init_params(cin, cout, width, nb, seed=seed)
+    for k in p:
+        if "_b" in k:
+            p[k] = rng.normal(0, 0.1, p[k].shape)
+    v = S.flatten(p, nb).astype(np.float32)
+    p = S.unflatten(v.astype(np.float64), cin, cout, width, nb)  # the float32 values the GPU holds
+    x = rng.normal(size=(nseq, L, cin)).astype(np.float32)
+    target = rng.normal(size=(nseq, L, cout)).astype(np.float32)
+    mask = (rng.uniform(size=(nseq, L)) > 0.25).astype(np.float32)
+    net = rpk.Net(cin, cout, width, nb, seed=1)
+    net.set_params(v)
+    dev = lambda a: torch.tensor(a, device="cuda")
+    return net, p, x, target, mask, dev
+
+
+@pytest.mark.parametrize("cin,cout,width,nb,nseq,L", [(3, 2, 80, 2, 5, 212), (7, 4, 128, 1, 2, 1024),
+                                                      (2, 1, 16, 0, 1, 4)])
+def test_forward_matches_oracle(cin, cout, width, nb, nseq, L):
+    net, p, x, _, _, dev = _case(cin, cout, width, nb, nseq, L, seed=11)
+    y = net.forward(dev(x)).cpu().numpy()
+    ref_b, _ = S.forward(p, x.astype(np.float64), nb, cout, S.bf16)
+    ref, _ = S.forward(p, x.astype(np.float64), nb, cout)
+    assert y.shape == ref.shape
+    assert _rel(y, ref_b) <= 1e-3, _rel(y, ref_b)
+    assert _rel(y, ref) <= 3e-2, _rel(y, ref)
+    net.close()
+
+
+@pytest.mark.parametrize("cin,cout,width,nb,nseq,L", [(3, 2, 80, 2, 5, 212), (7, 4, 128, 2, 3, 512)])
+def test_gradients_match_oracle(cin, cout, width, nb, nseq, L):
+    net, p, x, target, mask, dev = _case(cin, cout, width, nb, nseq, L, seed=12)
+    loss = net.loss_grad(dev(x), dev(target), dev(mask))
+    g = S.unflatten(net.params(grads=True).astype(np.float64), cin, cout, width, nb)
+    args = (p, x.astype(np.float64), target.astype(np.float64), mask.astype(np.float64), nb, cout)
+    loss_b, gb, _ = S.loss_and_grad(*args, rnd=S.bf16)
+    loss_e, ge, _ = S.loss_and_grad(*args)
+    assert abs(loss - loss_b) <= 1e-4 * loss_b
+    assert abs(loss - loss_e) <= 1e-2 * loss_e
+    for k in gb:
+        assert _rel(g[k], gb[k]) <= 3e-3, (k, _rel(g[k], gb[k]))
+        assert _rel(g[k], ge[k]) <= 6e-2, (k, _rel(g[k], ge[k]))
+    net.close()
+
+
+def test_ragged_forward_matches_per_sequence_oracle():
+    import torch
+    cin, cout, width, nb = 7, 4, 64, 2
+    lens = [4, 260, 1024, 36, 508]
+    net, p, x, _, _, dev = _case(cin, cout, width, nb, 1, sum(lens), seed=15)
+    y = net.forward_ragged(dev(x[0]), lens).cpu().numpy()
+    off = 0
+    for L in lens:
+        ref, _ = S.forward(p, x[:, off:off + L].astype(np.float64), nb, cout, S.bf16)
+        assert _rel(y[off:off + L], ref[0]) <= 1e-3, (L, _rel(y[off:off + L], ref[0]))
+        off += L
+    with pytest.raises(rpk.RpkError):
+        net.forward_ragged(dev(x[0]), [6, sum(lens) - 6])
+    net.close()
+
+
+def test_adam_step_matches_oracle():
+    cin, cout, width, nb = 3, 2, 32, 1
+    net, p, x, target, mask, dev = _case(cin, cout, width, nb, 2, 128, seed=13)
+    m = {k: np.zeros_like(a) for k, a in p.items()}
+    v = {k: np.zeros_like(a) for k, a in p.items()}
+    for step in range(1, 4):
+        net.loss_grad(dev(x), dev(target), dev(mask))
+        g = S.unflatten(net.params(grads=True).astype(np.float64), cin, cout, width, nb)
+        net.adam(1e-3)
+        S.adam(p, g, m, v, step, 1e-3)
+        got = S.unflatten(net.params().astype(np.float64), cin, cout, width, nb)
+        for k in p:
+            np.testing.assert_allclose(got[k], p[k], rtol=0, atol=1e-6 * max(1.0, np.abs(p[k]).max()))
+        p = got  # continue from the float32 parameters
+    net.close()
+
+
+def test_training_reduces_the_loss():
+    """A small regression (a smoothed shift of the input) learned by the GPU's own
+    forward, backward and Adam: the loss falls by more than 10x."""
+    import torch
+    rng = np.random.default_rng(14)
+    net = rpk.Net(2, 2, 32, 2, seed=3)
+    x = rng.normal(size=(8, 256, 2)).astype(np.float32)
+    t = 0.5 * (np.roll(x, 3, axis=1) + np.roll(x, -2, axis=1))
+    xd, td = torch.tensor(x, device="cuda"), torch.tensor(t, device="cuda")
+    md = torch.ones((8, 256), device="cuda")
+    first = net.loss_grad(xd, td, md)
+    for _ in range(300):
+        loss = net.loss_grad(xd, td, md)
+        net.adam(3e-3)
+    assert np.isfinite(loss) and loss < first / 10, (first, loss)
+    net.close()
+
+
+def test_argument_errors():
+    import torch
+    with pytest.raises(rpk.RpkError):
+        rpk.Net(3, 2, 20, 1)  # width not a multiple of 16
+    net = rpk.Net(3, 2, 32, 1)
+    with pytest.raises(rpk.RpkError):
+        net.forward(torch.zeros((2, 10, 3), device="cuda"))  # length not a multiple of 4
+    with pytest.raises(ValueError):
+        net.set_params(np.zeros(5, dtype=np.float32))
+    net.close()
