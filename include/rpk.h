@@ -296,6 +296,82 @@ rpk_status rpk_net_loss_grad(rpk_net* net, const float* x, const float* target,
 /* One Adam step (bias-corrected) with the stored gradients. Asynchronous. */
 rpk_status rpk_net_adam(rpk_net* net, float lr, float beta1, float beta2, float eps);
 
+/* ---- Surrogate rollout of batched tubes with LBM fallback -----------------
+ * (the paper has no learned component). The network maps the moments of a
+ * tube at step t to the increments of its conserved densities over `jump`
+ * steps: inputs per fine point (position 2x + s of point (s, x)) are 7
+ * features -- (rho, u_x, theta_T, E_R) shifted and scaled, two per-tube
+ * conditioning values, and 1 inside the tube / 0 in the reservoir padding --
+ * and outputs are 4 scaled increments of U = (rho, rho u_x,
+ * E = rho u_x^2 / 2 + 3 rho theta_T / 2 + E_R, E_R). */
+typedef struct {
+  int jump;            /* LBM steps one network application stands for (e.g. 32) */
+  int pad;             /* reservoir points each side of a tube in its sequence, >= 0 */
+  int spot_every;      /* spot check at windows 0, spot_every, 2 spot_every, ...; 0: none */
+  int project;         /* 1: rescale the mass and energy increments to zero net change */
+  double drift_tol;    /* relative mass or energy drift that hands a tube to the LBM */
+  double l1_tol;       /* estimated relative L1 density error that hands a tube to the LBM */
+  float in_shift[4];   /* feature k = (v_k - in_shift[k]) / in_scale[k], v = (rho, u_x, theta_T, E_R) */
+  float in_scale[4];
+  float out_scale[4];  /* increment of U_k = out_scale[k] * network output k */
+  int lbm_threads;     /* launch configuration of the LBM arm (rpk_batch_set_config) */
+  int lbm_ctas_per_sm;
+} rpk_sur_config;
+
+/* One sequence of network input: the padded tube, from padded position `crop`
+ * on, `len` points (a multiple of 4) written at point `out` of x / target /
+ * mask. Padded position c holds tube position c - pad when that lies in
+ * [0, 2 nx), else the left (c < pad) or right reservoir state. */
+typedef struct {
+  int64_t src;         /* float offset of the source moment block [4][2 nx] */
+  int64_t tgt;         /* float offset of the target moment block, or -1 (no target) */
+  int64_t out;         /* first point of the sequence in x, target and mask */
+  int nx, len, crop, pad_;
+  float res[2][4];     /* reservoir (rho, u_x, theta_T, E_R), left then right */
+  float cond[2];       /* conditioning features */
+} rpk_sur_seq;
+
+/* Network inputs (and, where tgt >= 0, normalised target increments
+ * (U_k(target) - U_k(source)) / out_scale[k] and a mask that is 1 at tube
+ * points at least `margin` points from both ends of the sequence) for nseq
+ * sequences; store and seqs are device pointers, maxlen bounds every len.
+ * x [..][7], target [..][4], mask [..] (target and mask may be NULL when no
+ * sequence has a target). Asynchronous on cuda_stream. */
+rpk_status rpk_sur_pack(const rpk_sur_config* cfg, const float* store, const rpk_sur_seq* seqs,
+                        int nseq, int maxlen, int margin, float* x, float* target, float* mask,
+                        void* cuda_stream);
+
+/* Moment blocks after one network application: for every tube of `seqs`
+ * (device, nseq entries, src = the tube's block in `state`, out = its
+ * sequence's first point in y), next[src..] = moments of U + increments,
+ * with the projection of cfg->project; flags[i] = 1 where a result is
+ * non-positive or non-finite; totals[2 i] = sum rho, totals[2 i + 1] = sum E
+ * over the tube (FP64). Device pointers; asynchronous. */
+rpk_status rpk_sur_apply(const rpk_sur_config* cfg, const float* state, const float* y,
+                         const rpk_sur_seq* seqs, int nseq, float* next, int* flags,
+                         double* totals, void* cuda_stream);
+
+typedef struct rpk_rollout rpk_rollout;
+/* A rollout engine for ntubes tubes (every relax.nsub > 0): the network `net`
+ * (not owned), per-tube conditioning cond[2 i], cond[2 i + 1] (host), and an
+ * internal FP32 batch of the same tubes for spot checks and fallback. */
+rpk_status rpk_rollout_create(rpk_net* net, const rpk_sur_config* cfg, int ntubes,
+                              const rpk_tube* tubes, const float* cond, void* cuda_stream,
+                              rpk_rollout** out);
+void rpk_rollout_destroy(rpk_rollout* r);
+/* Advance every tube by its nsteps from the moment blocks `state` (device,
+ * updated in place): floor(nsteps / jump) windows by the network, except that
+ * spot-check windows run on the LBM (whose result is kept) and compare the
+ * network's density with it; a tube whose mass or energy drift exceeds
+ * drift_tol, whose result is invalid, or whose estimated accumulated L1 error
+ * exceeds l1_tol finishes on the LBM from its last accepted state; remainders
+ * (nsteps mod jump) run on the LBM. stats (host, 4 per tube, may be NULL):
+ * step at which the LBM took over (-1: never), network windows kept, spot
+ * checks, LBM steps after the windows; est (host, per tube, may be NULL): the
+ * estimated L1 error; ms (host, 3, may be NULL): device time of the network
+ * windows, the spot checks and the final LBM run. Synchronises. */
+rpk_status rpk_rollout_run(rpk_rollout* r, float* state, int64_t* stats, double* est, double* ms);
+
 /* Conserved totals of hydrodynamic fields held by the caller in device memory,
  * computed without allocating anything. The paper has no counterpart; this is
  * for callers that cannot call cudaMalloc where they need the totals (a loop

@@ -186,3 +186,81 @@ def adam(p, g, m, v, step, lr, beta1=0.9, beta2=0.999, eps=1e-8):
         v[k] = beta2 * v[k] + (1.0 - beta2) * g[k] ** 2
         p[k] = p[k] - lr * (m[k] / c1) / (np.sqrt(v[k] / c2) + eps)
     return p
+
+
+# ---- moment blocks, network inputs and the conservative update ---------------
+# A tube of nx cells per sublattice has 2 nx points; point (s, x) has index
+# s nx + x and fine position 2x + s. A moment block is [4][2 nx]: rho, u_x,
+# theta_T, E_R. Conserved densities U = (rho, rho u_x, E, E_R) with
+# E = rho u_x^2 / 2 + 3 rho theta_T / 2 + E_R (translational energy of three
+# degrees of freedom plus the rotational energy density).
+
+def conserved(v):
+    """v (4, ...) = (rho, u_x, theta_T, E_R) -> U (4, ...)."""
+    rho, ux, th, er = v
+    return np.stack([rho, rho * ux, 0.5 * rho * ux ** 2 + 1.5 * rho * th + er, er])
+
+
+def primitive(U):
+    """Inverse of conserved."""
+    rho, m, E, er = U
+    ux = m / rho
+    return np.stack([rho, ux, (E - 0.5 * m * ux - er) / (1.5 * rho), er])
+
+
+def position_order(block, nx):
+    """[4][2 nx] in point order -> [4][2 nx] in fine-position order 2x + s."""
+    out = np.empty_like(block)
+    out[:, 0::2] = block[:, :nx]
+    out[:, 1::2] = block[:, nx:]
+    return out
+
+
+def point_order(seq, nx):
+    """Inverse of position_order."""
+    out = np.empty_like(seq)
+    out[:, :nx] = seq[:, 0::2]
+    out[:, nx:] = seq[:, 1::2]
+    return out
+
+
+def pack(src, tgt, nx, res, cond, pad, crop, length, margin, shift, scale, out_scale):
+    """Network input x (length, 7) of one padded tube, and (when tgt is not None)
+    the normalised target increments (length, 4) and the loss mask (length,).
+    res (2, 4): left / right reservoir (rho, u_x, theta_T, E_R)."""
+    shift, scale = np.asarray(shift, np.float32), np.asarray(scale, np.float32)
+    s = position_order(np.asarray(src, np.float64), nx)
+    t = position_order(np.asarray(tgt, np.float64), nx) if tgt is not None else None
+    x = np.zeros((length, 7), np.float32)
+    target = np.zeros((length, 4))
+    mask = np.zeros(length)
+    for l in range(length):
+        p = crop + l - pad
+        inside = 0 <= p < 2 * nx
+        v = s[:, p] if inside else np.asarray(res[0 if p < 0 else 1], np.float64)
+        x[l, :4] = (v.astype(np.float32) - shift) / scale
+        x[l, 4:6] = cond
+        x[l, 6] = 1.0 if inside else 0.0
+        if t is not None and inside and margin <= l < length - margin:
+            target[l] = (conserved(t[:, p]) - conserved(v)) / np.asarray(out_scale, np.float64)
+            mask[l] = 1.0
+    return x, target, mask
+
+
+def apply(block, y, nx, pad, crop, out_scale, project):
+    """Moment block after one network application: increments out_scale * y at
+    the tube's positions (y (length, 4) of its sequence); with ``project`` the
+    mass and energy increments d are replaced by d - |d| sum(d) / sum(|d|)
+    (zero net change, the correction put where the change is). Returns
+    (new block, invalid, (sum rho, sum E))."""
+    v = position_order(np.asarray(block, np.float64), nx)
+    d = (np.asarray(y, np.float64)[pad - crop:pad - crop + 2 * nx] * np.asarray(out_scale, np.float64)).T
+    if project:
+        for k in (0, 2):
+            a = np.abs(d[k]).sum()
+            if a > 0:
+                d[k] = d[k] - np.abs(d[k]) * (d[k].sum() / a)
+    U = conserved(v) + d
+    w = primitive(U)
+    bad = bool(np.any(~np.isfinite(w)) or np.any(w[0] <= 0) or np.any(w[2] <= 0) or np.any(w[3] <= 0))
+    return point_order(w, nx), bad, (float(U[0].sum()), float(U[2].sum()))

@@ -17,7 +17,8 @@ import os
 import numpy as np
 
 __all__ = ["Lattice", "RpkError", "load_library", "theta0", "map_gas", "auto_nsub",
-           "gas_from_nondim", "field_totals_noalloc", "Batch", "Net", "PRECISIONS", "library_path"]
+           "gas_from_nondim", "field_totals_noalloc", "Batch", "Net", "Rollout", "SurConfig", "SurSeq",
+           "sur_pack", "sur_apply", "PRECISIONS", "library_path"]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB_PATH = os.path.join(_HERE, "librpk.so")
@@ -51,6 +52,36 @@ class Relax(ctypes.Structure):
 class Tube(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int), ("nsteps", ctypes.c_int), ("relax", Relax),
                 ("res", ctypes.c_double * 12)]
+
+
+class SurConfig(ctypes.Structure):
+    _fields_ = [("jump", ctypes.c_int), ("pad", ctypes.c_int), ("spot_every", ctypes.c_int),
+                ("project", ctypes.c_int), ("drift_tol", ctypes.c_double),
+                ("l1_tol", ctypes.c_double), ("in_shift", ctypes.c_float * 4),
+                ("in_scale", ctypes.c_float * 4), ("out_scale", ctypes.c_float * 4),
+                ("lbm_threads", ctypes.c_int), ("lbm_ctas_per_sm", ctypes.c_int)]
+
+    @classmethod
+    def make(cls, **kw):
+        c = cls()
+        c.jump, c.pad, c.spot_every, c.project = 32, 128, 8, 1
+        c.drift_tol, c.l1_tol = 1e-4, 1e-2
+        for k in range(4):
+            c.in_scale[k] = c.out_scale[k] = 1.0
+        for k, v in kw.items():
+            if k in ("in_shift", "in_scale", "out_scale"):
+                for i in range(4):
+                    getattr(c, k)[i] = float(v[i])
+            else:
+                setattr(c, k, v)
+        return c
+
+
+class SurSeq(ctypes.Structure):
+    _fields_ = [("src", ctypes.c_int64), ("tgt", ctypes.c_int64), ("out", ctypes.c_int64),
+                ("nx", ctypes.c_int), ("len", ctypes.c_int), ("crop", ctypes.c_int),
+                ("pad_", ctypes.c_int), ("res", (ctypes.c_float * 4) * 2),
+                ("cond", ctypes.c_float * 2)]
 
 
 class Diag(ctypes.Structure):
@@ -109,6 +140,15 @@ def load_library(path=None):
         "rpk_batch_run": (i, [vp]),
         "rpk_batch_read_moments": (i, [vp, vp, vp, vp, vp, vp]),
         "rpk_batch_snapshots": (i, [vp, vp, ctypes.POINTER(i64)]),
+        "rpk_batch_init_device": (i, [vp, vp]),
+        "rpk_batch_set_steps": (i, [vp, ctypes.POINTER(i)]),
+        "rpk_batch_moments_device": (i, [vp, vp]),
+        "rpk_sur_pack": (i, [ctypes.POINTER(SurConfig), vp, vp, i, i, i, vp, vp, vp, vp]),
+        "rpk_sur_apply": (i, [ctypes.POINTER(SurConfig), vp, vp, vp, i, vp, vp, vp, vp]),
+        "rpk_rollout_create": (i, [vp, ctypes.POINTER(SurConfig), i, ctypes.POINTER(Tube),
+                                   ctypes.POINTER(ctypes.c_float), vp, ctypes.POINTER(vp)]),
+        "rpk_rollout_destroy": (None, [vp]),
+        "rpk_rollout_run": (i, [vp, vp, ctypes.POINTER(i64), ctypes.POINTER(d), ctypes.POINTER(d)]),
         "rpk_net_create": (i, [i, i, i, i, ctypes.c_uint64, vp, ctypes.POINTER(vp)]),
         "rpk_net_destroy": (None, [vp]),
         "rpk_net_num_params": (i64, [vp]),
@@ -390,6 +430,29 @@ class Batch:
             _check(code)
         return out
 
+    @property
+    def block_offsets(self):
+        """Float offset of each tube's moment block [4][2 nx] (8 nx floats per tube)."""
+        return 4 * self.offsets[:-1]
+
+    def init_device(self, state):
+        """Initialise from moment blocks (CUDA float32 tensor of 4 * total_pts)."""
+        _check(load_library().rpk_batch_init_device(self._h, _dev_f32(state, (4 * self.total_pts,), "state")))
+        return self
+
+    def set_steps(self, nsteps):
+        arr = (ctypes.c_int * len(self.tubes))(*[int(v) for v in nsteps])
+        _check(load_library().rpk_batch_set_steps(self._h, arr))
+        return self
+
+    def moments_device(self, out=None):
+        """Current moments as moment blocks (CUDA float32 tensor of 4 * total_pts)."""
+        import torch
+        if out is None:
+            out = torch.empty(4 * self.total_pts, device="cuda", dtype=torch.float32)
+        _check(load_library().rpk_batch_moments_device(self._h, _dev_f32(out, (4 * self.total_pts,), "out")))
+        return out
+
     def snapshots(self):
         """List per tube of float32 arrays (nsnap, 4, 2 nx): rho, u_x, theta_T, E_R at
         steps 0, save_every, ... of the last run."""
@@ -493,3 +556,114 @@ class Net:
 
     def adam(self, lr, beta1=0.9, beta2=0.999, eps=1e-8):
         _check(load_library().rpk_net_adam(self._h, lr, beta1, beta2, eps))
+
+
+def _seq_array(seqs):
+    """Sequence descriptors (dicts with src, tgt, out, nx, len, crop, res (2x4),
+    cond (2)) -> a CUDA uint8 tensor holding the rpk_sur_seq array."""
+    import torch
+    arr = (SurSeq * len(seqs))()
+    for a, d in zip(arr, seqs):
+        a.src, a.tgt, a.out = int(d["src"]), int(d.get("tgt", -1)), int(d["out"])
+        a.nx, a.len, a.crop = int(d["nx"]), int(d["len"]), int(d.get("crop", 0))
+        for side in range(2):
+            for k in range(4):
+                a.res[side][k] = float(d["res"][side][k])
+        a.cond[0], a.cond[1] = float(d["cond"][0]), float(d["cond"][1])
+    raw = np.frombuffer(bytes(arr), dtype=np.uint8).copy()
+    return torch.from_numpy(raw).cuda()
+
+
+def sur_pack(cfg, store, seqs, margin=0, x=None, target=None, mask=None, stream=None):
+    """Network inputs (and targets / mask when sequences carry tgt >= 0) for
+    the sequences; returns (x, target, mask) as CUDA float32 tensors."""
+    import torch
+    total = max(int(d["out"]) + int(d["len"]) for d in seqs)
+    maxlen = max(int(d["len"]) for d in seqs)
+    with_t = any(int(d.get("tgt", -1)) >= 0 for d in seqs)
+    if x is None:
+        x = torch.zeros((total, 7), device="cuda", dtype=torch.float32)
+    if with_t and target is None:
+        target = torch.zeros((total, 4), device="cuda", dtype=torch.float32)
+    if with_t and mask is None:
+        mask = torch.zeros(total, device="cuda", dtype=torch.float32)
+    dseq = _seq_array(seqs)
+    vp = ctypes.c_void_p
+    _check(load_library().rpk_sur_pack(
+        ctypes.byref(cfg), _dev_f32(store, name="store"), vp(dseq.data_ptr()), len(seqs), maxlen,
+        int(margin), _dev_f32(x, name="x"), _dev_f32(target, name="target") if with_t else None,
+        _dev_f32(mask, name="mask") if with_t else None, _stream_handle(stream)))
+    torch.cuda.synchronize()
+    return x, target, mask
+
+
+def sur_apply(cfg, state, y, seqs, stream=None):
+    """One conservative network update of the tubes in seqs: returns (next state
+    tensor, flags (numpy int), totals (numpy (n, 2)))."""
+    import torch
+    nxt = state.clone()
+    n = len(seqs)
+    flags = torch.zeros(n, device="cuda", dtype=torch.int32)
+    tot = torch.zeros((n, 2), device="cuda", dtype=torch.float64)
+    dseq = _seq_array(seqs)
+    vp = ctypes.c_void_p
+    _check(load_library().rpk_sur_apply(ctypes.byref(cfg), _dev_f32(state, name="state"),
+                                        _dev_f32(y, name="y"), vp(dseq.data_ptr()), n,
+                                        _dev_f32(nxt, name="next"), vp(flags.data_ptr()),
+                                        vp(tot.data_ptr()), _stream_handle(stream)))
+    torch.cuda.synchronize()
+    return nxt, flags.cpu().numpy(), tot.cpu().numpy()
+
+
+class Rollout:
+    """Surrogate rollout with LBM fallback (rpk_rollout_*): ``net`` a Net,
+    ``tubes`` as for Batch (every relax must carry nsub > 0), ``cond`` (ntubes,
+    2) conditioning features, ``cfg`` a SurConfig."""
+
+    def __init__(self, net, cfg, tubes, cond, stream=None):
+        lib = load_library()
+        arr = (Tube * len(tubes))()
+        for t, d in zip(arr, tubes):
+            t.nx, t.nsteps = int(d["nx"]), int(d["nsteps"])
+            r = d["relax"]
+            t.relax = Relax(r["delta"], r["tau"], r["tau1"], r.get("b", 0.0), r.get("k_r", 0.0),
+                            r.get("dt", 1.0), int(r.get("nsub", 0)))
+            for k in range(12):
+                t.res[k] = float(d["res"][k])
+        c = np.ascontiguousarray(cond, dtype=np.float32).reshape(-1)
+        if c.size != 2 * len(tubes):
+            raise ValueError("cond must have 2 values per tube")
+        h = ctypes.c_void_p()
+        _check(lib.rpk_rollout_create(net._h, ctypes.byref(cfg), len(tubes), arr,
+                                      c.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                      _stream_handle(stream), ctypes.byref(h)))
+        self._h, self._net, self.cfg = h, net, cfg
+        self.ntubes = len(tubes)
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            load_library().rpk_rollout_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def run(self, state):
+        """Advance the moment blocks ``state`` (CUDA float32 tensor) in place.
+        Returns a dict: fail_step, windows, checks, lbm_steps (per tube), est
+        (estimated L1 error per tube), ms (network, spot checks, final LBM)."""
+        n = self.ntubes
+        stats = np.zeros(4 * n, dtype=np.int64)
+        est = np.zeros(n)
+        ms = np.zeros(3)
+        _check(load_library().rpk_rollout_run(
+            self._h, _dev_f32(state, name="state"),
+            stats.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+            est.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+            ms.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+        st = stats.reshape(n, 4)
+        return {"fail_step": st[:, 0], "windows": st[:, 1], "checks": st[:, 2],
+                "lbm_steps": st[:, 3], "est": est, "ms": ms}

@@ -21,7 +21,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "-I" + INCLUDE, "--expt-relaxed-constexpr"]
 SOURCES = ["rpk_api.cu", "rpk_ops_f64.cu", "rpk_ops_f32.cu", "rpk_ops_f16.cu", "rpk_ops_bf16.cu",
-           "rpk_noalloc.cu", "rpk_batch.cu", "rpk_net.cu"]
+           "rpk_noalloc.cu", "rpk_batch.cu", "rpk_net.cu", "rpk_surrogate.cu"]
 
 
 def nvcc():

@@ -112,3 +112,83 @@ def test_adam_first_step_moves_by_lr_times_sign():
     for step in range(2, 6):
         S.adam(p, g, m, v, step, lr=0.01, eps=0.0)
     np.testing.assert_allclose(p["a"], -0.05 * np.sign(g["a"]), rtol=1e-10)
+
+
+def _tube_block(nx, rng):
+    rho = rng.uniform(0.2, 1.0, 2 * nx)
+    return np.stack([rho, rng.normal(0, 0.2, 2 * nx), rng.uniform(0.15, 0.4, 2 * nx),
+                     rho * rng.uniform(0.15, 0.4, 2 * nx)])
+
+
+def test_conserved_primitive_inverse_and_energy():
+    rng = np.random.default_rng(7)
+    v = _tube_block(9, rng)
+    np.testing.assert_allclose(S.primitive(S.conserved(v)), v, rtol=1e-13)
+    # one point by hand: rho 2, u 0.5, theta 0.3, E_R 0.4 -> E = 0.25 + 0.9 + 0.4
+    U = S.conserved(np.array([2.0, 0.5, 0.3, 0.4]))
+    np.testing.assert_allclose(U, [2.0, 1.0, 1.55, 0.4], rtol=1e-15)
+
+
+def test_position_order_interleaves_sublattices():
+    blk = np.arange(4 * 6, dtype=float).reshape(4, 6)  # nx = 3: points (s=0, x=0..2), (s=1, x=0..2)
+    seq = S.position_order(blk, 3)
+    np.testing.assert_array_equal(seq[0], [0, 3, 1, 4, 2, 5])
+    np.testing.assert_array_equal(S.point_order(seq, 3), blk)
+
+
+def test_pack_padding_and_features():
+    rng = np.random.default_rng(8)
+    nx, pad = 5, 4
+    src = _tube_block(nx, rng)
+    res = np.array([[1.0, 0.0, 0.3, 0.3], [0.5, 0.0, 0.25, 0.12]])
+    x, _, _ = S.pack(src, None, nx, res, (0.7, -0.2), pad, 0, 2 * nx + 2 * pad, 0,
+                     (0, 0, 0, 0), (1, 1, 1, 1), (1, 1, 1, 1))
+    assert np.all(x[:pad, 6] == 0) and np.all(x[pad:pad + 2 * nx, 6] == 1) and np.all(x[pad + 2 * nx:, 6] == 0)
+    np.testing.assert_allclose(x[:pad, :4], np.broadcast_to(res[0], (pad, 4)), rtol=1e-7)
+    np.testing.assert_allclose(x[pad + 2 * nx:, :4], np.broadcast_to(res[1], (pad, 4)), rtol=1e-7)
+    np.testing.assert_allclose(x[pad:pad + 2 * nx, :4].T, S.position_order(src, nx), rtol=1e-7)
+    np.testing.assert_allclose(x[:, 4:6], np.broadcast_to([0.7, -0.2], (2 * nx + 2 * pad, 2)), rtol=1e-7)
+
+
+def test_apply_inverts_pack_targets():
+    # the increments pack builds from (src, tgt), applied to src without
+    # projection, give back tgt
+    rng = np.random.default_rng(9)
+    nx, pad, crop = 7, 4, 2
+    src, tgt = _tube_block(nx, rng), _tube_block(nx, rng)
+    out_scale = (0.1, 0.05, 0.2, 0.03)
+    length = 2 * nx + 2 * pad - crop
+    _, t, mask = S.pack(src, tgt, nx, np.ones((2, 4)), (0, 0), pad, crop, length, 0,
+                        (0, 0, 0, 0), (1, 1, 1, 1), out_scale)
+    assert mask.sum() == 2 * nx
+    new, bad, tot = S.apply(src, t, nx, pad, crop, out_scale, project=False)
+    assert not bad
+    np.testing.assert_allclose(new, tgt, rtol=1e-12, atol=1e-14)
+    assert abs(tot[0] - tgt[0].sum()) < 1e-12
+
+
+def test_apply_projection_conserves_mass_and_energy():
+    rng = np.random.default_rng(10)
+    nx, pad = 11, 0
+    src = _tube_block(nx, rng)
+    y = rng.normal(0, 1, (2 * nx, 4))
+    out_scale = (0.01, 0.01, 0.01, 0.005)
+    new, bad, tot = S.apply(src, y, nx, pad, 0, out_scale, project=True)
+    U0, U1 = S.conserved(src), S.conserved(new)
+    assert abs(U1[0].sum() - U0[0].sum()) < 1e-12 and abs(U1[2].sum() - U0[2].sum()) < 1e-12
+    assert abs(tot[0] - U0[0].sum()) < 1e-12 and abs(tot[1] - U0[2].sum()) < 1e-12
+    # momentum and E_R increments are left alone
+    d = S.position_order(U1 - U0, nx)
+    np.testing.assert_allclose(d[1], 0.01 * y[:, 1], atol=1e-12)
+    np.testing.assert_allclose(d[3], 0.005 * y[:, 3], atol=1e-12)
+    # increments that already sum to zero are unchanged
+    y2 = y.copy()
+    y2[:, 0] -= y2[:, 0].mean()
+    y2[:, 2] -= y2[:, 2].mean()
+    a, _, _ = S.apply(src, y2, nx, pad, 0, out_scale, project=True)
+    b, _, _ = S.apply(src, y2, nx, pad, 0, out_scale, project=False)
+    np.testing.assert_allclose(a, b, rtol=1e-12, atol=1e-14)
+    # a negative density is reported
+    y3 = np.zeros((2 * nx, 4))
+    y3[3, 0] = -1e3
+    assert S.apply(src, y3, nx, pad, 0, out_scale, project=False)[1]
