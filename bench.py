@@ -249,6 +249,102 @@ def run_batch(args):
     return 0
 
 
+def run_surrogate(args):
+    """Learned surrogate against the plain batched LBM. Trains the network on
+    the LBM's snapshots of --train-tubes tubes of the sweep (the library's own
+    forward, backward and Adam kernels), then advances --tubes held-out tubes
+    (another seed of the same sweep) twice: by the plain batched LBM (one
+    graph-captured persistent launch) and by the surrogate rollout with its
+    LBM spot checks and hand-over. Reports the wall-clock ratio and the
+    relative L1 density error of every tube against the plain LBM. Prints one
+    JSON line (not the lattice line)."""
+    import torch
+    import paper_2201_05280_gb300 as rpk
+    from paper_2201_05280_gb300 import build as B
+    from paper_2201_05280_gb300 import surrogate as SG
+    B.build()
+    torch.cuda.set_device(0)
+    t0 = time.time()
+    specs, f = I.tube_sweep(args.train_tubes, THETA0, seed=args.train_seed)
+    tubes, cond = SG.make_tubes(specs, f, THETA0)
+    data = SG.TrainingSet(tubes, cond, f)
+    torch.cuda.synchronize()
+    t_data = time.time() - t0
+    n_pairs = len(data)
+    cfg = SG.default_config(THETA0)
+    net = rpk.Net(SG.CIN, SG.COUT, args.width, args.blocks, seed=args.train_seed)
+    t0 = time.time()
+    hist = SG.train(net, cfg, data, args.train_steps, batch=args.batch, crop_len=args.crop,
+                    noise=[float(v) for v in args.noise.split(",")], seed=args.train_seed)
+    torch.cuda.synchronize()
+    t_train = time.time() - t0
+    del data
+    torch.cuda.empty_cache()
+
+    specs, f = I.tube_sweep(args.tubes, THETA0, seed=args.eval_seed)
+    etubes, econd = SG.make_tubes(specs, f, THETA0)
+    blk0 = SG.initial_blocks(etubes, f)
+    bt = rpk.Batch(etubes, precision="f32", save_every=1 << 30)
+    bt.init_fields(f["rho"], f["u"], f["T"], f["R"])
+    tune = bt.autotune()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    bt.init_device(blk0).run()  # captures the graph
+    torch.cuda.synchronize()
+    bt.init_device(blk0)
+    with ClockSampler(0) as clk_lbm:
+        e0.record()
+        bt.run()
+        e1.record()
+        torch.cuda.synchronize()
+    lbm_ms = e0.elapsed_time(e1)
+    ref = bt.moments_device()
+    torch.cuda.synchronize()
+    ref = ref.cpu().numpy()
+    offs = bt.block_offsets
+    bt.close()
+    ccfg = SG.default_config(THETA0, spot_every=args.spot_every, l1_tol=args.l1_tol,
+                             anchor=int(args.anchor), lbm_threads=tune["threads"],
+                             lbm_ctas_per_sm=tune["ctas_per_sm"])
+    R = rpk.Rollout(net, ccfg, etubes, econd)
+    st = blk0.clone()
+    R.run(st)  # warm-up (graph capture of its LBM, workspaces)
+    st = blk0.clone()
+    torch.cuda.synchronize()
+    with ClockSampler(0) as clk_sur:
+        t1 = time.perf_counter()
+        e0.record()
+        res = R.run(st)
+        e1.record()
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t1
+    sur_ms = e0.elapsed_time(e1)
+    got = st.cpu().numpy()
+    l1 = np.array([np.abs(got[o:o + 2 * t["nx"]] - ref[o:o + 2 * t["nx"]]).sum() /
+                   np.abs(ref[o:o + 2 * t["nx"]]).sum() for o, t in zip(offs, etubes)])
+    handed = res["fail_step"] >= 0
+    windows_total = int(sum(t["nsteps"] // cfg.jump for t in etubes))
+    line = {"metric": METRIC, "mode": "surrogate", "value": lbm_ms / sur_ms, "unit": "x (plain LBM ms / surrogate ms)",
+            "n_gpus": 1, "higher_is_better": True, "dtype": "bf16 network, f32 LBM", "data": "synthetic",
+            "config": {"workload": "%d held-out quasi-1-D shock tubes of the sweep (seed %d)" % (args.tubes, args.eval_seed),
+                       "train_tubes": args.train_tubes, "train_pairs": n_pairs, "train_crops_seen": int(args.train_steps * args.batch),
+                       "jump": cfg.jump, "spot_every": args.spot_every, "l1_tol": args.l1_tol,
+                       "anchor": int(args.anchor), "network": {"width": args.width, "blocks": args.blocks,
+                                                               "params": net.num_params}},
+            "lbm_ms": lbm_ms, "surrogate_ms": sur_ms, "surrogate_wall_s": wall,
+            "surrogate_parts_ms": dict(zip(("network", "spot_checks", "final_lbm", "reruns"), res["ms"].tolist())),
+            "l1": {"mean": float(l1.mean()), "p90": float(np.percentile(l1, 90)), "max": float(l1.max()),
+                   "frac_le_1pct": float((l1 <= 0.01).mean())},
+            "tubes_handed_to_lbm": int(handed.sum()), "network_windows": int(res["windows"].sum()),
+            "windows_total": windows_total, "spot_checks": int(res["checks"].sum()),
+            "training": {"data_s": t_data, "train_s": t_train, "steps": args.train_steps,
+                         "loss_first": float(np.mean(hist[:50])), "loss_last": float(np.mean(hist[-200:]))},
+            "autotune": tune, "clocks": {"lbm": clk_lbm.summary(), "surrogate": clk_sur.summary()}}
+    print(json.dumps(line))
+    R.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -261,9 +357,23 @@ def main():
     ap.add_argument("--cpu-n", type=int, default=24, help="oracle sample box for cpu_baseline")
     ap.add_argument("--cpu-steps", type=int, default=100)
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--mode", default="lattice", choices=["lattice", "batch"],
-                    help="lattice: the 3-D step (default); batch: the shock-tube sweep")
-    ap.add_argument("--tubes", type=int, default=4096, help="tubes in --mode batch")
+    ap.add_argument("--mode", default="lattice", choices=["lattice", "batch", "surrogate"],
+                    help="lattice: the 3-D step (default); batch: the shock-tube sweep; "
+                         "surrogate: learned surrogate vs plain batched LBM")
+    ap.add_argument("--tubes", type=int, default=None,
+                    help="tubes in --mode batch (4096) / held-out tubes in --mode surrogate (512)")
+    ap.add_argument("--train-tubes", type=int, default=512)
+    ap.add_argument("--train-steps", type=int, default=16000)
+    ap.add_argument("--train-seed", type=int, default=1001)
+    ap.add_argument("--eval-seed", type=int, default=2002)
+    ap.add_argument("--width", type=int, default=128)
+    ap.add_argument("--blocks", type=int, default=6)
+    ap.add_argument("--batch", type=int, default=32)
+    ap.add_argument("--crop", type=int, default=1024)
+    ap.add_argument("--noise", default="3e-4,3e-4,1e-4,1e-4")
+    ap.add_argument("--spot-every", type=int, default=16)
+    ap.add_argument("--l1-tol", type=float, default=1e-2)
+    ap.add_argument("--anchor", type=int, default=0)
     ap.add_argument("--workload", default="waves", choices=["waves", "tgv"],
                     help="decaying wave field (default) or Taylor-Green vortex Ma 0.3 Re 1600")
     args = ap.parse_args()
@@ -276,7 +386,11 @@ def main():
     if args.impl == "reference":
         return run_reference(args, rank)
     if args.mode == "batch":
+        args.tubes = args.tubes or 4096
         return run_batch(args)
+    if args.mode == "surrogate":
+        args.tubes = args.tubes or 512
+        return run_surrogate(args)
 
     import torch
     import paper_2201_05280_gb300 as rpk

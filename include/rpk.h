@@ -299,8 +299,9 @@ rpk_status rpk_net_adam(rpk_net* net, float lr, float beta1, float beta2, float 
 /* ---- Surrogate rollout of batched tubes with LBM fallback -----------------
  * (the paper has no learned component). The network maps the moments of a
  * tube at step t to the increments of its conserved densities over `jump`
- * steps: inputs per fine point (position 2x + s of point (s, x)) are 7
- * features -- (rho, u_x, theta_T, E_R) shifted and scaled, two per-tube
+ * steps: inputs per fine point (position 2x + s of point (s, x)) are 11
+ * features -- v = (rho, u_x, theta_T, E_R) shifted and scaled, the change of v
+ * since the previous window scaled (zero without one), two per-tube
  * conditioning values, and 1 inside the tube / 0 in the reservoir padding --
  * and outputs are 4 scaled increments of U = (rho, rho u_x,
  * E = rho u_x^2 / 2 + 3 rho theta_T / 2 + E_R, E_R). */
@@ -309,11 +310,16 @@ typedef struct {
   int pad;             /* reservoir points each side of a tube in its sequence, >= 0 */
   int spot_every;      /* spot check at windows 0, spot_every, 2 spot_every, ...; 0: none */
   int project;         /* 1: rescale the mass and energy increments to zero net change */
+  int anchor;          /* 1: spot-check windows keep the LBM's result and a handed-over
+                          tube continues on the LBM from its last accepted state;
+                          0: the network's windows are kept and a handed-over tube
+                          runs on the LBM from its initial state */
   double drift_tol;    /* relative mass or energy drift that hands a tube to the LBM */
   double l1_tol;       /* estimated relative L1 density error that hands a tube to the LBM */
   float in_shift[4];   /* feature k = (v_k - in_shift[k]) / in_scale[k], v = (rho, u_x, theta_T, E_R) */
   float in_scale[4];
   float out_scale[4];  /* increment of U_k = out_scale[k] * network output k */
+  float in_dscale[4];  /* feature 4 + k = (v_k - v_k(previous window)) / in_dscale[k] */
   int lbm_threads;     /* launch configuration of the LBM arm (rpk_batch_set_config) */
   int lbm_ctas_per_sm;
 } rpk_sur_config;
@@ -325,6 +331,7 @@ typedef struct {
 typedef struct {
   int64_t src;         /* float offset of the source moment block [4][2 nx] */
   int64_t tgt;         /* float offset of the target moment block, or -1 (no target) */
+  int64_t prev;        /* float offset of the previous window's block, or -1 (none) */
   int64_t out;         /* first point of the sequence in x, target and mask */
   int nx, len, crop, pad_;
   float res[2][4];     /* reservoir (rho, u_x, theta_T, E_R), left then right */
@@ -334,12 +341,17 @@ typedef struct {
 /* Network inputs (and, where tgt >= 0, normalised target increments
  * (U_k(target) - U_k(source)) / out_scale[k] and a mask that is 1 at tube
  * points at least `margin` points from both ends of the sequence) for nseq
- * sequences; store and seqs are device pointers, maxlen bounds every len.
- * x [..][7], target [..][4], mask [..] (target and mask may be NULL when no
- * sequence has a target). Asynchronous on cuda_stream. */
+ * sequences; store and seqs are device pointers (prev offsets index `store`
+ * too), maxlen bounds every len. x [..][11], target [..][4], mask [..]
+ * (target and mask may be NULL when no sequence has a target). noise (host,
+ * 4 values, may be NULL): the source state of tube points is perturbed by
+ * noise[k] sqrt(3) (2 u - 1) per variable, u uniform in [0, 1) from output
+ * ((s << 32 | l) * 4 + k) + 1 of SplitMix64 seeded with `seed` (sequence s of
+ * the call, point l of the sequence); features and targets use the perturbed
+ * state. Asynchronous on cuda_stream. */
 rpk_status rpk_sur_pack(const rpk_sur_config* cfg, const float* store, const rpk_sur_seq* seqs,
-                        int nseq, int maxlen, int margin, float* x, float* target, float* mask,
-                        void* cuda_stream);
+                        int nseq, int maxlen, int margin, const float* noise, uint64_t seed,
+                        float* x, float* target, float* mask, void* cuda_stream);
 
 /* Moment blocks after one network application: for every tube of `seqs`
  * (device, nseq entries, src = the tube's block in `state`, out = its
@@ -360,17 +372,25 @@ rpk_status rpk_rollout_create(rpk_net* net, const rpk_sur_config* cfg, int ntube
                               rpk_rollout** out);
 void rpk_rollout_destroy(rpk_rollout* r);
 /* Advance every tube by its nsteps from the moment blocks `state` (device,
- * updated in place): floor(nsteps / jump) windows by the network, except that
- * spot-check windows run on the LBM (whose result is kept) and compare the
- * network's density with it; a tube whose mass or energy drift exceeds
- * drift_tol, whose result is invalid, or whose estimated accumulated L1 error
- * exceeds l1_tol finishes on the LBM from its last accepted state; remainders
- * (nsteps mod jump) run on the LBM. stats (host, 4 per tube, may be NULL):
- * step at which the LBM took over (-1: never), network windows kept, spot
- * checks, LBM steps after the windows; est (host, per tube, may be NULL): the
- * estimated L1 error; ms (host, 3, may be NULL): device time of the network
- * windows, the spot checks and the final LBM run. Synchronises. */
+ * updated in place): floor(nsteps / jump) windows by the network; at a spot
+ * check the LBM also runs the window and the network's density is compared
+ * with it (the error, times the windows until the next check, is added to the
+ * tube's estimate); a tube whose mass or energy drift exceeds drift_tol, whose
+ * result is invalid, or whose estimated accumulated L1 error exceeds l1_tol
+ * is handed to the LBM (see anchor); remainders
+ * (nsteps mod jump) run on the LBM; a tube whose final moments are invalid is
+ * run again by the LBM from its initial state. stats (host, 5 per tube, may be
+ * NULL): step at which the LBM took over (-1: never), network windows kept,
+ * spot checks, LBM steps after the windows, 1 if run again from the start;
+ * est (host, per tube, may be NULL): the estimated L1 error; ms (host, 4, may
+ * be NULL): device time of the network windows, the spot checks, the final LBM
+ * run and the repeated runs. Synchronises. */
 rpk_status rpk_rollout_run(rpk_rollout* r, float* state, int64_t* stats, double* est, double* ms);
+/* Spot-check errors of the last run: *windows = the largest window count; out
+ * (host, ntubes x *windows, may be NULL) = relative L1 density error of the
+ * network against the LBM per tube and checked window (NaN where unchecked,
+ * +inf where the network's result was invalid). */
+rpk_status rpk_rollout_errors(const rpk_rollout* r, double* out, int* windows);
 
 /* Conserved totals of hydrodynamic fields held by the caller in device memory,
  * computed without allocating anything. The paper has no counterpart; this is

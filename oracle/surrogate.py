@@ -224,23 +224,54 @@ def point_order(seq, nx):
     return out
 
 
-def pack(src, tgt, nx, res, cond, pad, crop, length, margin, shift, scale, out_scale):
-    """Network input x (length, 7) of one padded tube, and (when tgt is not None)
-    the normalised target increments (length, 4) and the loss mask (length,).
-    res (2, 4): left / right reservoir (rho, u_x, theta_T, E_R)."""
+_M64 = (1 << 64) - 1
+
+
+def splitmix64(seed, n):
+    """Output n + 1 of SplitMix64 seeded with ``seed`` (Steele, Lea & Flood,
+    "Fast splittable pseudorandom number generators", OOPSLA 2014): add the
+    golden gamma 0x9E3779B97F4A7C15 n + 1 times, then the output mix
+    z ^= z >> 30; z *= 0xBF58476D1CE4E5B9; z ^= z >> 27; z *= 0x94D049BB133111EB;
+    z ^= z >> 31 (all modulo 2^64)."""
+    z = (seed + (n + 1) * 0x9E3779B97F4A7C15) & _M64
+    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & _M64
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & _M64
+    return z ^ (z >> 31)
+
+
+def pack(src, tgt, nx, res, cond, pad, crop, length, margin, shift, scale, out_scale,
+         prev=None, dscale=(1.0, 1.0, 1.0, 1.0), noise=None, seed=0, seq_index=0):
+    """Network input x (length, 11) of one padded tube, and (when tgt is not
+    None) the normalised target increments (length, 4) and the loss mask
+    (length,). Features: (v - shift) / scale, (v - v_prev) / dscale (zero
+    without a previous block and in the padding), cond, inside indicator.
+    res (2, 4): left / right reservoir (rho, u_x, theta_T, E_R). ``noise``: at
+    tube points v_k is replaced by v_k + noise_k sqrt(3) (2 u - 1) with u =
+    2^-53 (splitmix64(seed, ((seq_index << 32) | l) 4 + k) >> 11), and
+    features and targets use the perturbed state."""
     shift, scale = np.asarray(shift, np.float32), np.asarray(scale, np.float32)
+    dscale = np.asarray(dscale, np.float32)
     s = position_order(np.asarray(src, np.float64), nx)
+    q = position_order(np.asarray(prev, np.float64), nx) if prev is not None else None
     t = position_order(np.asarray(tgt, np.float64), nx) if tgt is not None else None
-    x = np.zeros((length, 7), np.float32)
+    x = np.zeros((length, 11), np.float32)
     target = np.zeros((length, 4))
     mask = np.zeros(length)
     for l in range(length):
         p = crop + l - pad
         inside = 0 <= p < 2 * nx
-        v = s[:, p] if inside else np.asarray(res[0 if p < 0 else 1], np.float64)
+        v = s[:, p].copy() if inside else np.asarray(res[0 if p < 0 else 1], np.float64)
+        if inside and noise is not None:
+            for k in range(4):
+                if noise[k] != 0.0:
+                    h = splitmix64(seed, (((seq_index << 32) | l) * 4 + k) & _M64)
+                    u = (h >> 11) * 2.0 ** -53
+                    v[k] += float(np.float32(noise[k])) * 1.7320508075688772 * (2.0 * u - 1.0)
+        w = q[:, p] if (inside and prev is not None) else v
         x[l, :4] = (v.astype(np.float32) - shift) / scale
-        x[l, 4:6] = cond
-        x[l, 6] = 1.0 if inside else 0.0
+        x[l, 4:8] = (v.astype(np.float32) - w.astype(np.float32)) / dscale
+        x[l, 8:10] = cond
+        x[l, 10] = 1.0 if inside else 0.0
         if t is not None and inside and margin <= l < length - margin:
             target[l] = (conserved(t[:, p]) - conserved(v)) / np.asarray(out_scale, np.float64)
             mask[l] = 1.0

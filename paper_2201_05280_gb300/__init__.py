@@ -56,20 +56,21 @@ class Tube(ctypes.Structure):
 
 class SurConfig(ctypes.Structure):
     _fields_ = [("jump", ctypes.c_int), ("pad", ctypes.c_int), ("spot_every", ctypes.c_int),
-                ("project", ctypes.c_int), ("drift_tol", ctypes.c_double),
+                ("project", ctypes.c_int), ("anchor", ctypes.c_int), ("drift_tol", ctypes.c_double),
                 ("l1_tol", ctypes.c_double), ("in_shift", ctypes.c_float * 4),
                 ("in_scale", ctypes.c_float * 4), ("out_scale", ctypes.c_float * 4),
+                ("in_dscale", ctypes.c_float * 4),
                 ("lbm_threads", ctypes.c_int), ("lbm_ctas_per_sm", ctypes.c_int)]
 
     @classmethod
     def make(cls, **kw):
         c = cls()
-        c.jump, c.pad, c.spot_every, c.project = 32, 128, 8, 1
+        c.jump, c.pad, c.spot_every, c.project, c.anchor = 32, 128, 8, 1, 1
         c.drift_tol, c.l1_tol = 1e-4, 1e-2
         for k in range(4):
-            c.in_scale[k] = c.out_scale[k] = 1.0
+            c.in_scale[k] = c.out_scale[k] = c.in_dscale[k] = 1.0
         for k, v in kw.items():
-            if k in ("in_shift", "in_scale", "out_scale"):
+            if k in ("in_shift", "in_scale", "out_scale", "in_dscale"):
                 for i in range(4):
                     getattr(c, k)[i] = float(v[i])
             else:
@@ -78,7 +79,8 @@ class SurConfig(ctypes.Structure):
 
 
 class SurSeq(ctypes.Structure):
-    _fields_ = [("src", ctypes.c_int64), ("tgt", ctypes.c_int64), ("out", ctypes.c_int64),
+    _fields_ = [("src", ctypes.c_int64), ("tgt", ctypes.c_int64), ("prev", ctypes.c_int64),
+                ("out", ctypes.c_int64),
                 ("nx", ctypes.c_int), ("len", ctypes.c_int), ("crop", ctypes.c_int),
                 ("pad_", ctypes.c_int), ("res", (ctypes.c_float * 4) * 2),
                 ("cond", ctypes.c_float * 2)]
@@ -143,12 +145,14 @@ def load_library(path=None):
         "rpk_batch_init_device": (i, [vp, vp]),
         "rpk_batch_set_steps": (i, [vp, ctypes.POINTER(i)]),
         "rpk_batch_moments_device": (i, [vp, vp]),
-        "rpk_sur_pack": (i, [ctypes.POINTER(SurConfig), vp, vp, i, i, i, vp, vp, vp, vp]),
+        "rpk_sur_pack": (i, [ctypes.POINTER(SurConfig), vp, vp, i, i, i, ctypes.POINTER(ctypes.c_float),
+                             ctypes.c_uint64, vp, vp, vp, vp]),
         "rpk_sur_apply": (i, [ctypes.POINTER(SurConfig), vp, vp, vp, i, vp, vp, vp, vp]),
         "rpk_rollout_create": (i, [vp, ctypes.POINTER(SurConfig), i, ctypes.POINTER(Tube),
                                    ctypes.POINTER(ctypes.c_float), vp, ctypes.POINTER(vp)]),
         "rpk_rollout_destroy": (None, [vp]),
         "rpk_rollout_run": (i, [vp, vp, ctypes.POINTER(i64), ctypes.POINTER(d), ctypes.POINTER(d)]),
+        "rpk_rollout_errors": (i, [vp, vp, ctypes.POINTER(i)]),
         "rpk_net_create": (i, [i, i, i, i, ctypes.c_uint64, vp, ctypes.POINTER(vp)]),
         "rpk_net_destroy": (None, [vp]),
         "rpk_net_num_params": (i64, [vp]),
@@ -559,12 +563,13 @@ class Net:
 
 
 def _seq_array(seqs):
-    """Sequence descriptors (dicts with src, tgt, out, nx, len, crop, res (2x4),
-    cond (2)) -> a CUDA uint8 tensor holding the rpk_sur_seq array."""
+    """Sequence descriptors (dicts with src, tgt, prev, out, nx, len, crop, res
+    (2x4), cond (2)) -> a CUDA uint8 tensor holding the rpk_sur_seq array."""
     import torch
     arr = (SurSeq * len(seqs))()
     for a, d in zip(arr, seqs):
         a.src, a.tgt, a.out = int(d["src"]), int(d.get("tgt", -1)), int(d["out"])
+        a.prev = int(d.get("prev", -1))
         a.nx, a.len, a.crop = int(d["nx"]), int(d["len"]), int(d.get("crop", 0))
         for side in range(2):
             for k in range(4):
@@ -574,7 +579,8 @@ def _seq_array(seqs):
     return torch.from_numpy(raw).cuda()
 
 
-def sur_pack(cfg, store, seqs, margin=0, x=None, target=None, mask=None, stream=None):
+def sur_pack(cfg, store, seqs, margin=0, x=None, target=None, mask=None, noise=None, seed=0,
+             stream=None):
     """Network inputs (and targets / mask when sequences carry tgt >= 0) for
     the sequences; returns (x, target, mask) as CUDA float32 tensors."""
     import torch
@@ -582,16 +588,17 @@ def sur_pack(cfg, store, seqs, margin=0, x=None, target=None, mask=None, stream=
     maxlen = max(int(d["len"]) for d in seqs)
     with_t = any(int(d.get("tgt", -1)) >= 0 for d in seqs)
     if x is None:
-        x = torch.zeros((total, 7), device="cuda", dtype=torch.float32)
+        x = torch.zeros((total, 11), device="cuda", dtype=torch.float32)
     if with_t and target is None:
         target = torch.zeros((total, 4), device="cuda", dtype=torch.float32)
     if with_t and mask is None:
         mask = torch.zeros(total, device="cuda", dtype=torch.float32)
     dseq = _seq_array(seqs)
     vp = ctypes.c_void_p
+    nz = (ctypes.c_float * 4)(*[float(v) for v in noise]) if noise is not None else None
     _check(load_library().rpk_sur_pack(
         ctypes.byref(cfg), _dev_f32(store, name="store"), vp(dseq.data_ptr()), len(seqs), maxlen,
-        int(margin), _dev_f32(x, name="x"), _dev_f32(target, name="target") if with_t else None,
+        int(margin), nz, int(seed), _dev_f32(x, name="x"), _dev_f32(target, name="target") if with_t else None,
         _dev_f32(mask, name="mask") if with_t else None, _stream_handle(stream)))
     torch.cuda.synchronize()
     return x, target, mask
@@ -653,17 +660,27 @@ class Rollout:
 
     def run(self, state):
         """Advance the moment blocks ``state`` (CUDA float32 tensor) in place.
-        Returns a dict: fail_step, windows, checks, lbm_steps (per tube), est
-        (estimated L1 error per tube), ms (network, spot checks, final LBM)."""
+        Returns a dict: fail_step, windows, checks, lbm_steps, rerun (per
+        tube), est (estimated L1 error per tube), ms (network, spot checks,
+        final LBM, repeated runs)."""
         n = self.ntubes
-        stats = np.zeros(4 * n, dtype=np.int64)
+        stats = np.zeros(5 * n, dtype=np.int64)
         est = np.zeros(n)
-        ms = np.zeros(3)
+        ms = np.zeros(4)
         _check(load_library().rpk_rollout_run(
             self._h, _dev_f32(state, name="state"),
             stats.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
             est.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
             ms.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
-        st = stats.reshape(n, 4)
+        st = stats.reshape(n, 5)
         return {"fail_step": st[:, 0], "windows": st[:, 1], "checks": st[:, 2],
-                "lbm_steps": st[:, 3], "est": est, "ms": ms}
+                "lbm_steps": st[:, 3], "rerun": st[:, 4], "est": est, "ms": ms}
+
+    def errors(self):
+        """(ntubes, windows) spot-check L1 errors of the last run (NaN: unchecked)."""
+        w = ctypes.c_int()
+        _check(load_library().rpk_rollout_errors(self._h, None, ctypes.byref(w)))
+        out = np.full((self.ntubes, max(w.value, 1)), np.nan)
+        _check(load_library().rpk_rollout_errors(self._h, out.ctypes.data_as(ctypes.c_void_p),
+                                                 ctypes.byref(w)))
+        return out[:, :w.value]

@@ -172,6 +172,202 @@ __global__ void __launch_bounds__(kThreads) k_conv(ConvArgs P) {
       }
 }
 
+// ---------------------------------------------------------------------------
+// Tensor-core (tcgen05) path of the residual-block convolutions: Co = Ci = 128,
+// 5 taps. One persistent CTA per SM holds the layer's BF16 weights in shared
+// memory (A: 128 x 640, K-major) and walks over tiles of 128 output positions
+// of one sequence. Per tile it stages the 132 input rows (positions q0 - 2 ..
+// q0 + 129, activation applied, BF16) once; the operand of tap t is the same
+// tile seen from row t (forward) or 4 - t (input gradient), which the
+// interleaved no-swizzle layout (rows 16 bytes apart inside each 8-column
+// chunk) turns into a start-address offset. 40 MMAs (M 128, N 128, K 16)
+// accumulate into 128 TMEM columns; one thread issues them and commits to an
+// mbarrier; the epilogue reads TMEM rows (lane = output channel) and applies
+// bias, mask and residual as k_conv does.
+constexpr int TC_M = 128, TC_N = 128, TC_KC = 128, TC_TAPS = 5;
+constexpr int TC_ROWS = TC_N + TC_TAPS - 1;                // 132 staged rows
+constexpr int TC_K = TC_TAPS * TC_KC;                      // 640
+constexpr uint32_t TC_A_LBO = TC_M * 16;                   // bytes between 8-wide k chunks of A
+constexpr uint32_t TC_B_LBO = TC_ROWS * 16;                // bytes between 8-wide k chunks of B
+constexpr uint32_t TC_A_BYTES = (TC_K / 8) * TC_A_LBO;     // 163840
+constexpr uint32_t TC_B_BYTES = (TC_KC / 8) * TC_B_LBO;    // 33792
+constexpr uint32_t TC_USED = TC_A_BYTES + TC_B_BYTES + 64;  // + mbarrier and TMEM address
+// The whole opt-in shared memory of an SM: one CTA per SM either way, and every
+// address an operand descriptor can reach stays inside the allocation.
+constexpr uint32_t TC_SMEM = 227 * 1024;
+static_assert(TC_USED <= TC_SMEM, "tensor-core tiles exceed shared memory");
+constexpr int TC_THREADS = 128;
+constexpr long long TC_WAIT_LIMIT = 1ll << 24;             // mbarrier polls before giving up
+
+struct TcArgs {
+  const __nv_bfloat16* A;  // [128][5][128]
+  const float* X;          // [npos][128]
+  float* out;              // [npos][128]
+  const float* bias;
+  const float* res;
+  const float* mask;
+  const int4* tiles;       // per tile (q0, count, sequence start, sequence length), or null
+  int ntiles, seq_len, tiles_per_seq, sgn, relu_in;
+  unsigned* error;         // set to 1 when an mbarrier wait gives up
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// tcgen05 shared-memory matrix descriptor: start, leading (k-chunk) and stride
+// (8-row group) byte offsets, descriptor version 1, no swizzle.
+__device__ __forceinline__ uint64_t tc_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+// Instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, both
+// K-major, N >> 3 at bit 17, M >> 4 at bit 24.
+constexpr uint32_t TC_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TC_N >> 3) << 17) |
+                              ((uint32_t)(TC_M >> 4) << 24);
+
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t phase) {
+  for (long long it = 0; it < TC_WAIT_LIMIT; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(mbar), "r"(phase)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+__global__ void __launch_bounds__(TC_THREADS, 1) k_conv_tc(TcArgs P) {
+  extern __shared__ __align__(1024) unsigned char tc_smem[];
+  unsigned char* sA = tc_smem;
+  unsigned char* sB = tc_smem + TC_A_BYTES;
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(tc_smem + TC_A_BYTES + TC_B_BYTES);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tc_smem + TC_A_BYTES + TC_B_BYTES + 16);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(TC_N)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(mbar)), "r"(1) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  // weights: chunk c (k = 8c .. 8c + 7) of row m at c * TC_A_LBO + m * 16
+  for (int e = tid; e < TC_M * (TC_K / 8); e += TC_THREADS) {
+    const int m = e % TC_M, c = e / TC_M;
+    const uint4 v = *reinterpret_cast<const uint4*>(P.A + (int64_t)m * TC_K + 8 * c);
+    *reinterpret_cast<uint4*>(sA + c * TC_A_LBO + m * 16) = v;
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+  const uint32_t a_base = smem_u32(sA), b_base = smem_u32(sB), mb = smem_u32(mbar);
+  uint32_t phase = 0;
+  bool ok = true;
+
+  for (int tile = blockIdx.x; tile < P.ntiles && ok; tile += gridDim.x) {
+    int q0, cnt, lo, len;
+    if (P.tiles) {
+      const int4 d = P.tiles[tile];
+      q0 = d.x, cnt = d.y, lo = d.z, len = d.w;
+    } else {
+      const int sq = tile / P.tiles_per_seq, part = tile - sq * P.tiles_per_seq;
+      lo = sq * P.seq_len;
+      len = P.seq_len;
+      q0 = lo + part * TC_N;
+      cnt = min(TC_N, len - part * TC_N);
+    }
+    // stage rows r = 0 .. 131 (positions q0 - 2 + r), zero outside the sequence
+    for (int e = tid; e < TC_ROWS * (TC_KC / 8); e += TC_THREADS) {
+      const int r = e % TC_ROWS, c = e / TC_ROWS;
+      const int q = q0 - 2 + r;
+      uint4 packed = make_uint4(0u, 0u, 0u, 0u);
+      if (q >= lo && q < lo + len) {
+        const float4* src = reinterpret_cast<const float4*>(P.X + (int64_t)q * TC_KC + 8 * c);
+        float4 f0 = src[0], f1 = src[1];
+        if (P.relu_in) {
+          f0.x = fmaxf(f0.x, 0.f), f0.y = fmaxf(f0.y, 0.f), f0.z = fmaxf(f0.z, 0.f), f0.w = fmaxf(f0.w, 0.f);
+          f1.x = fmaxf(f1.x, 0.f), f1.y = fmaxf(f1.y, 0.f), f1.z = fmaxf(f1.z, 0.f), f1.w = fmaxf(f1.w, 0.f);
+        }
+        packed = make_uint4(pack_bf16(f0.x, f0.y), pack_bf16(f0.z, f0.w), pack_bf16(f1.x, f1.y),
+                            pack_bf16(f1.z, f1.w));
+      }
+      *reinterpret_cast<uint4*>(sB + c * TC_B_LBO + r * 16) = packed;
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll 1
+      for (int t = 0; t < TC_TAPS; ++t) {
+        const int row0 = P.sgn > 0 ? t : TC_TAPS - 1 - t;
+#pragma unroll
+        for (int s = 0; s < TC_KC / 16; ++s) {
+          const uint64_t ad = tc_desc(a_base + (uint32_t)(t * (TC_KC / 8) + 2 * s) * TC_A_LBO, TC_A_LBO, 128);
+          const uint64_t bd = tc_desc(b_base + (uint32_t)(2 * s) * TC_B_LBO + (uint32_t)row0 * 16, TC_B_LBO, 128);
+          const uint32_t acc = (t | s) ? 1u : 0u;
+          asm volatile(
+              "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+              " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+              "l"(ad), "l"(bd), "r"(TC_IDESC), "r"(acc)
+              : "memory");
+        }
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mb)
+                   : "memory");
+    }
+    __syncwarp();
+    // every thread waits; the CTA proceeds only if all saw the commit
+    ok = !__syncthreads_or(mbar_wait(mb, phase) ? 0 : 1);
+    if (!ok && tid == 0) atomicOr(P.error, 1u);
+    phase ^= 1u;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (ok) {
+      const int m = warp * 32 + lane;  // TMEM lane = output channel
+      const float bm = P.bias ? P.bias[m] : 0.f;
+#pragma unroll 1
+      for (int j = 0; j < TC_N / 32; ++j) {
+        uint32_t v[32];
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+            "%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+              "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+              "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]),
+              "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]),
+              "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+            : "r"(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(j * 32)));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+          const int n = j * 32 + i;
+          if (n < cnt) {
+            const int64_t o = (int64_t)(q0 + n) * TC_M + m;
+            float val = __uint_as_float(v[i]) + bm;
+            if (P.mask && !(P.mask[o] > 0.f)) val = 0.f;
+            if (P.res) val += P.res[o];
+            P.out[o] = val;
+          }
+        }
+      }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+  }
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_N) : "memory");
+}
+
 struct DwArgs {
   const float* dY;  // [npos][M]
   const float* X;   // [npos][Kc]
@@ -355,6 +551,11 @@ struct rpk_net {
   int2* qseq = nullptr;        // ragged sequence table, cap_q entries
   int* starts = nullptr;       // ragged sequence starts, cap_seq + 1 entries
   int cap_seq = 0;
+  int4* tiles = nullptr;       // ragged tensor-core tiles (q0, count, start, length)
+  int ntiles = 0, cap_tiles = 0;
+  unsigned* tc_error = nullptr;  // set by k_conv_tc when a wait gives up
+  int nsm = 0;
+  bool tc = false;             // the tensor-core path serves the block convolutions
 };
 
 namespace {
@@ -390,6 +591,16 @@ rpk_status ensure_workspace(rpk_net* N, int64_t nq) {
   return RPK_OK;
 }
 
+// Error word of the tensor-core path (synchronises the stream).
+rpk_status tc_status(rpk_net* N) {
+  if (!N->tc_error) return RPK_OK;
+  unsigned e = 0;
+  RPK_CUDA(cudaMemcpyAsync(&e, N->tc_error, sizeof(unsigned), cudaMemcpyDeviceToHost, N->stream));
+  RPK_CUDA(cudaStreamSynchronize(N->stream));
+  if (e) return rpk::fail(RPK_ERR_CUDA, "tensor-core convolution: an mbarrier wait gave up");
+  return RPK_OK;
+}
+
 rpk_status refresh_bf16(rpk_net* N) {
   for (const auto& L : N->layers) {
     const int64_t n = (int64_t)L.Co * L.taps * L.Ci;
@@ -404,6 +615,21 @@ rpk_status refresh_bf16(rpk_net* N) {
 rpk_status conv(rpk_net* N, const __nv_bfloat16* A, int M, int taps, int Kc, int sgn,
                 const float* X, int relu_in, float* out, const float* bias, const float* res,
                 const float* mask, int64_t nq, int seq_len, const int2* qseq = nullptr) {
+  const bool aligned = (((uintptr_t)A | (uintptr_t)X) & 15) == 0;
+  if (N->tc && M == TC_M && Kc == TC_KC && taps == TC_TAPS && aligned && nq > 0) {
+    TcArgs T{A, X, out, bias, res, mask, nullptr, 0, seq_len, 0, sgn, relu_in, N->tc_error};
+    if (qseq) {
+      T.tiles = N->tiles;
+      T.ntiles = N->ntiles;
+    } else {
+      T.tiles_per_seq = (seq_len + TC_N - 1) / TC_N;
+      T.ntiles = (int)(nq / seq_len) * T.tiles_per_seq;
+    }
+    const int grid = std::max(1, std::min(T.ntiles, N->nsm));
+    k_conv_tc<<<grid, TC_THREADS, TC_SMEM, N->stream>>>(T);
+    RPK_CUDA(cudaGetLastError());
+    return RPK_OK;
+  }
   ConvArgs P{A, X, out, bias, res, mask, qseq, M, Kc, taps, sgn, relu_in, (int)nq, seq_len};
   const dim3 grid((unsigned)((nq + BN - 1) / BN), (unsigned)((M + BM - 1) / BM));
   k_conv<<<grid, kThreads, 0, N->stream>>>(P);
@@ -545,11 +771,20 @@ rpk_status rpk_net_create(int cin, int cout, int width, int nblocks, uint64_t se
   if (st == RPK_OK) st = net_alloc((void**)&N->wb, sizeof(__nv_bfloat16) * N->nwb);
   if (st == RPK_OK) st = net_alloc((void**)&N->wtb, sizeof(__nv_bfloat16) * N->nwb);
   if (st == RPK_OK) st = net_alloc((void**)&N->loss, 2 * sizeof(double));
+  if (st == RPK_OK) st = net_alloc((void**)&N->tc_error, sizeof(unsigned));
+  if (st == RPK_OK) {
+    cudaDeviceGetAttribute(&N->nsm, cudaDevAttrMultiProcessorCount, N->device);
+    N->tc = width == TC_M &&
+            cudaFuncSetAttribute(k_conv_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM) ==
+                cudaSuccess;
+    cudaGetLastError();
+  }
   cudaError_t err = cudaSuccess;
   if (st == RPK_OK)
     err = cudaMemcpyAsync(N->w, w.data(), sizeof(float) * N->nparams, cudaMemcpyHostToDevice, N->stream);
   if (st == RPK_OK && err == cudaSuccess) err = cudaMemsetAsync(N->m, 0, sizeof(float) * N->nparams, N->stream);
   if (st == RPK_OK && err == cudaSuccess) err = cudaMemsetAsync(N->v, 0, sizeof(float) * N->nparams, N->stream);
+  if (st == RPK_OK && err == cudaSuccess) err = cudaMemsetAsync(N->tc_error, 0, sizeof(unsigned), N->stream);
   if (st == RPK_OK && err == cudaSuccess) st = refresh_bf16(N);
   if (st == RPK_OK && err == cudaSuccess) err = cudaStreamSynchronize(N->stream);
   if (st != RPK_OK || err != cudaSuccess) {
@@ -564,8 +799,8 @@ rpk_status rpk_net_create(int cin, int cout, int width, int nblocks, uint64_t se
 void rpk_net_destroy(rpk_net* N) {
   if (!N) return;
   cudaStreamSynchronize(N->stream);
-  void* p[] = {N->w,    N->g,       N->m,     N->v,     N->wb,    N->wtb,   N->act,
-               N->work, N->headout, N->dybuf, N->loss, N->qseq, N->starts};
+  void* p[] = {N->w,    N->g,       N->m,     N->v,    N->wb,     N->wtb,  N->act,
+               N->work, N->headout, N->dybuf, N->loss, N->qseq, N->starts, N->tiles, N->tc_error};
   for (void* q : p)
     if (q) cudaFree(q);
   delete N;
@@ -622,11 +857,28 @@ rpk_status rpk_net_forward_ragged(rpk_net* N, const float* x, int nseq, const in
   }
   RPK_CUDA(cudaMemcpyAsync(N->starts, starts.data(), sizeof(int) * (nseq + 1),
                            cudaMemcpyHostToDevice, N->stream));
+  // tensor-core tiles: 128 positions of one sequence each
+  std::vector<int4> tiles;
+  for (int s = 0; s < nseq; ++s)
+    for (int q = starts[s]; q < starts[s + 1]; q += TC_N)
+      tiles.push_back(make_int4(q, std::min(TC_N, starts[s + 1] - q), starts[s], starts[s + 1] - starts[s]));
+  if ((int)tiles.size() > N->cap_tiles) {
+    cudaFree(N->tiles);
+    N->tiles = nullptr;
+    N->cap_tiles = 0;
+    st = net_alloc((void**)&N->tiles, sizeof(int4) * tiles.size());
+    if (st != RPK_OK) return st;
+    N->cap_tiles = (int)tiles.size();
+  }
+  N->ntiles = (int)tiles.size();
+  RPK_CUDA(cudaMemcpyAsync(N->tiles, tiles.data(), sizeof(int4) * tiles.size(), cudaMemcpyHostToDevice,
+                           N->stream));
   k_fill_qseq<<<nseq, 256, 0, N->stream>>>(N->starts, N->qseq);
   RPK_CUDA(cudaGetLastError());
   st = forward(N, x, nq, 0, N->qseq, y);
-  // the starts table is read by k_fill_qseq before this host vector goes away
+  // the host tables are read before they go away
   if (st == RPK_OK) RPK_CUDA(cudaStreamSynchronize(N->stream));
+  if (st == RPK_OK) st = tc_status(N);
   return st;
 }
 
@@ -652,7 +904,7 @@ rpk_status rpk_net_loss_grad(rpk_net* N, const float* x, const float* target, co
   if (err == cudaSuccess && st == RPK_OK) err = cudaStreamSynchronize(N->stream);
   if (st != RPK_OK) return st;
   if (err != cudaSuccess) return rpk::cuda_fail(err, "rpk_net_loss_grad");
-  return RPK_OK;
+  return tc_status(N);
 }
 
 rpk_status rpk_net_adam(rpk_net* N, float lr, float beta1, float beta2, float eps) {

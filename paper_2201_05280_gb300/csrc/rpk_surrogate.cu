@@ -19,10 +19,12 @@
 
 namespace {
 
-constexpr int kCin = 7, kCout = 4;
+constexpr int kCin = 11, kCout = 4;
 
 struct Norm {
-  float shift[4], scale[4], out_scale[4];
+  float shift[4], scale[4], out_scale[4], dscale[4];
+  float noise[4];  // training-input perturbation: uniform, standard deviation noise[k]
+  unsigned long long seed;
   int pad, project;
 };
 
@@ -32,9 +34,12 @@ Norm make_norm(const rpk_sur_config* c) {
     n.shift[k] = c->in_shift[k];
     n.scale[k] = c->in_scale[k];
     n.out_scale[k] = c->out_scale[k];
+    n.dscale[k] = c->in_dscale[k];
   }
   n.pad = c->pad;
   n.project = c->project;
+  for (int k = 0; k < 4; ++k) n.noise[k] = 0.f;
+  n.seed = 0;
   return n;
 }
 
@@ -51,32 +56,59 @@ __device__ __forceinline__ void load_point(const float* blk, int np, int pt, dou
   for (int k = 0; k < 4; ++k) v[k] = (double)blk[(int64_t)k * np + pt];
 }
 
+// Output number n + 1 of the SplitMix64 generator seeded with `seed` (Steele,
+// Lea & Flood, OOPSLA 2014): the state after n + 1 increments of the golden
+// gamma, through the generator's output mix.
+__device__ __forceinline__ uint64_t splitmix64(uint64_t seed, uint64_t n) {
+  uint64_t z = seed + (n + 1) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
 // Fine position p of a tube -> its point index s nx + x.
 __device__ __forceinline__ int point_of(int nx, int p) { return (p & 1) * nx + (p >> 1); }
 
-__global__ void k_pack(const float* __restrict__ store, const rpk_sur_seq* __restrict__ seqs, Norm N,
-                       int margin, float* __restrict__ x, float* __restrict__ target,
-                       float* __restrict__ mask) {
+__global__ void k_pack(const float* __restrict__ store, const float* __restrict__ prev_store,
+                       const rpk_sur_seq* __restrict__ seqs, Norm N, int margin,
+                       float* __restrict__ x, float* __restrict__ target, float* __restrict__ mask) {
   const rpk_sur_seq& S = seqs[blockIdx.y];
   const int l = blockIdx.x * blockDim.x + threadIdx.x;
   if (l >= S.len) return;
   const int np = 2 * S.nx;
   const int p = S.crop + l - N.pad;
   const bool inside = p >= 0 && p < np;
-  double v[4];
+  double v[4], q[4];
   if (inside) {
     load_point(store + S.src, np, point_of(S.nx, p), v);
+    // perturbed source state (training only): v_k + noise_k sqrt(3) (2 u - 1), u uniform
+    // in [0, 1) from draw ((sequence << 32 | l) * 4 + k)
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      if (N.noise[k] != 0.f) {
+        const uint64_t h = splitmix64(N.seed, ((((uint64_t)blockIdx.y) << 32) | (uint64_t)l) * 4 + k);
+        const double u = (double)(h >> 11) * 0x1.0p-53;
+        v[k] += (double)N.noise[k] * 1.7320508075688772 * (2.0 * u - 1.0);
+      }
+    if (S.prev >= 0)
+      load_point(prev_store + S.prev, np, point_of(S.nx, p), q);
+    else
+#pragma unroll
+      for (int k = 0; k < 4; ++k) q[k] = v[k];
   } else {
     const int side = p < 0 ? 0 : 1;
 #pragma unroll
-    for (int k = 0; k < 4; ++k) v[k] = (double)S.res[side][k];
+    for (int k = 0; k < 4; ++k) q[k] = v[k] = (double)S.res[side][k];
   }
   float* xo = x + (S.out + l) * kCin;
 #pragma unroll
-  for (int k = 0; k < 4; ++k) xo[k] = ((float)v[k] - N.shift[k]) / N.scale[k];
-  xo[4] = S.cond[0];
-  xo[5] = S.cond[1];
-  xo[6] = inside ? 1.f : 0.f;
+  for (int k = 0; k < 4; ++k) {
+    xo[k] = ((float)v[k] - N.shift[k]) / N.scale[k];
+    xo[4 + k] = ((float)v[k] - (float)q[k]) / N.dscale[k];
+  }
+  xo[8] = S.cond[0];
+  xo[9] = S.cond[1];
+  xo[10] = inside ? 1.f : 0.f;
   if (S.tgt < 0 || !target) return;
   const bool use = inside && l >= margin && l < S.len - margin;
   float* to = target + (S.out + l) * kCout;
@@ -217,6 +249,27 @@ __global__ void k_totals(const float* __restrict__ state, const rpk_sur_seq* __r
   }
 }
 
+// flags[i] = 1 where a tube's moment block holds a non-positive rho, theta_T or
+// E_R, or a non-finite value.
+__global__ void k_valid(const float* __restrict__ state, const rpk_sur_seq* __restrict__ seqs,
+                        int* __restrict__ flags) {
+  __shared__ int bad;
+  if (threadIdx.x == 0) bad = 0;
+  __syncthreads();
+  const rpk_sur_seq& S = seqs[blockIdx.x];
+  const int np = 2 * S.nx;
+  const float* b = state + S.src;
+  bool mine = false;
+  for (int p = threadIdx.x; p < np; p += blockDim.x) {
+    const float r = b[p], u = b[np + p], th = b[2 * np + p], er = b[3 * np + p];
+    mine |= !(r > 0.f) || !(th > 0.f) || !(er > 0.f) || !isfinite(r) || !isfinite(u) ||
+            !isfinite(th) || !isfinite(er);
+  }
+  if (mine) bad = 1;
+  __syncthreads();
+  if (threadIdx.x == 0) flags[blockIdx.x] = bad;
+}
+
 // Copy whole moment blocks src -> dst for the listed tubes.
 __global__ void k_copy_blocks(const float* __restrict__ src, float* __restrict__ dst,
                               const rpk_sur_seq* __restrict__ seqs) {
@@ -230,8 +283,9 @@ rpk_status check_config(const rpk_sur_config* c) {
   if (c->jump < 1 || c->pad < 0 || c->pad % 4 || c->spot_every < 0)
     return rpk::fail(RPK_ERR_ARG, "jump >= 1, pad >= 0 a multiple of 4, spot_every >= 0");
   for (int k = 0; k < 4; ++k)
-    if (!(c->in_scale[k] != 0.f) || !(c->out_scale[k] != 0.f) || !std::isfinite(c->in_scale[k]) ||
-        !std::isfinite(c->out_scale[k]) || !std::isfinite(c->in_shift[k]))
+    if (!(c->in_scale[k] != 0.f) || !(c->out_scale[k] != 0.f) || !(c->in_dscale[k] != 0.f) ||
+        !std::isfinite(c->in_scale[k]) || !std::isfinite(c->out_scale[k]) ||
+        !std::isfinite(c->in_dscale[k]) || !std::isfinite(c->in_shift[k]))
       return rpk::fail(RPK_ERR_ARG, "scales must be finite and non-zero");
   return RPK_OK;
 }
@@ -248,7 +302,9 @@ struct rpk_rollout {
   std::vector<int64_t> blk;  // float offset of each tube's moment block
   int64_t state_floats = 0, seq_points = 0;
   rpk_batch* batch = nullptr;
-  float *next = nullptr, *lbm = nullptr, *x = nullptr, *y = nullptr;
+  float *next = nullptr, *lbm = nullptr, *init = nullptr, *prev = nullptr, *x = nullptr, *y = nullptr;
+  std::vector<double> trace;  // per tube and window: spot-check L1 error (NaN: no check)
+  int trace_windows = 0;
   rpk_sur_seq* seqs = nullptr;   // ntubes sequence descriptors (active tubes first)
   rpk_sur_seq* lists = nullptr;  // 2 x ntubes descriptors for block copies
   int* flags = nullptr;
@@ -270,7 +326,7 @@ rpk_status ro_alloc(void** p, size_t bytes) {
 
 void free_rollout(rpk_rollout* R) {
   if (R->batch) rpk_batch_destroy(R->batch);
-  void* p[] = {R->next, R->lbm, R->x, R->y, R->seqs, R->lists, R->flags, R->sums};
+  void* p[] = {R->next, R->lbm, R->init, R->prev, R->x, R->y, R->seqs, R->lists, R->flags, R->sums};
   for (void* q : p)
     if (q) cudaFree(q);
   for (auto& e : R->ev)
@@ -288,6 +344,7 @@ rpk_sur_seq make_seq(const rpk_rollout* R, int tube, int64_t out) {
   const rpk_tube& t = R->tubes[tube];
   s.src = R->blk[tube];
   s.tgt = -1;
+  s.prev = -1;
   s.out = out;
   s.nx = t.nx;
   s.len = seq_len(R, tube);
@@ -339,17 +396,24 @@ float elapsed(rpk_rollout* R) {
 extern "C" {
 
 rpk_status rpk_sur_pack(const rpk_sur_config* cfg, const float* store, const rpk_sur_seq* seqs,
-                        int nseq, int maxlen, int margin, float* x, float* target, float* mask,
-                        void* cuda_stream) {
+                        int nseq, int maxlen, int margin, const float* noise, uint64_t seed,
+                        float* x, float* target, float* mask, void* cuda_stream) {
   rpk_status st = check_config(cfg);
   if (st != RPK_OK) return st;
   if (!store || !seqs || !x) return rpk::fail(RPK_ERR_ARG, "NULL argument");
   if (nseq < 0 || maxlen < 0 || margin < 0 || nseq > 65535)
     return rpk::fail(RPK_ERR_ARG, "0 <= nseq <= 65535, maxlen >= 0, margin >= 0");
   if (nseq == 0 || maxlen == 0) return RPK_OK;
+  Norm N = make_norm(cfg);
+  if (noise)
+    for (int k = 0; k < 4; ++k) {
+      if (!(noise[k] >= 0.f) || !std::isfinite(noise[k])) return rpk::fail(RPK_ERR_ARG, "noise must be >= 0");
+      N.noise[k] = noise[k];
+    }
+  N.seed = seed;
   const dim3 grid((unsigned)((maxlen + 255) / 256), (unsigned)nseq);
-  k_pack<<<grid, 256, 0, static_cast<cudaStream_t>(cuda_stream)>>>(store, seqs, make_norm(cfg),
-                                                                    margin, x, target, mask);
+  k_pack<<<grid, 256, 0, static_cast<cudaStream_t>(cuda_stream)>>>(store, store, seqs, N, margin, x,
+                                                                    target, mask);
   RPK_CUDA(cudaGetLastError());
   return RPK_OK;
 }
@@ -400,6 +464,8 @@ rpk_status rpk_rollout_create(rpk_net* net, const rpk_sur_config* cfg, int ntube
     st = rpk_batch_set_config(R->batch, cfg->lbm_threads, std::max(1, cfg->lbm_ctas_per_sm));
   if (st == RPK_OK) st = ro_alloc((void**)&R->next, sizeof(float) * R->state_floats);
   if (st == RPK_OK) st = ro_alloc((void**)&R->lbm, sizeof(float) * R->state_floats);
+  if (st == RPK_OK) st = ro_alloc((void**)&R->init, sizeof(float) * R->state_floats);
+  if (st == RPK_OK) st = ro_alloc((void**)&R->prev, sizeof(float) * R->state_floats);
   if (st == RPK_OK) st = ro_alloc((void**)&R->x, sizeof(float) * kCin * R->seq_points);
   if (st == RPK_OK) st = ro_alloc((void**)&R->y, sizeof(float) * kCout * R->seq_points);
   if (st == RPK_OK) st = ro_alloc((void**)&R->seqs, sizeof(rpk_sur_seq) * ntubes);
@@ -451,8 +517,13 @@ rpk_status rpk_rollout_run(rpk_rollout* R, float* state, int64_t* stats, double*
       E0[i] = tot[2 * i + 1];
     }
   }
+  RPK_CUDA(cudaMemcpyAsync(R->init, state, sizeof(float) * R->state_floats, cudaMemcpyDeviceToDevice,
+                           R->stream));
+  R->trace.assign((size_t)T * std::max(maxJ, 1), std::nan(""));
+  R->trace_windows = maxJ;
   const Norm N = make_norm(&R->cfg);
   std::vector<int> active, lens, steps(T);
+  std::vector<char> has_prev(T, 0);
   std::vector<rpk_sur_seq> h;
   std::vector<int> flags(T);
   std::vector<double> sums(4 * T);
@@ -467,6 +538,7 @@ rpk_status rpk_rollout_run(rpk_rollout* R, float* state, int64_t* stats, double*
     int64_t off = 0;
     for (int a = 0; a < A; ++a) {
       h[a] = make_seq(R, active[a], off);
+      if (has_prev[active[a]]) h[a].prev = h[a].src;  // the same block of R->prev
       lens[a] = h[a].len;
       off += h[a].len;
     }
@@ -474,8 +546,8 @@ rpk_status rpk_rollout_run(rpk_rollout* R, float* state, int64_t* stats, double*
     cudaEventRecord(R->ev[0], R->stream);
     RPK_CUDA(cudaMemcpyAsync(R->seqs, h.data(), sizeof(rpk_sur_seq) * A, cudaMemcpyHostToDevice, R->stream));
     int maxlen = *std::max_element(lens.begin(), lens.end());
-    k_pack<<<dim3((maxlen + 255) / 256, A), 256, 0, R->stream>>>(state, R->seqs, N, 0, R->x, nullptr,
-                                                                 nullptr);
+    k_pack<<<dim3((maxlen + 255) / 256, A), 256, 0, R->stream>>>(state, R->prev, R->seqs, N, 0, R->x,
+                                                                 nullptr, nullptr);
     RPK_CUDA(cudaGetLastError());
     // the network runs on its own stream: the packed inputs must be complete
     RPK_CUDA(cudaStreamSynchronize(R->stream));
@@ -499,31 +571,50 @@ rpk_status rpk_rollout_run(rpk_rollout* R, float* state, int64_t* stats, double*
     RPK_CUDA(cudaMemcpyAsync(flags.data(), R->flags, sizeof(int) * A, cudaMemcpyDeviceToHost, R->stream));
     RPK_CUDA(cudaMemcpyAsync(sums.data(), R->sums, sizeof(double) * 4 * T, cudaMemcpyDeviceToHost, R->stream));
     RPK_CUDA(cudaStreamSynchronize(R->stream));
-    std::vector<int> from_next, from_lbm;
+    std::vector<int> from_next, from_lbm, from_init;
+    const bool anchor = R->cfg.anchor != 0;
     for (int a = 0; a < A; ++a) {
       const int i = active[a];
+      const double dm = std::fabs(sums[2 * a] - M0[i]) / std::fabs(M0[i]);
+      const double de = std::fabs(sums[2 * a + 1] - E0[i]) / std::fabs(E0[i]);
+      const bool valid = !flags[a] && dm <= R->cfg.drift_tol && de <= R->cfg.drift_tol;
+      bool keep_net = !spot && valid, to_lbm = false;
       if (spot) {
-        // the LBM's window is kept; its error stands for the windows up to the next check
+        // the network's window error stands for the windows up to the next check
         const double e = sums[2 * T + 2 * a] / std::max(sums[2 * T + 2 * a + 1], 1e-300);
-        const int ahead = std::min(C - 1, J[i] - j - 1);
+        R->trace[(size_t)i * maxJ + j] = flags[a] ? HUGE_VAL : e;
+        const int ahead = anchor ? std::min(C - 1, J[i] - j - 1) : std::min(C, J[i] - j);
         est[i] += (std::isfinite(e) && !flags[a]) ? e * ahead : HUGE_VAL;
         checks[i] += 1;
-        from_lbm.push_back(i);
-        if (est[i] > R->cfg.l1_tol) fail_step[i] = (j + 1) * jump;
-      } else {
-        const double dm = std::fabs(sums[2 * a] - M0[i]) / std::fabs(M0[i]);
-        const double de = std::fabs(sums[2 * a + 1] - E0[i]) / std::fabs(E0[i]);
-        if (flags[a] || !(dm <= R->cfg.drift_tol) || !(de <= R->cfg.drift_tol)) {
-          fail_step[i] = j * jump;  // the pre-window state stays
+        const bool over = !(est[i] <= R->cfg.l1_tol);
+        if (anchor) {
+          to_lbm = true;  // the LBM's window is kept
+          if (over) fail_step[i] = (j + 1) * jump;
         } else {
-          windows[i] += 1;
-          from_next.push_back(i);
+          keep_net = valid && !over;
         }
       }
+      if (keep_net) {
+        windows[i] += 1;
+        from_next.push_back(i);
+      } else if (to_lbm) {
+        from_lbm.push_back(i);
+      } else if (anchor) {
+        fail_step[i] = j * jump;  // the pre-window state stays
+      } else {
+        fail_step[i] = 0;  // the LBM runs the tube from its initial state
+        from_init.push_back(i);
+      }
     }
-    rpk_status st2 = copy_blocks(R, R->next, state, from_next, R->lists);
+    // the window's start becomes the next window's previous state
+    std::vector<int> kept(from_next);
+    kept.insert(kept.end(), from_lbm.begin(), from_lbm.end());
+    rpk_status st2 = copy_blocks(R, state, R->prev, kept, R->lists);
+    if (st2 == RPK_OK) st2 = copy_blocks(R, R->next, state, from_next, R->lists);
     if (st2 == RPK_OK) st2 = copy_blocks(R, R->lbm, state, from_lbm, R->lists + T);
+    if (st2 == RPK_OK) st2 = copy_blocks(R, R->init, state, from_init, R->lists);
     if (st2 != RPK_OK) return st2;
+    for (int i : kept) has_prev[i] = 1;
   }
   // the LBM finishes every tube: fallback tubes from their last accepted state,
   // the others for their remainder steps
@@ -545,13 +636,43 @@ rpk_status rpk_rollout_run(rpk_rollout* R, float* state, int64_t* stats, double*
     st = copy_blocks(R, R->lbm, state, rest, R->lists);
     if (st != RPK_OK) return st;
   }
+  // a tube whose final moments are invalid is run again by the LBM from its
+  // initial state
+  std::vector<int> rerun(T, 0), again;
+  {
+    std::vector<rpk_sur_seq> hs(T);
+    for (int i = 0; i < T; ++i) hs[i] = make_seq(R, i, 0);
+    RPK_CUDA(cudaMemcpyAsync(R->seqs, hs.data(), sizeof(rpk_sur_seq) * T, cudaMemcpyHostToDevice, R->stream));
+    k_valid<<<T, 256, 0, R->stream>>>(state, R->seqs, R->flags);
+    RPK_CUDA(cudaGetLastError());
+    RPK_CUDA(cudaMemcpyAsync(flags.data(), R->flags, sizeof(int) * T, cudaMemcpyDeviceToHost, R->stream));
+    RPK_CUDA(cudaStreamSynchronize(R->stream));
+    for (int i = 0; i < T; ++i)
+      if (flags[i]) {
+        rerun[i] = 1;
+        again.push_back(i);
+      }
+  }
+  double t_rerun = 0.0;
+  if (!again.empty()) {
+    std::vector<int> full(T, 0);
+    for (int i : again) full[i] = R->tubes[i].nsteps;
+    cudaEventRecord(R->ev[0], R->stream);
+    rpk_status st = lbm_run(R, R->init, full);
+    if (st != RPK_OK) return st;
+    cudaEventRecord(R->ev[1], R->stream);
+    t_rerun = elapsed(R);
+    st = copy_blocks(R, R->lbm, state, again, R->lists);
+    if (st != RPK_OK) return st;
+  }
   RPK_CUDA(cudaStreamSynchronize(R->stream));
   if (stats)
     for (int i = 0; i < T; ++i) {
-      stats[4 * i] = fail_step[i];
-      stats[4 * i + 1] = windows[i];
-      stats[4 * i + 2] = checks[i];
-      stats[4 * i + 3] = steps[i];
+      stats[5 * i] = rerun[i] ? 0 : fail_step[i];
+      stats[5 * i + 1] = windows[i];
+      stats[5 * i + 2] = checks[i];
+      stats[5 * i + 3] = rerun[i] ? R->tubes[i].nsteps : steps[i];
+      stats[5 * i + 4] = rerun[i];
     }
   if (est_out)
     for (int i = 0; i < T; ++i) est_out[i] = est[i];
@@ -559,7 +680,15 @@ rpk_status rpk_rollout_run(rpk_rollout* R, float* state, int64_t* stats, double*
     ms[0] = t_net;
     ms[1] = t_spot;
     ms[2] = t_fb;
+    ms[3] = t_rerun;
   }
+  return RPK_OK;
+}
+
+rpk_status rpk_rollout_errors(const rpk_rollout* R, double* out, int* windows) {
+  if (!R || !windows) return rpk::fail(RPK_ERR_ARG, "NULL argument");
+  *windows = R->trace_windows;
+  if (out && !R->trace.empty()) std::memcpy(out, R->trace.data(), sizeof(double) * R->trace.size());
   return RPK_OK;
 }
 

@@ -5,9 +5,10 @@ conservative update all run in librpk's kernels (see ``Net``, ``sur_pack``,
 ``Rollout``); this module draws minibatches and marshals descriptors.
 
 A training pair is (moments at step 32 k, moments at step 32 (k + 1)) of one
-tube; the network sees a crop of the tube padded with its reservoir states and
-learns the increments of the conserved densities (rho, rho u_x, E, E_R) over
-the window. The paper has no learned component; the data come from its
+tube, with the moments at step 32 (k - 1) as the previous window (none for
+k = 0); the network sees a crop of the tube padded with its reservoir states
+and learns the increments of the conserved densities (rho, rho u_x, E, E_R)
+over the window. The paper has no learned component; the data come from its
 method."""
 import math
 
@@ -17,13 +18,13 @@ import paper_2201_05280_gb300 as rpk
 
 GAMMA = 1.4
 PR = 0.71
-CIN, COUT = 7, 4
+CIN, COUT = 11, 4
 
-# numpy view of rpk_sur_seq (80 bytes)
-SEQ_DTYPE = np.dtype([("src", "<i8"), ("tgt", "<i8"), ("out", "<i8"), ("nx", "<i4"),
-                      ("len", "<i4"), ("crop", "<i4"), ("pad_", "<i4"), ("res", "<f4", (2, 4)),
-                      ("cond", "<f4", (2,))])
-assert SEQ_DTYPE.itemsize == 80
+# numpy view of rpk_sur_seq (88 bytes)
+SEQ_DTYPE = np.dtype([("src", "<i8"), ("tgt", "<i8"), ("prev", "<i8"), ("out", "<i8"),
+                      ("nx", "<i4"), ("len", "<i4"), ("crop", "<i4"), ("pad_", "<i4"),
+                      ("res", "<f4", (2, 4)), ("cond", "<f4", (2,))])
+assert SEQ_DTYPE.itemsize == 88
 
 # Feature and output scales for the sweep's states (left state rho = 1,
 # theta = theta0; right states down to rho ~ 0.12, theta ~ 0.42 theta0; flows
@@ -32,7 +33,7 @@ assert SEQ_DTYPE.itemsize == 80
 def default_config(theta0, **kw):
     base = dict(jump=32, pad=128, spot_every=8, project=1, drift_tol=1e-4, l1_tol=1e-2,
                 in_shift=(0.55, 0.0, theta0, 0.17), in_scale=(0.3, 0.3, 0.1, 0.1),
-                out_scale=(0.05, 0.03, 0.05, 0.03))
+                out_scale=(0.015, 0.011, 0.013, 0.0045), in_dscale=(0.015, 0.02, 0.005, 0.005))
     base.update(kw)
     return rpk.SurConfig.make(**base)
 
@@ -90,7 +91,7 @@ class TrainingSet:
         bt.close()
         self.tubes, self.cond = tubes, np.asarray(cond, np.float32)
         self.res = np.stack([reservoirs(t) for t in tubes])
-        offs, src, tgt, tube_of = 0, [], [], []
+        offs, src, tgt, prev, tube_of = 0, [], [], [], []
         flat = []
         for i, s in enumerate(snaps):
             n = s.shape[0]
@@ -98,12 +99,14 @@ class TrainingSet:
             for k in range(n - 1):
                 src.append(offs + k * blk)
                 tgt.append(offs + (k + 1) * blk)
+                prev.append(offs + (k - 1) * blk if k > 0 else -1)
                 tube_of.append(i)
             flat.append(s.reshape(-1))
             offs += n * blk
         self.store = torch.from_numpy(np.concatenate(flat)).cuda()
         self.src = np.asarray(src, np.int64)
         self.tgt = np.asarray(tgt, np.int64)
+        self.prev = np.asarray(prev, np.int64)
         self.tube = np.asarray(tube_of, np.int64)
         self.nx = np.array([t["nx"] for t in tubes], np.int32)
 
@@ -118,7 +121,7 @@ class TrainingSet:
         tb = self.tube[idx]
         nx = self.nx[tb]
         full = 2 * nx + 2 * pad
-        d["src"], d["tgt"] = self.src[idx], self.tgt[idx]
+        d["src"], d["tgt"], d["prev"] = self.src[idx], self.tgt[idx], self.prev[idx]
         d["out"] = np.arange(n, dtype=np.int64) * crop_len
         d["nx"], d["len"] = nx, crop_len
         d["crop"] = (rng.uniform(size=n) * np.maximum(full - crop_len, 0) + 0.5).astype(np.int32)
@@ -133,10 +136,13 @@ def _upload(desc):
 
 
 def train(net, cfg, data, steps, batch=32, crop_len=1024, lr=1e-3, lr_end=1e-5, margin=None,
-          seed=0, log_every=0):
+          seed=0, noise=None, log_every=0):
     """Adam on the masked MSE of the normalised increments; cosine learning
     rate from lr to lr_end. The loss mask leaves out points closer than the
-    network's receptive radius to a crop edge. Returns the loss history."""
+    network's receptive radius to a crop edge. ``noise`` (4 standard
+    deviations of rho, u_x, theta_T, E_R) perturbs the source states, so that
+    the network learns to undo errors of its own earlier windows. Returns the
+    loss history."""
     import ctypes
     import torch
     lib = rpk.load_library()
@@ -146,13 +152,14 @@ def train(net, cfg, data, steps, batch=32, crop_len=1024, lr=1e-3, lr_end=1e-5, 
     x = torch.zeros((batch, crop_len, CIN), device="cuda")
     t = torch.zeros((batch, crop_len, COUT), device="cuda")
     m = torch.zeros((batch, crop_len), device="cuda")
+    nz = (ctypes.c_float * 4)(*[float(v) for v in noise]) if noise is not None else None
     hist = []
     for it in range(steps):
         idx = rng.integers(0, len(data), size=batch)
         desc = _upload(data.descriptors(idx, crop_len, cfg.pad, rng))
         rpk._check(lib.rpk_sur_pack(ctypes.byref(cfg), rpk._dev_f32(data.store), ctypes.c_void_p(desc.data_ptr()),
-                                    batch, crop_len, margin, rpk._dev_f32(x), rpk._dev_f32(t),
-                                    rpk._dev_f32(m), None))
+                                    batch, crop_len, margin, nz, seed * 1000003 + it,
+                                    rpk._dev_f32(x), rpk._dev_f32(t), rpk._dev_f32(m), None))
         loss = net.loss_grad(x, t, m)
         a = lr_end + 0.5 * (lr - lr_end) * (1 + math.cos(math.pi * it / max(1, steps)))
         net.adam(a)

@@ -95,7 +95,7 @@ def test_device_blocks_match_fields_and_reinitialise():
 def _cfg(**kw):
     base = dict(jump=JUMP, pad=16, spot_every=0, project=0, drift_tol=1e300, l1_tol=1e300,
                 in_shift=(0.5, 0.0, T0, 0.15), in_scale=(0.3, 0.3, 0.1, 0.1),
-                out_scale=(0.02, 0.01, 0.03, 0.01))
+                out_scale=(0.02, 0.01, 0.03, 0.01), in_dscale=(0.01, 0.02, 0.004, 0.005))
     base.update(kw)
     return rpk.SurConfig.make(**base)
 
@@ -108,7 +108,9 @@ def test_pack_matches_oracle():
     blocks = [np.stack([rng.uniform(0.2, 1, 2 * n), rng.normal(0, 0.2, 2 * n), rng.uniform(0.15, 0.4, 2 * n),
                         rng.uniform(0.05, 0.4, 2 * n)]) for n in nxs]
     tgts = [b * rng.uniform(0.9, 1.1, b.shape) for b in blocks]
-    store = np.concatenate([b.ravel() for b in blocks] + [b.ravel() for b in tgts]).astype(np.float32)
+    prevs = [b * rng.uniform(0.95, 1.05, b.shape) for b in blocks]
+    store = np.concatenate([b.ravel() for b in blocks] + [b.ravel() for b in tgts] +
+                           [b.ravel() for b in prevs]).astype(np.float32)
     offs = np.cumsum([0] + [8 * n for n in nxs])
     toff = offs[-1]
     seqs, refs = [], []
@@ -116,11 +118,15 @@ def test_pack_matches_oracle():
     for i, (n, crop, length, margin) in enumerate(zip(nxs, [0, 10, 3], [48, 36, 60], [0, 4, 4])):
         res = rng.uniform(0.1, 1.0, (2, 4))
         cond = rng.normal(size=2)
-        seqs.append(dict(src=offs[i], tgt=toff + offs[i], out=out, nx=n, len=length, crop=crop, res=res, cond=cond))
+        prev = 2 * toff + offs[i] if i != 1 else -1  # the middle sequence has no previous window
+        seqs.append(dict(src=offs[i], tgt=toff + offs[i], prev=prev, out=out, nx=n, len=length, crop=crop,
+                         res=res, cond=cond))
         refs.append(S.pack(blocks[i].astype(np.float32).astype(np.float64),
                            tgts[i].astype(np.float32).astype(np.float64), n, res.astype(np.float32),
                            cond.astype(np.float32), cfg.pad, crop, length, margin, list(cfg.in_shift),
-                           list(cfg.in_scale), list(cfg.out_scale)) + (margin,))
+                           list(cfg.in_scale), list(cfg.out_scale),
+                           prev=prevs[i].astype(np.float32).astype(np.float64) if i != 1 else None,
+                           dscale=list(cfg.in_dscale)) + (margin,))
         out += length
     for i, sq in enumerate(seqs):
         x, t, m = rpk.sur_pack(cfg, torch.tensor(store, device="cuda"), [sq], margin=refs[i][3])
@@ -128,6 +134,19 @@ def test_pack_matches_oracle():
         np.testing.assert_allclose(x.cpu().numpy()[sl], refs[i][0], rtol=2.4e-7, atol=1e-30)
         np.testing.assert_array_equal(m.cpu().numpy()[sl], refs[i][2])
         np.testing.assert_allclose(t.cpu().numpy()[sl], refs[i][1], rtol=1e-6, atol=1e-6)
+    # perturbed sources: all sequences in one call (sequence index = draw stream)
+    noise = (1e-3, 2e-3, 5e-4, 5e-4)
+    x, t, m = rpk.sur_pack(cfg, torch.tensor(store, device="cuda"), seqs, margin=0, noise=noise, seed=99)
+    for i, sq in enumerate(seqs):
+        ref = S.pack(blocks[i].astype(np.float32).astype(np.float64),
+                     tgts[i].astype(np.float32).astype(np.float64), nxs[i], sq["res"].astype(np.float32),
+                     np.asarray(sq["cond"], np.float32), cfg.pad, sq["crop"], sq["len"], 0,
+                     list(cfg.in_shift), list(cfg.in_scale), list(cfg.out_scale),
+                     prev=prevs[i].astype(np.float32).astype(np.float64) if i != 1 else None,
+                     dscale=list(cfg.in_dscale), noise=noise, seed=99, seq_index=i)
+        sl = slice(sq["out"], sq["out"] + sq["len"])
+        np.testing.assert_allclose(x.cpu().numpy()[sl], ref[0], rtol=1e-6, atol=1e-6)
+        np.testing.assert_allclose(t.cpu().numpy()[sl], ref[1], rtol=1e-5, atol=1e-5)
 
 
 @pytest.mark.parametrize("project", [0, 1])
@@ -159,7 +178,7 @@ def test_apply_matches_oracle(project):
 
 
 def _net(head_bias=None):
-    net = rpk.Net(7, 4, 16, 0, seed=1)
+    net = rpk.Net(11, 4, 16, 0, seed=1)
     v = np.zeros(net.num_params, dtype=np.float32)
     if head_bias is not None:
         v[-16:] = head_bias
@@ -260,3 +279,26 @@ def test_rollout_drift_check_and_projection():
     ref = _lbm(tubes, blk, [t["nsteps"] - JUMP * j for t, j in zip(tubes, J)])
     np.testing.assert_array_equal(state.cpu().numpy(), ref.cpu().numpy())
     R.close()
+
+
+def test_rollout_without_anchor_reruns_handed_tubes_from_the_start():
+    tubes, f = _tubes(4, (40, 100), seed=28, min_steps=100)
+    blk = _blocks(tubes, f)
+    net = _net()
+    R = rpk.Rollout(net, _cfg(spot_every=4, l1_tol=0.0, anchor=0), tubes, [t["cond"] for t in tubes])
+    state = blk.clone()
+    st = R.run(state)
+    np.testing.assert_array_equal(st["fail_step"], 0)
+    np.testing.assert_array_equal(st["checks"], 1)
+    np.testing.assert_array_equal(st["lbm_steps"], [t["nsteps"] for t in tubes])
+    ref = _lbm(tubes, blk, [t["nsteps"] for t in tubes])
+    np.testing.assert_array_equal(state.cpu().numpy(), ref.cpu().numpy())
+    # with a generous bound the zero network's windows are all kept
+    R2 = rpk.Rollout(net, _cfg(spot_every=4, l1_tol=10.0, anchor=0), tubes, [t["cond"] for t in tubes])
+    state = blk.clone()
+    st = R2.run(state)
+    J = [t["nsteps"] // JUMP for t in tubes]
+    np.testing.assert_array_equal(st["windows"], J)
+    np.testing.assert_array_equal(st["fail_step"], -1)
+    R.close()
+    R2.close()

@@ -143,11 +143,17 @@ def test_pack_padding_and_features():
     res = np.array([[1.0, 0.0, 0.3, 0.3], [0.5, 0.0, 0.25, 0.12]])
     x, _, _ = S.pack(src, None, nx, res, (0.7, -0.2), pad, 0, 2 * nx + 2 * pad, 0,
                      (0, 0, 0, 0), (1, 1, 1, 1), (1, 1, 1, 1))
-    assert np.all(x[:pad, 6] == 0) and np.all(x[pad:pad + 2 * nx, 6] == 1) and np.all(x[pad + 2 * nx:, 6] == 0)
+    assert np.all(x[:pad, 10] == 0) and np.all(x[pad:pad + 2 * nx, 10] == 1) and np.all(x[pad + 2 * nx:, 10] == 0)
+    assert np.all(x[:, 4:8] == 0)  # no previous window
     np.testing.assert_allclose(x[:pad, :4], np.broadcast_to(res[0], (pad, 4)), rtol=1e-7)
     np.testing.assert_allclose(x[pad + 2 * nx:, :4], np.broadcast_to(res[1], (pad, 4)), rtol=1e-7)
     np.testing.assert_allclose(x[pad:pad + 2 * nx, :4].T, S.position_order(src, nx), rtol=1e-7)
-    np.testing.assert_allclose(x[:, 4:6], np.broadcast_to([0.7, -0.2], (2 * nx + 2 * pad, 2)), rtol=1e-7)
+    np.testing.assert_allclose(x[:, 8:10], np.broadcast_to([0.7, -0.2], (2 * nx + 2 * pad, 2)), rtol=1e-7)
+    prev = src * 0.9
+    x2, _, _ = S.pack(src, None, nx, res, (0.7, -0.2), pad, 0, 2 * nx + 2 * pad, 0,
+                      (0, 0, 0, 0), (1, 1, 1, 1), (1, 1, 1, 1), prev=prev, dscale=(2, 2, 2, 2))
+    np.testing.assert_allclose(x2[pad:pad + 2 * nx, 4:8].T, S.position_order(0.05 * src, nx), rtol=1e-5)
+    assert np.all(x2[:pad, 4:8] == 0) and np.all(x2[pad + 2 * nx:, 4:8] == 0)
 
 
 def test_apply_inverts_pack_targets():
@@ -192,3 +198,27 @@ def test_apply_projection_conserves_mass_and_energy():
     y3 = np.zeros((2 * nx, 4))
     y3[3, 0] = -1e3
     assert S.apply(src, y3, nx, pad, 0, out_scale, project=False)[1]
+
+
+def test_splitmix64_reference_values():
+    # first outputs of SplitMix64 seeded with 0, as published with the generator
+    assert S.splitmix64(0, 0) == 0xE220A8397B1DCDAF
+    assert S.splitmix64(0, 1) == 0x6E789E6AA1B965F4
+    assert S.splitmix64(0, 2) == 0x06C45D188009454F
+
+
+def test_pack_noise_perturbs_source_state():
+    rng = np.random.default_rng(11)
+    nx, pad = 6, 4
+    src, tgt = _tube_block(nx, rng), _tube_block(nx, rng)
+    args = (src, tgt, nx, np.ones((2, 4)), (0, 0), pad, 0, 2 * nx + 2 * pad, 0, (0, 0, 0, 0), (1, 1, 1, 1),
+            (1, 1, 1, 1))
+    x0, t0, _ = S.pack(*args)
+    x1, t1, _ = S.pack(*args, noise=(1e-2, 0, 0, 2e-3), seed=7)
+    d = x1[:, :4] - x0[:, :4]
+    assert np.all(d[:pad] == 0) and np.all(d[pad + 2 * nx:] == 0)  # padding is not perturbed
+    assert np.all(d[:, 1:3] == 0)
+    assert 0 < np.abs(d[pad:pad + 2 * nx, 0]).max() <= 1.8e-2
+    # the target undoes the perturbation: U(tgt) - U(v + e) for rho is the old target minus e
+    np.testing.assert_allclose(t1[pad:pad + 2 * nx, 0], t0[pad:pad + 2 * nx, 0] - d[pad:pad + 2 * nx, 0],
+                               atol=1e-6)
