@@ -49,12 +49,12 @@ class Params(ctypes.Structure):
     _fields_ = [("delta", ctypes.c_double), ("tau", ctypes.c_double),
                 ("tau1", ctypes.c_double), ("b", ctypes.c_double),
                 ("kr", ctypes.c_double), ("dt", ctypes.c_double),
-                ("nsub", ctypes.c_int), ("bcx", ctypes.c_int)]
+                ("nsub", ctypes.c_int), ("bcx", ctypes.c_int), ("diff", ctypes.c_int)]
 
     def __repr__(self):
-        return ("Params(delta=%g, tau=%g, tau1=%g, b=%g, kr=%g, dt=%g, nsub=%d, bcx=%d)"
+        return ("Params(delta=%g, tau=%g, tau1=%g, b=%g, kr=%g, dt=%g, nsub=%d, bcx=%d, diff=%d)"
                 % (self.delta, self.tau, self.tau1, self.b, self.kr, self.dt,
-                   self.nsub, self.bcx))
+                   self.nsub, self.bcx, self.diff))
 
 
 _lib = None
@@ -74,6 +74,7 @@ def _configure(lib):
         "ora_point_f": (None, [P, _dp, d, _dp]),
         "ora_init": (i, [P, i, i, i, _dp, _dp, _dp, _dp, _dp, _dp]),
         "ora_step": (i, [P, i, i, i, _dp, _dp, _dp, _dp, l]),
+        "ora_diffuse_be_line": (i, [i, d, d, _dp, _dp, _dp, d, d, d, d]),
         "ora_fields": (None, [P, i, i, i, _dp, _dp, _dp, _dp, _dp, _dp, _dp]),
         "ora_diag": (None, [P, i, i, i, _dp, _dp, _dp]),
     }
@@ -156,9 +157,23 @@ def target(rho, u, Lam):
     return f
 
 
-def make_params(delta, tau, tau1, b=0.0, kr=0.0, dt=1.0, nsub=1, bcx=0):
+def make_params(delta, tau, tau1, b=0.0, kr=0.0, dt=1.0, nsub=1, bcx=0, diff=0):
+    """diff = 0: FTCS sub-steps of the rotational diffusion (Sec. 5); 1: one
+    backward-Euler step per sublattice line (variant for quasi-1-D tubes)."""
     return Params(float(delta), float(tau), float(tau1), float(b), float(kr), float(dt),
-                  int(nsub), int(bcx))
+                  int(nsub), int(bcx), int(diff))
+
+
+def diffuse_be_line(delta, dt, rho, kap, Er, thl, kl, thr, kr):
+    """The backward-Euler diffusion stage on one line (ora_diffuse_be_line);
+    returns the new Er."""
+    Er = _f64(Er).copy()
+    rc = _load().ora_diffuse_be_line(len(Er), float(delta), float(dt), _ptr(_f64(rho)),
+                                     _ptr(_f64(kap)), _ptr(Er), float(thl), float(kl),
+                                     float(thr), float(kr))
+    if rc:
+        raise MemoryError("ora_diffuse_be_line")
+    return Er
 
 
 def point_init(P, rho, u, T, R):
@@ -219,6 +234,8 @@ class State:
             raise ValueError("bcx=1 needs reservoir states")
         rc = _load().ora_step(ctypes.byref(self.P), self.nx, self.ny, self.nz, _ptr(res),
                               _ptr(self.g), _ptr(self.Er), _ptr(self.uprev), int(n))
+        if rc == 2:
+            raise ValueError("the backward-Euler diffusion variant needs ny = nz = 1 and bcx = 1")
         if rc != 0:
             raise MemoryError("oracle step could not allocate its work arrays")
         self.t += int(n)

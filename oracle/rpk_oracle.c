@@ -61,6 +61,8 @@ typedef struct {
     double dt;    /* time step (1 in lattice units) */
     int nsub;     /* FTCS sub-steps of the rotational diffusion per time step */
     int bcx;      /* 0: periodic in x; 1: fixed reservoirs beyond both x ends */
+    int diff;     /* rotational diffusion: 0 FTCS sub-steps (Sec. 5); 1 one backward-Euler
+                     step (variant for quasi-1-D tubes: ny = nz = 1, bcx = 1) */
 } ora_params;
 
 static void put(int i, double cx, double cy, double cz, double w)
@@ -459,6 +461,48 @@ int ora_init(const ora_params *P, int nx, int ny, int nz, const double *rho, con
 }
 
 /*
+ * Backward-Euler variant of the diffusion stage on one line of n points with
+ * reservoir ends (the variant for quasi-1-D tubes): the flux-form equation
+ * dEr/dt = d/dx(kappa_R d theta_R/dx), theta_R = 2 Er/(delta rho), taken in one
+ * implicit step of dt with the face coefficients of the explicit scheme:
+ *   (delta rho_p / 2) th_p - dt [K+ (th_{p+1} - th_p) - K- (th_p - th_{p-1})] = Er_p,
+ *   K+- = (kap_p + kap_{p+-1}) / 2,
+ * where th_{-1} = thl, kap_{-1} = kl (low-x reservoir) and th_n = thr,
+ * kap_n = kr (high-x reservoir). The tridiagonal system is solved by Gaussian
+ * elimination without pivoting (the Thomas algorithm; the matrix is strictly
+ * diagonally dominant), then Er_p = delta rho_p th_p / 2.
+ */
+int ora_diffuse_be_line(int n, double delta, double dt, const double *rho, const double *kap,
+                        double *Er, double thl, double kl, double thr, double kr)
+{
+    double *cp = (double *)malloc(sizeof(double) * n);
+    double *rp = (double *)malloc(sizeof(double) * n);
+    int p;
+    if (!cp || !rp) {
+        free(cp); free(rp);
+        return 1;
+    }
+    for (p = 0; p < n; p++) {
+        const double km = 0.5 * (kap[p] + (p > 0 ? kap[p - 1] : kl));
+        const double kp = 0.5 * (kap[p] + (p < n - 1 ? kap[p + 1] : kr));
+        const double a = p > 0 ? -dt * km : 0.0;
+        const double c = p < n - 1 ? -dt * kp : 0.0;
+        const double b = 0.5 * delta * rho[p] + dt * (km + kp);
+        double r = Er[p];
+        double m;
+        if (p == 0) r += dt * km * thl;
+        if (p == n - 1) r += dt * kp * thr;
+        m = (p > 0) ? b - a * cp[p - 1] : b;
+        cp[p] = c / m;
+        rp[p] = (p > 0) ? (r - a * rp[p - 1]) / m : r / m;
+    }
+    for (p = n - 2; p >= 0; p--) rp[p] -= cp[p] * rp[p + 1]; /* rp now holds theta_R */
+    for (p = 0; p < n; p++) Er[p] = 0.5 * delta * rho[p] * rp[p];
+    free(cp); free(rp);
+    return 0;
+}
+
+/*
  * nsteps time steps. Each step, in this order:
  *   1. collide every point (moments, recovery, targets, relaxation, and the
  *      rotational exchange), keeping rho, u and kappa_R of time t;
@@ -474,7 +518,9 @@ int ora_init(const ora_params *P, int nx, int ny, int nz, const double *rho, con
  *   4. diffuse: nsub FTCS sub-steps of dt/nsub of the flux-form equation
  *      dEr/dt = div(kappa_R grad theta_R), theta_R = 2 Er/(delta rho), face
  *      coefficients the mean of the two kappa_R values (Sec. 5, step 3, with
- *      eq. rotHeatFlux_simple; E_R = delta rho theta_R / 2, Sec. 3).
+ *      eq. rotHeatFlux_simple; E_R = delta rho theta_R / 2, Sec. 3); with
+ *      diff = 1 instead one backward-Euler step per sublattice line
+ *      (ora_diffuse_be_line; quasi-1-D tubes only).
  * res (bcx = 1 only): 12 doubles, rho, ux, uy, uz, T, R of the low-x and then
  * the high-x reservoir.
  */
@@ -499,6 +545,10 @@ int ora_step(const ora_params *P, int nx, int ny, int nz, const double *res, dou
         return 1;
     }
     need_lattice();
+    if (P->diff == 1 && (ny != 1 || nz != 1 || P->bcx != 1)) {
+        free(gs); free(rho); free(u); free(kap); free(Ep); free(Ec); free(th); free(v);
+        return 2;
+    }
     if (P->bcx == 1) {
         make_ghost(P, res, &gh[0]);
         make_ghost(P, res + 6, &gh[1]);
@@ -544,7 +594,21 @@ int ora_step(const ora_params *P, int nx, int ny, int nz, const double *res, dou
             Ec[p] = 0.5 * (Er[p] + Ep[p] - P->dt * div);
         }
         memcpy(Er, Ec, sizeof(double) * N);
-        /* 4. FTCS diffusion sub-steps */
+        /* 4. diffusion: backward Euler per sublattice line (variant) ... */
+        if (P->diff == 1) {
+            int sl;
+            for (sl = 0; sl < 2; sl++) {
+                const long o = (long)sl * nx;
+                if (ora_diffuse_be_line(nx, P->delta, P->dt, rho + o, kap + o, Er + o,
+                                        2.0 * gh[0].Er / (P->delta * gh[0].rho), gh[0].kap,
+                                        2.0 * gh[1].Er / (P->delta * gh[1].rho), gh[1].kap)) {
+                    free(gs); free(rho); free(u); free(kap); free(Ep); free(Ec); free(th); free(v);
+                    return 1;
+                }
+            }
+            continue;
+        }
+        /* ... or FTCS sub-steps */
         for (k = 0; k < P->nsub; k++) {
             const double h = P->dt / P->nsub;
             for (p = 0; p < N; p++) th[p] = 2.0 * Er[p] / (P->delta * rho[p]);
