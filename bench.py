@@ -35,6 +35,7 @@ THETA0 = 0.2948964908710633
 GAS = dict(gamma=1.4, nu=0.02, lam=0.6, Pr=0.71, b=0.0)
 STORE_BYTES = {"f64": 8, "f32": 4, "f16dev": 2, "bf16dev": 2}
 FALLBACK_HBM_GBS = 6800.0
+FALLBACK_BF16_TFLOPS = 1900.0  # burst; about 1700 sustained
 
 
 def algorithmic_bytes_per_point(prec):
@@ -59,6 +60,22 @@ def load_peaks():
     except (OSError, ValueError):
         pass
     return FALLBACK_HBM_GBS, "fallback"
+
+
+def load_bf16_peak(sustained=False):
+    """Dense BF16 tensor peak in TFLOP/s: the measured cuBLAS figure if the
+    peaks file holds one, else the fallback."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    keys = ("bf16_tflops_sustained",) if sustained else ("bf16_tflops",)
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        for k in keys:
+            if k in d:
+                return float(d[k]), "measured"
+    except (OSError, ValueError):
+        pass
+    return (1700.0 if sustained else FALLBACK_BF16_TFLOPS), "fallback"
 
 
 def ncu_traffic(prec):
@@ -220,6 +237,7 @@ def run_batch(args):
         tubes.append({"nx": sp["nx"], "nsteps": sp["nsteps"], "relax": r, "res": sp["res"]})
     stream = torch.cuda.Stream()
     bt = rpk.Batch(tubes, precision="f32", save_every=32, stream=stream)
+    bt.set_diffusion(args.diffusion)
     bt.init_fields(f["rho"], f["u"], f["T"], f["R"])
     tune = bt.autotune()
     torch.cuda.synchronize()
@@ -241,7 +259,7 @@ def run_batch(args):
                        "points": int(sum(2 * t["nx"] for t in tubes)),
                        "point_updates": int(updates), "save_every": 32,
                        "lengths": [500, 4000], "pressure_ratio": [2, 20], "kn": [1e-3, 1e-1],
-                       "eta_B_over_eta": [0.3, 2.0]},
+                       "eta_B_over_eta": [0.3, 2.0], "rotational_diffusion": args.diffusion},
             "autotune": tune, "gpu_launches": 1, "all_finite": finite,
             "clocks": clk.summary()}
     print(json.dumps(line))
@@ -267,7 +285,7 @@ def run_surrogate(args):
     t0 = time.time()
     specs, f = I.tube_sweep(args.train_tubes, THETA0, seed=args.train_seed)
     tubes, cond = SG.make_tubes(specs, f, THETA0)
-    data = SG.TrainingSet(tubes, cond, f)
+    data = SG.TrainingSet(tubes, cond, f, diffusion=args.diffusion)
     torch.cuda.synchronize()
     t_data = time.time() - t0
     n_pairs = len(data)
@@ -285,6 +303,7 @@ def run_surrogate(args):
     etubes, econd = SG.make_tubes(specs, f, THETA0)
     blk0 = SG.initial_blocks(etubes, f)
     bt = rpk.Batch(etubes, precision="f32", save_every=1 << 30)
+    bt.set_diffusion(args.diffusion)
     bt.init_fields(f["rho"], f["u"], f["T"], f["R"])
     tune = bt.autotune()
     e0 = torch.cuda.Event(enable_timing=True)
@@ -303,9 +322,35 @@ def run_surrogate(args):
     ref = ref.cpu().numpy()
     offs = bt.block_offsets
     bt.close()
+    # the network alone: one ragged forward pass over every held-out tube
+    # (padded with its reservoirs), timed with CUDA events on the network's stream
+    seqs, out = [], 0
+    for o, t, c in zip(offs, etubes, econd):
+        L = (2 * t["nx"] + 2 * cfg.pad + 3) // 4 * 4
+        seqs.append(dict(src=int(o), out=out, nx=t["nx"], len=L, res=SG.reservoirs(t), cond=c))
+        out += L
+    xin, _, _ = rpk.sur_pack(cfg, blk0, seqs)
+    lens = [d["len"] for d in seqs]
+    for _ in range(3):
+        net.forward_ragged(xin, lens)
+    torch.cuda.synchronize()
+    fw = []
+    for _ in range(5):
+        e0.record()
+        net.forward_ragged(xin, lens)
+        e1.record()
+        torch.cuda.synchronize()
+        fw.append(e0.elapsed_time(e1))
+    fwd_ms = statistics.median(fw)
+    coarse = sum(lens) // 4
+    w = args.width
+    flop_pos = 2 * (4 * SG.CIN * w + args.blocks * 2 * 5 * w * w + w * 4 * SG.COUT)
+    fwd_tflops = coarse * flop_pos / (fwd_ms * 1e-3) / 1e12
+    peak = load_bf16_peak()
     ccfg = SG.default_config(THETA0, spot_every=args.spot_every, l1_tol=args.l1_tol,
                              anchor=int(args.anchor), lbm_threads=tune["threads"],
-                             lbm_ctas_per_sm=tune["ctas_per_sm"])
+                             lbm_ctas_per_sm=tune["ctas_per_sm"],
+                             lbm_diffusion=1 if args.diffusion == "implicit" else 0)
     R = rpk.Rollout(net, ccfg, etubes, econd)
     st = blk0.clone()
     R.run(st)  # warm-up (graph capture of its LBM, workspaces)
@@ -329,12 +374,18 @@ def run_surrogate(args):
             "config": {"workload": "%d held-out quasi-1-D shock tubes of the sweep (seed %d)" % (args.tubes, args.eval_seed),
                        "train_tubes": args.train_tubes, "train_pairs": n_pairs, "train_crops_seen": int(args.train_steps * args.batch),
                        "jump": cfg.jump, "spot_every": args.spot_every, "l1_tol": args.l1_tol,
-                       "anchor": int(args.anchor), "network": {"width": args.width, "blocks": args.blocks,
+                       "anchor": int(args.anchor), "rotational_diffusion": args.diffusion,
+                       "network": {"width": args.width, "blocks": args.blocks,
                                                                "params": net.num_params}},
             "lbm_ms": lbm_ms, "surrogate_ms": sur_ms, "surrogate_wall_s": wall,
             "surrogate_parts_ms": dict(zip(("network", "spot_checks", "final_lbm", "reruns"), res["ms"].tolist())),
             "l1": {"mean": float(l1.mean()), "p90": float(np.percentile(l1, 90)), "max": float(l1.max()),
                    "frac_le_1pct": float((l1 <= 0.01).mean())},
+            "roofline": {"bound": "tensor", "kernel": "network forward (k_conv_tc + k_conv)",
+                         "achieved": fwd_tflops, "peak": peak[0], "unit": "TFLOP/s",
+                         "frac": fwd_tflops / peak[0], "peak_source": peak[1],
+                         "flop_per_coarse_position": flop_pos, "positions": coarse,
+                         "forward_ms": fwd_ms, "traffic": None},
             "tubes_handed_to_lbm": int(handed.sum()), "network_windows": int(res["windows"].sum()),
             "windows_total": windows_total, "spot_checks": int(res["checks"].sum()),
             "training": {"data_s": t_data, "train_s": t_train, "steps": args.train_steps,
@@ -362,6 +413,9 @@ def main():
                          "surrogate: learned surrogate vs plain batched LBM")
     ap.add_argument("--tubes", type=int, default=None,
                     help="tubes in --mode batch (4096) / held-out tubes in --mode surrogate (512)")
+    ap.add_argument("--diffusion", default="ftcs", choices=["ftcs", "implicit"],
+                    help="rotational diffusion of the batched tubes: the paper's FTCS "
+                         "sub-steps or the backward-Euler variant")
     ap.add_argument("--train-tubes", type=int, default=512)
     ap.add_argument("--train-steps", type=int, default=16000)
     ap.add_argument("--train-seed", type=int, default=1001)

@@ -225,6 +225,13 @@ rpk_status rpk_batch_init(rpk_batch* b, const double* rho, const double* u, cons
 /* Launch configuration of the persistent kernel: threads per CTA (a multiple
  * of 32 in [64, 512]) and CTAs per SM (>= 1, limited by shared memory). */
 rpk_status rpk_batch_set_config(rpk_batch* b, int threads, int ctas_per_sm);
+/* Rotational diffusion of the batch: mode 0 (default) the nsub FTCS sub-steps
+ * of the paper's scheme (Sec. 5, rotational step 3); mode 1 a variant that
+ * takes the same flux-form equation in one backward-Euler step per time step,
+ * (delta rho / 2) theta' - dt [K+ (theta'_+ - theta') - K- (theta' - theta'_-)]
+ * = E_R, solved per sublattice line by cyclic reduction (unconditionally
+ * stable: nsub is ignored). Takes effect at the next rpk_batch_run. */
+rpk_status rpk_batch_set_diffusion(rpk_batch* b, int mode);
 
 /* Time every supported launch configuration on a sample of the batch's own
  * tubes (a scratch copy; the batch state is untouched) and keep the fastest.
@@ -322,6 +329,7 @@ typedef struct {
   float in_dscale[4];  /* feature 4 + k = (v_k - v_k(previous window)) / in_dscale[k] */
   int lbm_threads;     /* launch configuration of the LBM arm (rpk_batch_set_config) */
   int lbm_ctas_per_sm;
+  int lbm_diffusion;   /* rotational diffusion of the LBM arm (rpk_batch_set_diffusion) */
 } rpk_sur_config;
 
 /* One sequence of network input: the padded tube, from padded position `crop`

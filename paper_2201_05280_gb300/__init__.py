@@ -60,7 +60,8 @@ class SurConfig(ctypes.Structure):
                 ("l1_tol", ctypes.c_double), ("in_shift", ctypes.c_float * 4),
                 ("in_scale", ctypes.c_float * 4), ("out_scale", ctypes.c_float * 4),
                 ("in_dscale", ctypes.c_float * 4),
-                ("lbm_threads", ctypes.c_int), ("lbm_ctas_per_sm", ctypes.c_int)]
+                ("lbm_threads", ctypes.c_int), ("lbm_ctas_per_sm", ctypes.c_int),
+                ("lbm_diffusion", ctypes.c_int)]
 
     @classmethod
     def make(cls, **kw):
@@ -138,6 +139,7 @@ def load_library(path=None):
         "rpk_batch_destroy": (None, [vp]),
         "rpk_batch_init": (i, [vp, vp, vp, vp, vp]),
         "rpk_batch_set_config": (i, [vp, i, i]),
+        "rpk_batch_set_diffusion": (i, [vp, i]),
         "rpk_batch_autotune": (i, [vp, ctypes.POINTER(i64)]),
         "rpk_batch_run": (i, [vp]),
         "rpk_batch_read_moments": (i, [vp, vp, vp, vp, vp, vp]),
@@ -409,6 +411,12 @@ class Batch:
         _check(load_library().rpk_batch_init(self._h, *[x.ctypes.data_as(ctypes.c_void_p)
                                                         for x in a]))
         self._keep = a
+        return self
+
+    def set_diffusion(self, mode):
+        """'ftcs' (the paper's sub-stepped scheme, default) or 'implicit'
+        (one backward-Euler step per time step)."""
+        _check(load_library().rpk_batch_set_diffusion(self._h, {"ftcs": 0, "implicit": 1}[mode]))
         return self
 
     def set_config(self, threads, ctas_per_sm=1):

@@ -54,7 +54,7 @@ __global__ void __launch_bounds__(kThreads)
     k_batch(TubeDev<Real>* __restrict__ tubes, const int* __restrict__ order, int ntubes,
             int* __restrict__ counter, Store* __restrict__ pop0, Store* __restrict__ pop1,
             Real* __restrict__ e_state, Real* __restrict__ ux_state, float* __restrict__ snaps,
-            int save_every, int max_np, unsigned* __restrict__ status) {
+            int save_every, int max_np, int implicit, unsigned* __restrict__ status) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Real* sE = reinterpret_cast<Real*>(smem_raw);  // auxiliary E_R (state), then corrector
   Real* sS = sE + max_np;                        // e* after exchange, then theta_R
@@ -160,54 +160,132 @@ __global__ void __launch_bounds__(kThreads)
         sS[p] = (Real(2) * val - t0d * dr) / (K.delta * (Real(1) + dr));
       }
       __syncthreads();
-      // 4. FTCS sub-steps: e += h sum_faces K_face (theta_nb - theta). The first
-      //    uses theta_R of the corrector (sS) and updates e in place; later ones
-      //    use theta_R = a e + c with a = 2/(delta(1 + D)), c = -delta theta0 D/(delta(1 + D))
-      //    (affine in e at fixed rho), ping-ponging e between sE and sS with one
-      //    barrier per sub-step.
-      for (int p = tid; p < np; p += kThreads) {
-        const int s = p >= nx, x = p - s * nx;
-        const Real thp = sS[p], kp = sK[p];
-        const Real thm = x == 0 ? thGl : sS[p - 1], km = x == 0 ? gl[kGhKap] : sK[p - 1];
-        const Real thq = x + 1 >= nx ? thGh : sS[p + 1], kq = x + 1 >= nx ? gh[kGhKap] : sK[p + 1];
-        Real acc = Real(0);
-        acc += Real(0.5) * (kp + km) * (thm - thp);
-        acc += Real(0.5) * (kp + kq) * (thq - thp);
-        sE[p] = sE[p] + K.hsub * acc;
-      }
-      __syncthreads();
-      if (nsub > 1) {
+      if (implicit) {
+        // 4'. backward-Euler variant: per sublattice line solve
+        //     (delta rho / 2) phi - dt [K+ (phi_+ - phi) - K- (phi - phi_-)] = e - delta theta0 D / 2
+        //     for phi = theta_R - theta0 by cyclic reduction in shared memory:
+        //     a -> sP, b -> sK, c -> sS, right-hand side and then phi -> sE.
         for (int p = tid; p < np; p += kThreads) {
-          const Real dr = sD[p];
-          const Real inv = Real(1) / (K.delta * (Real(1) + dr));
-          sP[p] = Real(2) * inv;    // a
-          sD[p] = -t0d * dr * inv;  // c
+          const int s = p >= nx, x = p - s * nx;
+          const Real kp = sK[p];
+          const Real km = x == 0 ? gl[kGhKap] : sK[p - 1];
+          const Real kq = x + 1 >= nx ? gh[kGhKap] : sK[p + 1];
+          sP[p] = -K.dt * Real(0.5) * (kp + km);
+          sS[p] = -K.dt * Real(0.5) * (kp + kq);
         }
         __syncthreads();
-        Real* ein = sE;
-        Real* eout = sS;
-        for (int k = 1; k < nsub; ++k) {
-          for (int p = tid; p < np; p += kThreads) {
-            const int s = p >= nx, x = p - s * nx;
-            const Real ep = ein[p];
-            const Real thp = sP[p] * ep + sD[p], kp = sK[p];
-            const Real thm = x == 0 ? thGl : sP[p - 1] * ein[p - 1] + sD[p - 1];
-            const Real km = x == 0 ? gl[kGhKap] : sK[p - 1];
-            const Real thq = x + 1 >= nx ? thGh : sP[p + 1] * ein[p + 1] + sD[p + 1];
-            const Real kq = x + 1 >= nx ? gh[kGhKap] : sK[p + 1];
-            Real acc = Real(0);
-            acc += Real(0.5) * (kp + km) * (thm - thp);
-            acc += Real(0.5) * (kp + kq) * (thq - thp);
-            eout[p] = ep + K.hsub * acc;
+        for (int p = tid; p < np; p += kThreads) {
+          const int s = p >= nx, x = p - s * nx;
+          const Real a = sP[p], c = sS[p], dr = sD[p];
+          sK[p] = Real(0.5) * K.delta * (Real(1) + dr) - a - c;
+          Real r = sE[p] - Real(0.5) * t0d * dr;
+          if (x == 0) {
+            r -= a * thGl;
+            sP[p] = Real(0);
+          }
+          if (x + 1 >= nx) {
+            r -= c * thGh;
+            sS[p] = Real(0);
+          }
+          sE[p] = r;
+        }
+        __syncthreads();
+        int h = 1;
+        for (; 2 * h <= nx; h *= 2) {
+          const int cnt = nx / (2 * h);  // x = 2h - 1, 4h - 1, ... < nx per line
+          for (int j = tid; j < 2 * cnt; j += kThreads) {
+            const int s = j >= cnt, k = j - s * cnt;
+            const int x = (k + 1) * 2 * h - 1, p = s * nx + x;
+            const int L = p - h;
+            const Real al = -sP[p] / sK[L];
+            Real a = al * sP[L], b = sK[p] + al * sS[L], c = Real(0), r = sE[p] + al * sE[L];
+            if (x + h < nx) {
+              const int R = p + h;
+              const Real ga = -sS[p] / sK[R];
+              c = ga * sS[R];
+              b += ga * sP[R];
+              r += ga * sE[R];
+            }
+            sP[p] = a;
+            sK[p] = b;
+            sS[p] = c;
+            sE[p] = r;
           }
           __syncthreads();
-          Real* tmp = ein;
-          ein = eout;
-          eout = tmp;
         }
-        if (ein != sE) {
-          for (int p = tid; p < np; p += kThreads) sE[p] = ein[p];
+        // the top equation of each line, x = h - 1, is now uncoupled
+        if (tid < 2) {
+          const int p = tid * nx + h - 1;
+          sE[p] = sE[p] / sK[p];
+        }
+        __syncthreads();
+        for (h /= 2; h >= 1; h /= 2) {
+          const int cnt = (nx + h) / (2 * h);  // x = h - 1, 3h - 1, ... < nx per line
+          for (int j = tid; j < 2 * cnt; j += kThreads) {
+            const int s = j >= cnt, k = j - s * cnt;
+            const int x = (2 * k + 1) * h - 1, p = s * nx + x;
+            Real r = sE[p];
+            if (x - h >= 0) r -= sP[p] * sE[p - h];
+            if (x + h < nx) r -= sS[p] * sE[p + h];
+            sE[p] = r / sK[p];
+          }
           __syncthreads();
+        }
+        for (int p = tid; p < np; p += kThreads) {
+          const Real dr = sD[p];
+          sE[p] = Real(0.5) * K.delta * ((Real(1) + dr) * sE[p] + K.theta0 * dr);
+        }
+        __syncthreads();
+      } else {
+        // 4. FTCS sub-steps: e += h sum_faces K_face (theta_nb - theta). The first
+        //    uses theta_R of the corrector (sS) and updates e in place; later ones
+        //    use theta_R = a e + c with a = 2/(delta(1 + D)), c = -delta theta0 D/(delta(1 + D))
+        //    (affine in e at fixed rho), ping-ponging e between sE and sS with one
+        //    barrier per sub-step.
+        for (int p = tid; p < np; p += kThreads) {
+          const int s = p >= nx, x = p - s * nx;
+          const Real thp = sS[p], kp = sK[p];
+          const Real thm = x == 0 ? thGl : sS[p - 1], km = x == 0 ? gl[kGhKap] : sK[p - 1];
+          const Real thq = x + 1 >= nx ? thGh : sS[p + 1], kq = x + 1 >= nx ? gh[kGhKap] : sK[p + 1];
+          Real acc = Real(0);
+          acc += Real(0.5) * (kp + km) * (thm - thp);
+          acc += Real(0.5) * (kp + kq) * (thq - thp);
+          sE[p] = sE[p] + K.hsub * acc;
+        }
+        __syncthreads();
+        if (nsub > 1) {
+          for (int p = tid; p < np; p += kThreads) {
+            const Real dr = sD[p];
+            const Real inv = Real(1) / (K.delta * (Real(1) + dr));
+            sP[p] = Real(2) * inv;    // a
+            sD[p] = -t0d * dr * inv;  // c
+          }
+          __syncthreads();
+          Real* ein = sE;
+          Real* eout = sS;
+          for (int k = 1; k < nsub; ++k) {
+            for (int p = tid; p < np; p += kThreads) {
+              const int s = p >= nx, x = p - s * nx;
+              const Real ep = ein[p];
+              const Real thp = sP[p] * ep + sD[p], kp = sK[p];
+              const Real thm = x == 0 ? thGl : sP[p - 1] * ein[p - 1] + sD[p - 1];
+              const Real km = x == 0 ? gl[kGhKap] : sK[p - 1];
+              const Real thq = x + 1 >= nx ? thGh : sP[p + 1] * ein[p + 1] + sD[p + 1];
+              const Real kq = x + 1 >= nx ? gh[kGhKap] : sK[p + 1];
+              Real acc = Real(0);
+              acc += Real(0.5) * (kp + km) * (thm - thp);
+              acc += Real(0.5) * (kp + kq) * (thq - thp);
+              eout[p] = ep + K.hsub * acc;
+            }
+            __syncthreads();
+            Real* tmp = ein;
+            ein = eout;
+            eout = tmp;
+          }
+          if (ein != sE) {
+            for (int p = tid; p < np; p += kThreads) sE[p] = ein[p];
+            __syncthreads();
+          }
         }
       }
       cur ^= 1;
@@ -379,10 +457,11 @@ struct rpk_batch {
   int* steps_dev = nullptr;   // per-tube step counts for rpk_batch_set_steps
   std::vector<int> max_steps; // step counts given at creation (bound the snapshot storage)
   bool nsub_ok = false;       // every tube's FTCS sub-step count is resolved
+  int implicit = 0;           // rotational diffusion: 0 FTCS sub-steps, 1 backward Euler
   bool init_ok = false;
   int threads = 256, ctas_per_sm = 1;
   cudaGraphExec_t graph = nullptr;
-  int graph_threads = 0, graph_ctas = 0;
+  int graph_threads = 0, graph_ctas = 0, graph_implicit = 0;
 };
 
 namespace {
@@ -438,7 +517,7 @@ rpk_status upload_order(rpk_batch* B) {
   for (int i = 0; i < B->ntubes; ++i) order[i] = i;
   std::vector<double> work(B->ntubes);
   for (int i = 0; i < B->ntubes; ++i)
-    work[i] = 2.0 * B->tubes[i].nx * B->tubes[i].nsteps * (8.0 + B->nsub[i]);
+    work[i] = 2.0 * B->tubes[i].nx * B->tubes[i].nsteps * (8.0 + (B->implicit ? 4.0 : B->nsub[i]));
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return work[a] > work[b]; });
   RPK_CUDA(cudaMemcpyAsync(B->order_dev, order.data(), sizeof(int) * B->ntubes,
                            cudaMemcpyHostToDevice, B->stream));
@@ -501,7 +580,8 @@ rpk_status launch_batch(rpk_batch* B, cudaStream_t stream, int threads, int ctas
   case NT:                                                                                     \
     k_batch<Store, Real, NT><<<grid, NT, smem, stream>>>(tubes, B->order_dev, B->ntubes,       \
                                                          B->counter, p0, p1, es, us, B->snaps, \
-                                                         B->save_every, max_np, B->status);    \
+                                                         B->save_every, max_np, B->implicit,   \
+                                                         B->status);                           \
     break;
     RPK_LAUNCH(128)
     RPK_LAUNCH(256)
@@ -741,6 +821,13 @@ rpk_status rpk_batch_moments_device(rpk_batch* B, float* state) {
   return RPK_OK;
 }
 
+rpk_status rpk_batch_set_diffusion(rpk_batch* B, int mode) {
+  if (!B) return fail(RPK_ERR_ARG, "NULL batch");
+  if (mode != 0 && mode != 1) return fail(RPK_ERR_ARG, "mode must be 0 (FTCS) or 1 (backward Euler)");
+  B->implicit = mode;
+  return RPK_OK;
+}
+
 rpk_status rpk_batch_set_config(rpk_batch* B, int threads, int ctas_per_sm) {
   if (!B) return fail(RPK_ERR_ARG, "NULL batch");
   if (!config_fits(B, threads, ctas_per_sm))
@@ -755,7 +842,8 @@ rpk_status rpk_batch_run(rpk_batch* B) {
   if (!B) return fail(RPK_ERR_ARG, "NULL batch");
   if (!B->init_ok) return fail(RPK_ERR_STATE, "initialise the batch first");
   RPK_CUDA(cudaSetDevice(B->device));
-  if (!B->graph || B->graph_threads != B->threads || B->graph_ctas != B->ctas_per_sm) {
+  if (!B->graph || B->graph_threads != B->threads || B->graph_ctas != B->ctas_per_sm ||
+      B->graph_implicit != B->implicit) {
     if (B->graph) {
       cudaGraphExecDestroy(B->graph);
       B->graph = nullptr;
@@ -785,6 +873,7 @@ rpk_status rpk_batch_run(rpk_batch* B) {
     if (err != cudaSuccess) return cuda_fail(err, "batch graph capture");
     B->graph_threads = B->threads;
     B->graph_ctas = B->ctas_per_sm;
+    B->graph_implicit = B->implicit;
   }
   RPK_CUDA(cudaGraphLaunch(B->graph, B->stream));
   return RPK_OK;
@@ -849,6 +938,7 @@ rpk_status rpk_batch_autotune(rpk_batch* B, int64_t out[3]) {
   rpk_status st = rpk_batch_create(B->precision, nsample, tv.data(), 1 << 30, B->stream, &S);
   if (st != RPK_OK) return st;
   S->max_nx = B->max_nx;  // same shared-memory footprint as the real launch
+  S->implicit = B->implicit;
   std::vector<double> rho(S->total_pts, 1.0), u(3 * S->total_pts, 0.0), T(S->total_pts, kTheta0);
   st = rpk_batch_init(S, rho.data(), u.data(), T.data(), T.data());
   double best_ms = 1e300;

@@ -460,6 +460,7 @@ rpk_status rpk_rollout_create(rpk_net* net, const rpk_sur_config* cfg, int ntube
     R->seq_points += seq_len(R, i);
   }
   st = rpk_batch_create(RPK_F32, ntubes, tubes, 1 << 30, cuda_stream, &R->batch);
+  if (st == RPK_OK) st = rpk_batch_set_diffusion(R->batch, cfg->lbm_diffusion);
   if (st == RPK_OK && cfg->lbm_threads > 0)
     st = rpk_batch_set_config(R->batch, cfg->lbm_threads, std::max(1, cfg->lbm_ctas_per_sm));
   if (st == RPK_OK) st = ro_alloc((void**)&R->next, sizeof(float) * R->state_floats);

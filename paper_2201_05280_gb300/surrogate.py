@@ -80,9 +80,10 @@ class TrainingSet:
     """Snapshots of an LBM run of the tubes held on the device, with the index
     of all consecutive pairs."""
 
-    def __init__(self, tubes, cond, fields, save_every=32, stream=None):
+    def __init__(self, tubes, cond, fields, save_every=32, diffusion="ftcs", stream=None):
         import torch
         bt = rpk.Batch(tubes, precision="f32", save_every=save_every, stream=stream)
+        bt.set_diffusion(diffusion)
         bt.init_fields(fields["rho"], fields["u"], fields["T"], fields["R"])
         self.tune = bt.autotune()
         bt.run()

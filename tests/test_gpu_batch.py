@@ -41,8 +41,8 @@ def _relax_for(spec, fields_T, fields_R):
     return dict(delta=d, tau=tau, tau1=tau1, b=b, k_r=kr, nsub=nsub)
 
 
-def _setup(ntubes, L, seed, nsteps_cap=None):
-    specs, f = I.tube_sweep(ntubes, T0, seed=seed, L=L)
+def _setup(ntubes, L, seed, nsteps_cap=None, ratio=(2.0, 20.0)):
+    specs, f = I.tube_sweep(ntubes, T0, seed=seed, L=L, ratio=ratio)
     tubes = []
     for i, sp in enumerate(specs):
         lo, hi = 2 * sum(s["nx"] for s in specs[:i]), 2 * sum(s["nx"] for s in specs[:i + 1])
@@ -53,9 +53,9 @@ def _setup(ntubes, L, seed, nsteps_cap=None):
     return tubes, f
 
 
-def _oracle_tube(t, f, save_every, nruns=1):
+def _oracle_tube(t, f, save_every, nruns=1, diff=0):
     r = t["relax"]
-    P = O.make_params(r["delta"], r["tau"], r["tau1"], r["b"], r["k_r"], 1.0, r["nsub"], 1)
+    P = O.make_params(r["delta"], r["tau"], r["tau1"], r["b"], r["k_r"], 1.0, r["nsub"], 1, diff)
     lo, hi = t["lo"], t["hi"]
     S = O.State(P, t["nx"], 1, 1, reservoirs=t["res"]).init_fields(
         f["rho"][lo:hi], f["u"][:, lo:hi], f["T"][lo:hi], f["R"][lo:hi])
@@ -150,3 +150,40 @@ def test_batch_longest_tube_fits_shared_memory():
     B.close()
     with pytest.raises(rpk.RpkError):
         rpk.Batch([dict(tubes[0], nx=nmax + 1)], precision="f32")
+
+
+@pytest.mark.parametrize("prec,tol", [("f64", 1e-12), ("f32", 5e-5)])
+def test_batch_implicit_diffusion_matches_oracle(prec, tol):
+    """The backward-Euler variant (cyclic reduction on the GPU, Thomas in the
+    oracle) on tubes with large and small diffusion numbers, including one
+    tube of odd length and one of a single cell pair."""
+    save_every = 16
+    tubes, f = _setup(6, (24, 300), seed=31, nsteps_cap=60)
+    B = rpk.Batch(tubes, precision=prec, save_every=save_every)
+    B.set_diffusion("implicit")
+    B.init_fields(f["rho"], f["u"], f["T"], f["R"]).run()
+    got = B.read_moments()
+    for i, t in enumerate(tubes):
+        ref, _ = _oracle_tube(t, f, save_every, diff=1)
+        lo, hi = t["lo"], t["hi"]
+        g = {k: (got[k][:, lo:hi] if k == "u" else got[k][lo:hi]) for k in got}
+        _cmp(g, ref, tol)
+    B.close()
+
+
+def test_batch_implicit_tiny_and_odd_tubes():
+    # weak pressure ratios: a strong shock on a few cells breaks the Hermite-3
+    # populations' positivity in the oracle too
+    tubes, f = _setup(5, (2, 9), seed=38, ratio=(2.0, 2.5))
+    for t in tubes:
+        t["nsteps"] = 20
+    assert sorted({t["nx"] % 2 for t in tubes}) == [0, 1]
+    B = rpk.Batch(tubes, precision="f64", save_every=8)
+    B.set_diffusion("implicit")
+    B.init_fields(f["rho"], f["u"], f["T"], f["R"]).run()
+    got = B.read_moments()
+    for t in tubes:
+        ref, _ = _oracle_tube(t, f, 8, diff=1)
+        lo, hi = t["lo"], t["hi"]
+        _cmp({k: (got[k][:, lo:hi] if k == "u" else got[k][lo:hi]) for k in got}, ref, 1e-12)
+    B.close()
