@@ -174,30 +174,33 @@ __global__ void __launch_bounds__(kThreads) k_conv(ConvArgs P) {
 
 // ---------------------------------------------------------------------------
 // Tensor-core (tcgen05) path of the residual-block convolutions: Co = Ci = 128,
-// 5 taps. One persistent CTA per SM holds the layer's BF16 weights in shared
+// 5 taps. One persistent CTA per SM keeps the layer's BF16 weights in shared
 // memory (A: 128 x 640, K-major) and walks over tiles of 128 output positions
-// of one sequence. Per tile it stages the 132 input rows (positions q0 - 2 ..
-// q0 + 129, activation applied, BF16) once; the operand of tap t is the same
-// tile seen from row t (forward) or 4 - t (input gradient), which the
-// interleaved no-swizzle layout (rows 16 bytes apart inside each 8-column
-// chunk) turns into a start-address offset. 40 MMAs (M 128, N 128, K 16)
-// accumulate into 128 TMEM columns; one thread issues them and commits to an
-// mbarrier; the epilogue reads TMEM rows (lane = output channel) and applies
-// bias, mask and residual as k_conv does.
+// of one sequence. Three roles run concurrently on double buffers:
+//   producers (warps 4-7) stage the tile's 132 input rows (positions
+//     q0 - 2 .. q0 + 129, activation applied, BF16) into B[i % 2];
+//   one issuing thread (warp 4, lane 0) waits for B[i % 2] and for the
+//     accumulator i % 2 to be free, issues 40 MMAs (M 128, N 128, K 16) into
+//     TMEM columns 128 (i % 2) .. + 127 and commits to two mbarriers (B free,
+//     accumulator full);
+//   the epilogue (warps 0-3, TMEM lane = output channel) reads the
+//     accumulator, applies bias, mask and residual as k_conv does, and frees it.
+// The operand of tap t is the staged tile seen from row t (forward) or 4 - t
+// (input gradient): in the interleaved no-swizzle layout (rows 16 bytes apart
+// inside each 8-column chunk) a row shift is a start-address offset.
 constexpr int TC_M = 128, TC_N = 128, TC_KC = 128, TC_TAPS = 5;
 constexpr int TC_ROWS = TC_N + TC_TAPS - 1;                // 132 staged rows
 constexpr int TC_K = TC_TAPS * TC_KC;                      // 640
 constexpr uint32_t TC_A_LBO = TC_M * 16;                   // bytes between 8-wide k chunks of A
 constexpr uint32_t TC_B_LBO = TC_ROWS * 16;                // bytes between 8-wide k chunks of B
 constexpr uint32_t TC_A_BYTES = (TC_K / 8) * TC_A_LBO;     // 163840
-constexpr uint32_t TC_B_BYTES = (TC_KC / 8) * TC_B_LBO;    // 33792
-constexpr uint32_t TC_USED = TC_A_BYTES + TC_B_BYTES + 64;  // + mbarrier and TMEM address
-// The whole opt-in shared memory of an SM: one CTA per SM either way, and every
-// address an operand descriptor can reach stays inside the allocation.
-constexpr uint32_t TC_SMEM = 227 * 1024;
-static_assert(TC_USED <= TC_SMEM, "tensor-core tiles exceed shared memory");
-constexpr int TC_THREADS = 128;
-constexpr long long TC_WAIT_LIMIT = 1ll << 24;             // mbarrier polls before giving up
+constexpr uint32_t TC_B_BYTES = (TC_KC / 8) * TC_B_LBO;    // 33792 per buffer
+constexpr uint32_t TC_BAR_OFF = TC_A_BYTES + 2 * TC_B_BYTES;
+constexpr uint32_t TC_SMEM = TC_BAR_OFF + 128;             // 8 mbarriers + TMEM address
+static_assert(TC_SMEM <= 227 * 1024, "tensor-core tiles exceed shared memory");
+constexpr int TC_THREADS = 256;
+constexpr int TC_COLS = 2 * TC_N;                          // two accumulators
+constexpr long long TC_WAIT_LIMIT = 1ll << 22;             // mbarrier polls before giving up
 
 struct TcArgs {
   const __nv_bfloat16* A;  // [128][5][128]
@@ -227,37 +230,60 @@ __device__ __forceinline__ uint64_t tc_desc(uint32_t saddr, uint32_t lbo, uint32
 constexpr uint32_t TC_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TC_N >> 3) << 17) |
                               ((uint32_t)(TC_M >> 4) << 24);
 
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t phase) {
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
   for (long long it = 0; it < TC_WAIT_LIMIT; ++it) {
     uint32_t done;
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
         " selp.u32 %0, 1, 0, p;\n}\n"
         : "=r"(done)
-        : "r"(mbar), "r"(phase)
+        : "r"(mbar), "r"(parity)
         : "memory");
     if (done) return true;
   }
   return false;
 }
 
+__device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(mbar) : "memory");
+}
+
+__device__ __forceinline__ void tc_tile(const TcArgs& P, int tile, int& q0, int& cnt, int& lo, int& len) {
+  if (P.tiles) {
+    const int4 d = P.tiles[tile];
+    q0 = d.x, cnt = d.y, lo = d.z, len = d.w;
+  } else {
+    const int sq = tile / P.tiles_per_seq, part = tile - sq * P.tiles_per_seq;
+    lo = sq * P.seq_len;
+    len = P.seq_len;
+    q0 = lo + part * TC_N;
+    cnt = min(TC_N, len - part * TC_N);
+  }
+}
+
 __global__ void __launch_bounds__(TC_THREADS, 1) k_conv_tc(TcArgs P) {
   extern __shared__ __align__(1024) unsigned char tc_smem[];
   unsigned char* sA = tc_smem;
   unsigned char* sB = tc_smem + TC_A_BYTES;
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(tc_smem + TC_A_BYTES + TC_B_BYTES);
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tc_smem + TC_A_BYTES + TC_B_BYTES + 16);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(tc_smem + TC_BAR_OFF);
+  // bars: 0-1 B full, 2-3 B free, 4-5 accumulator full, 6-7 accumulator free
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tc_smem + TC_BAR_OFF + 64);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_u32(tmem_slot)),
-                 "r"(TC_N)
+                 "r"(TC_COLS)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(mbar)), "r"(1) : "memory");
+    for (int b = 0; b < 2; ++b) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bars + b)), "r"(128) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bars + 2 + b)), "r"(1) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bars + 4 + b)), "r"(1) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bars + 6 + b)), "r"(128) : "memory");
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   // weights: chunk c (k = 8c .. 8c + 7) of row m at c * TC_A_LBO + m * 16
@@ -266,74 +292,93 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv_tc(TcArgs P) {
     const uint4 v = *reinterpret_cast<const uint4*>(P.A + (int64_t)m * TC_K + 8 * c);
     *reinterpret_cast<uint4*>(sA + c * TC_A_LBO + m * 16) = v;
   }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tmem_slot;
-  const uint32_t a_base = smem_u32(sA), b_base = smem_u32(sB), mb = smem_u32(mbar);
-  uint32_t phase = 0;
+  const uint32_t a_base = smem_u32(sA), b_base = smem_u32(sB);
+  const uint32_t bar0 = smem_u32(bars);
   bool ok = true;
 
-  for (int tile = blockIdx.x; tile < P.ntiles && ok; tile += gridDim.x) {
-    int q0, cnt, lo, len;
-    if (P.tiles) {
-      const int4 d = P.tiles[tile];
-      q0 = d.x, cnt = d.y, lo = d.z, len = d.w;
-    } else {
-      const int sq = tile / P.tiles_per_seq, part = tile - sq * P.tiles_per_seq;
-      lo = sq * P.seq_len;
-      len = P.seq_len;
-      q0 = lo + part * TC_N;
-      cnt = min(TC_N, len - part * TC_N);
-    }
-    // stage rows r = 0 .. 131 (positions q0 - 2 + r), zero outside the sequence
-    for (int e = tid; e < TC_ROWS * (TC_KC / 8); e += TC_THREADS) {
-      const int r = e % TC_ROWS, c = e / TC_ROWS;
-      const int q = q0 - 2 + r;
-      uint4 packed = make_uint4(0u, 0u, 0u, 0u);
-      if (q >= lo && q < lo + len) {
-        const float4* src = reinterpret_cast<const float4*>(P.X + (int64_t)q * TC_KC + 8 * c);
-        float4 f0 = src[0], f1 = src[1];
-        if (P.relu_in) {
-          f0.x = fmaxf(f0.x, 0.f), f0.y = fmaxf(f0.y, 0.f), f0.z = fmaxf(f0.z, 0.f), f0.w = fmaxf(f0.w, 0.f);
-          f1.x = fmaxf(f1.x, 0.f), f1.y = fmaxf(f1.y, 0.f), f1.z = fmaxf(f1.z, 0.f), f1.w = fmaxf(f1.w, 0.f);
+  if (warp >= 4) {
+    // producers, and the issuing thread
+    const int ptid = tid - 128;
+    for (int i = 0, tile = blockIdx.x; tile < P.ntiles && ok; ++i, tile += gridDim.x) {
+      const int b = i & 1;
+      if (i >= 2) ok = __all_sync(0xffffffffu, mbar_wait(bar0 + 8 * (2 + b), ((i >> 1) - 1) & 1));
+      if (!ok) break;
+      int q0, cnt, lo, len;
+      tc_tile(P, tile, q0, cnt, lo, len);
+      unsigned char* dst = sB + b * TC_B_BYTES;
+      for (int e = ptid; e < TC_ROWS * (TC_KC / 8); e += 128) {
+        const int r = e % TC_ROWS, c = e / TC_ROWS;
+        const int q = q0 - 2 + r;
+        uint4 packed = make_uint4(0u, 0u, 0u, 0u);
+        if (q >= lo && q < lo + len) {
+          const float4* src = reinterpret_cast<const float4*>(P.X + (int64_t)q * TC_KC + 8 * c);
+          float4 f0 = src[0], f1 = src[1];
+          if (P.relu_in) {
+            f0.x = fmaxf(f0.x, 0.f), f0.y = fmaxf(f0.y, 0.f), f0.z = fmaxf(f0.z, 0.f), f0.w = fmaxf(f0.w, 0.f);
+            f1.x = fmaxf(f1.x, 0.f), f1.y = fmaxf(f1.y, 0.f), f1.z = fmaxf(f1.z, 0.f), f1.w = fmaxf(f1.w, 0.f);
+          }
+          packed = make_uint4(pack_bf16(f0.x, f0.y), pack_bf16(f0.z, f0.w), pack_bf16(f1.x, f1.y),
+                              pack_bf16(f1.z, f1.w));
         }
-        packed = make_uint4(pack_bf16(f0.x, f0.y), pack_bf16(f0.z, f0.w), pack_bf16(f1.x, f1.y),
-                            pack_bf16(f1.z, f1.w));
+        *reinterpret_cast<uint4*>(dst + c * TC_B_LBO + r * 16) = packed;
       }
-      *reinterpret_cast<uint4*>(sB + c * TC_B_LBO + r * 16) = packed;
-    }
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    __syncthreads();
-    if (tid == 0) {
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      mbar_arrive(bar0 + 8 * b);  // B full (128 arrivals)
+      if (ptid == 0) {
+        // the issuing thread: B staged by all producers, accumulator free
+        bool go = mbar_wait(bar0 + 8 * b, (i >> 1) & 1);
+        if (go && i >= 2) go = mbar_wait(bar0 + 8 * (6 + b), ((i >> 1) - 1) & 1);
+        if (go) {
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t bb = b_base + (uint32_t)b * TC_B_BYTES;
+          const uint32_t d = tmem + (uint32_t)(b * TC_N);
 #pragma unroll 1
-      for (int t = 0; t < TC_TAPS; ++t) {
-        const int row0 = P.sgn > 0 ? t : TC_TAPS - 1 - t;
+          for (int t = 0; t < TC_TAPS; ++t) {
+            const int row0 = P.sgn > 0 ? t : TC_TAPS - 1 - t;
 #pragma unroll
-        for (int s = 0; s < TC_KC / 16; ++s) {
-          const uint64_t ad = tc_desc(a_base + (uint32_t)(t * (TC_KC / 8) + 2 * s) * TC_A_LBO, TC_A_LBO, 128);
-          const uint64_t bd = tc_desc(b_base + (uint32_t)(2 * s) * TC_B_LBO + (uint32_t)row0 * 16, TC_B_LBO, 128);
-          const uint32_t acc = (t | s) ? 1u : 0u;
-          asm volatile(
-              "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-              " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-              "l"(ad), "l"(bd), "r"(TC_IDESC), "r"(acc)
-              : "memory");
+            for (int s = 0; s < TC_KC / 16; ++s) {
+              const uint64_t ad =
+                  tc_desc(a_base + (uint32_t)(t * (TC_KC / 8) + 2 * s) * TC_A_LBO, TC_A_LBO, 128);
+              const uint64_t bd = tc_desc(bb + (uint32_t)(2 * s) * TC_B_LBO + (uint32_t)row0 * 16, TC_B_LBO, 128);
+              const uint32_t acc = (t | s) ? 1u : 0u;
+              asm volatile(
+                  "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                  " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+                  "l"(ad), "l"(bd), "r"(TC_IDESC), "r"(acc)
+                  : "memory");
+            }
+          }
+          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                           bar0 + 8 * (2 + b))
+                       : "memory");
+          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                           bar0 + 8 * (4 + b))
+                       : "memory");
+        } else {
+          atomicOr(P.error, 1u);
         }
       }
-      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mb)
-                   : "memory");
+      __syncwarp();
     }
-    __syncwarp();
-    // every thread waits; the CTA proceeds only if all saw the commit
-    ok = !__syncthreads_or(mbar_wait(mb, phase) ? 0 : 1);
-    if (!ok && tid == 0) atomicOr(P.error, 1u);
-    phase ^= 1u;
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (ok) {
-      const int m = warp * 32 + lane;  // TMEM lane = output channel
-      const float bm = P.bias ? P.bias[m] : 0.f;
+  } else {
+    // epilogue: TMEM lane = output channel m
+    const int m = warp * 32 + lane;
+    const float bm = P.bias ? P.bias[m] : 0.f;
+    for (int i = 0, tile = blockIdx.x; tile < P.ntiles; ++i, tile += gridDim.x) {
+      const int b = i & 1;
+      ok = __all_sync(0xffffffffu, mbar_wait(bar0 + 8 * (4 + b), (i >> 1) & 1));
+      if (!ok) {
+        if (lane == 0) atomicOr(P.error, 1u);
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      int q0, cnt, lo, len;
+      tc_tile(P, tile, q0, cnt, lo, len);
 #pragma unroll 1
       for (int j = 0; j < TC_N / 32; ++j) {
         uint32_t v[32];
@@ -345,27 +390,28 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv_tc(TcArgs P) {
               "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]),
               "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]),
               "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
-            : "r"(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(j * 32)));
+            : "r"(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(b * TC_N + j * 32)));
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-        for (int i = 0; i < 32; ++i) {
-          const int n = j * 32 + i;
+        for (int k = 0; k < 32; ++k) {
+          const int n = j * 32 + k;
           if (n < cnt) {
             const int64_t o = (int64_t)(q0 + n) * TC_M + m;
-            float val = __uint_as_float(v[i]) + bm;
+            float val = __uint_as_float(v[k]) + bm;
             if (P.mask && !(P.mask[o] > 0.f)) val = 0.f;
             if (P.res) val += P.res[o];
             P.out[o] = val;
           }
         }
       }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      mbar_arrive(bar0 + 8 * (6 + b));  // accumulator free (128 arrivals)
     }
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
   }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (warp == 0)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_N) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_COLS) : "memory");
 }
 
 struct DwArgs {
