@@ -49,12 +49,13 @@ class Params(ctypes.Structure):
     _fields_ = [("delta", ctypes.c_double), ("tau", ctypes.c_double),
                 ("tau1", ctypes.c_double), ("b", ctypes.c_double),
                 ("kr", ctypes.c_double), ("dt", ctypes.c_double),
-                ("nsub", ctypes.c_int), ("bcx", ctypes.c_int), ("diff", ctypes.c_int)]
+                ("nsub", ctypes.c_int), ("bcx", ctypes.c_int), ("diff", ctypes.c_int),
+                ("rot_mode", ctypes.c_int)]
 
     def __repr__(self):
-        return ("Params(delta=%g, tau=%g, tau1=%g, b=%g, kr=%g, dt=%g, nsub=%d, bcx=%d, diff=%d)"
-                % (self.delta, self.tau, self.tau1, self.b, self.kr, self.dt,
-                   self.nsub, self.bcx, self.diff))
+        return ("Params(delta=%g, tau=%g, tau1=%g, b=%g, kr=%g, dt=%g, nsub=%d, bcx=%d, diff=%d, "
+                "rot_mode=%d)" % (self.delta, self.tau, self.tau1, self.b, self.kr, self.dt,
+                                  self.nsub, self.bcx, self.diff, self.rot_mode))
 
 
 _lib = None
@@ -157,11 +158,13 @@ def target(rho, u, Lam):
     return f
 
 
-def make_params(delta, tau, tau1, b=0.0, kr=0.0, dt=1.0, nsub=1, bcx=0, diff=0):
+def make_params(delta, tau, tau1, b=0.0, kr=0.0, dt=1.0, nsub=1, bcx=0, diff=0, rot_mode=0):
     """diff = 0: FTCS sub-steps of the rotational diffusion (Sec. 5); 1: one
-    backward-Euler step per sublattice line (variant for quasi-1-D tubes)."""
+    backward-Euler step per sublattice line (variant for quasi-1-D tubes).
+    rot_mode = 0: conservative form on the auxiliary energy Er; 1: the paper's
+    four-step theta_R solver (Sec. 5), the state then holds theta_R."""
     return Params(float(delta), float(tau), float(tau1), float(b), float(kr), float(dt),
-                  int(nsub), int(bcx), int(diff))
+                  int(nsub), int(bcx), int(diff), int(rot_mode))
 
 
 def diffuse_be_line(delta, dt, rho, kap, Er, thl, kl, thr, kr):

@@ -63,6 +63,8 @@ typedef struct {
     int bcx;      /* 0: periodic in x; 1: fixed reservoirs beyond both x ends */
     int diff;     /* rotational diffusion: 0 FTCS sub-steps (Sec. 5); 1 one backward-Euler
                      step (variant for quasi-1-D tubes: ny = nz = 1, bcx = 1) */
+    int rot_mode; /* 0: conservative form, the state holds Er (auxiliary energy density);
+                     1: the paper's theta_R solver (Sec. 5, four steps), the state holds theta_R */
 } ora_params;
 
 static void put(int i, double cx, double cy, double cz, double w)
@@ -236,11 +238,18 @@ static void recover(const ora_params *P, const double *g, double Er, moments *m)
 
     a_ = P->delta * P->dt / (2.0 * P->tau1 * (3.0 + P->delta));
     X = 3.0 * P->dt / (2.0 * P->tau1 * (3.0 + P->delta));
-    Rt = 2.0 * Er / (P->delta * rho);
-    /* (1 + a) T - a R = thetaTg ;  -X T + (1 + X) R = Rt */
-    det = (1.0 + a_) * (1.0 + X) - a_ * X;
-    m->T = (m->thetaTg * (1.0 + X) + a_ * Rt) / det;
-    m->R = ((1.0 + a_) * Rt + X * m->thetaTg) / det;
+    if (P->rot_mode == 1) {
+        /* paper mode: the state is theta_R itself; the g-level translational
+         * temperature relation (1 + a) T - a R = thetaTg gives T */
+        m->R = Er;
+        m->T = (m->thetaTg + a_ * m->R) / (1.0 + a_);
+    } else {
+        Rt = 2.0 * Er / (P->delta * rho);
+        /* (1 + a) T - a R = thetaTg ;  -X T + (1 + X) R = Rt */
+        det = (1.0 + a_) * (1.0 + X) - a_ * X;
+        m->T = (m->thetaTg * (1.0 + X) + a_ * Rt) / det;
+        m->R = ((1.0 + a_) * Rt + X * m->thetaTg) / det;
+    }
     m->theta = (3.0 * m->T + P->delta * m->R) / (3.0 + P->delta);
 
     fac = 1.0 + P->dt / (2.0 * tau_star(P)) - P->b * P->dt / (2.0 * P->tau);
@@ -281,7 +290,8 @@ static void collide(const ora_params *P, double *g, double *Er, moments *m_out)
     targets(P, &m, fES, fEq);
     for (i = 0; i < Q; i++)
         g[i] = (1.0 - 2.0 * bs) * g[i] + 2.0 * bs * ts * (fES[i] / P->tau + fEq[i] / P->tau1);
-    *Er = *Er + P->dt * (P->delta * m.rho / 2.0) * (m.theta - m.R) / P->tau1;
+    if (P->rot_mode != 1) /* paper mode relaxes theta_R in the transport stage */
+        *Er = *Er + P->dt * (P->delta * m.rho / 2.0) * (m.theta - m.R) / P->tau1;
     if (m_out) *m_out = m;
 }
 
@@ -323,8 +333,11 @@ void ora_point_init(const ora_params *P, double rho, const double *u, double T, 
         double Omega = (f[i] - f[i]) / P->tau + (fEq[i] - f[i]) / P->tau1;
         g[i] = f[i] - 0.5 * P->dt * Omega;
     }
-    *Er = 0.5 * P->delta * rho * R -
-          0.5 * P->dt * (0.5 * P->delta * rho) * (theta - R) / P->tau1;
+    if (P->rot_mode == 1)
+        *Er = R; /* paper mode: the state is theta_R */
+    else
+        *Er = 0.5 * P->delta * rho * R -
+              0.5 * P->dt * (0.5 * P->delta * rho) * (theta - R) / P->tau1;
 }
 
 /* out: rho, ux, uy, uz, T, R, theta, thetaTg, sigma[9] (17 values) */
@@ -441,7 +454,7 @@ static void make_ghost(const ora_params *P, const double *st, ghost *gh)
 {
     /* st: rho, ux, uy, uz, T, R */
     double theta = (3.0 * st[4] + P->delta * st[5]) / (3.0 + P->delta);
-    ora_point_init(P, st[0], st + 1, st[4], st[5], gh->g, &gh->Er);
+    ora_point_init(P, st[0], st + 1, st[4], st[5], gh->g, &gh->Er); /* theta_R in paper mode */
     gh->rho = st[0];
     gh->u[0] = st[1]; gh->u[1] = st[2]; gh->u[2] = st[3];
     gh->kap = kappa_R(P, st[0], theta);
@@ -515,6 +528,8 @@ int ora_diffuse_be_line(int n, double delta, double dt, const double *rho, const
  *      term -Er div v enters the linear acoustics, and v = u(t) would leave a
  *      first-order error there (a negative bulk viscosity of order dt);
  *      uprev (3 planes) holds u(t-1) on entry and u(t_end - 1) on return;
+ * (rot_mode = 1 replaces 3 and 4 by the paper's four steps on theta_R, see
+ * below.)
  *   4. diffuse: nsub FTCS sub-steps of dt/nsub of the flux-form equation
  *      dEr/dt = div(kappa_R grad theta_R), theta_R = 2 Er/(delta rho), face
  *      coefficients the mean of the two kappa_R values (Sec. 5, step 3, with
@@ -537,16 +552,17 @@ int ora_step(const ora_params *P, int nx, int ny, int nz, const double *res, dou
     double *Ec = (double *)malloc(sizeof(double) * N);
     double *th = (double *)malloc(sizeof(double) * N);
     double *v = (double *)malloc(sizeof(double) * 3 * N);
+    double *Tt = (double *)malloc(sizeof(double) * N);
     ghost gh[2];
     long p, t;
     int i, a, k;
-    if (!gs || !rho || !u || !kap || !Ep || !Ec || !th || !v) {
-        free(gs); free(rho); free(u); free(kap); free(Ep); free(Ec); free(th); free(v);
+    if (!gs || !rho || !u || !kap || !Ep || !Ec || !th || !v || !Tt) {
+        free(gs); free(rho); free(u); free(kap); free(Ep); free(Ec); free(th); free(v); free(Tt);
         return 1;
     }
     need_lattice();
-    if (P->diff == 1 && (ny != 1 || nz != 1 || P->bcx != 1)) {
-        free(gs); free(rho); free(u); free(kap); free(Ep); free(Ec); free(th); free(v);
+    if ((P->diff == 1 && (ny != 1 || nz != 1 || P->bcx != 1)) || (P->diff == 1 && P->rot_mode == 1)) {
+        free(gs); free(rho); free(u); free(kap); free(Ep); free(Ec); free(th); free(v); free(Tt);
         return 2;
     }
     if (P->bcx == 1) {
@@ -562,6 +578,7 @@ int ora_step(const ora_params *P, int nx, int ny, int nz, const double *res, dou
             rho[p] = m.rho;
             for (a = 0; a < 3; a++) u[a * N + p] = m.u[a];
             kap[p] = kappa_R(P, m.rho, m.theta);
+            Tt[p] = m.T;
         }
         /* 2. pull streaming */
         for (p = 0; p < N; p++) {
@@ -571,6 +588,53 @@ int ora_step(const ora_params *P, int nx, int ny, int nz, const double *res, dou
                 long q = pull_source(P, &G, s, x, y, z, i);
                 g[p * Q + i] = (q >= 0) ? gs[q * Q + i] : gh[-1 - q].g[i];
             }
+        }
+        if (P->rot_mode == 1) {
+            /* paper mode (Sec. 5, four steps on theta_R, held in Er[]), with
+             * theta_T(f) of time t in both relaxation half steps */
+            const double X = 3.0 * P->dt / (2.0 * P->tau1 * (3.0 + P->delta));
+            /* 1. backward-Euler half step of the relaxation */
+            for (p = 0; p < N; p++) Er[p] = (Er[p] + X * Tt[p]) / (1.0 + X);
+            /* 2. MacCormack on u . grad theta_R: forward differences in the
+             *    predictor, backward in the corrector, u of time t */
+            for (p = 0; p < N; p++) {
+                double adv = 0.0;
+                for (a = 0; a < 3; a++) {
+                    long qf = axis_nb(P, &G, p, a, +1);
+                    double Rq = (qf >= 0) ? Er[qf] : gh[-1 - qf].Er;
+                    adv += u[a * N + p] * (Rq - Er[p]);
+                }
+                Ep[p] = Er[p] - P->dt * adv;
+            }
+            for (p = 0; p < N; p++) {
+                double adv = 0.0;
+                for (a = 0; a < 3; a++) {
+                    long qb = axis_nb(P, &G, p, a, -1);
+                    double Rq = (qb >= 0) ? Ep[qb] : gh[-1 - qb].Er;
+                    adv += u[a * N + p] * (Ep[p] - Rq);
+                }
+                Ec[p] = 0.5 * (Er[p] + Ep[p] - P->dt * adv);
+            }
+            memcpy(Er, Ec, sizeof(double) * N);
+            /* 3. FTCS of (2 / (rho delta)) kappa_R lap theta_R, nsub sub-steps */
+            for (k = 0; k < P->nsub; k++) {
+                const double h = P->dt / P->nsub;
+                for (p = 0; p < N; p++) {
+                    double lap = 0.0;
+                    for (a = 0; a < 3; a++) {
+                        long qp = axis_nb(P, &G, p, a, +1), qm = axis_nb(P, &G, p, a, -1);
+                        double Rp = (qp >= 0) ? Er[qp] : gh[-1 - qp].Er;
+                        double Rm = (qm >= 0) ? Er[qm] : gh[-1 - qm].Er;
+                        lap += Rp - 2.0 * Er[p] + Rm;
+                    }
+                    Ec[p] = Er[p] + h * 2.0 * kap[p] / (rho[p] * P->delta) * lap;
+                }
+                memcpy(Er, Ec, sizeof(double) * N);
+            }
+            /* 4. second backward-Euler half step */
+            for (p = 0; p < N; p++) Er[p] = (Er[p] + X * Tt[p]) / (1.0 + X);
+            memcpy(uprev, u, sizeof(double) * 3 * N);
+            continue;
         }
         /* 3. MacCormack advection of Er with v = (3 u(t) - u(t-1))/2 */
         for (p = 0; p < 3 * N; p++) v[p] = 1.5 * u[p] - 0.5 * uprev[p];
@@ -603,6 +667,7 @@ int ora_step(const ora_params *P, int nx, int ny, int nz, const double *res, dou
                                         2.0 * gh[0].Er / (P->delta * gh[0].rho), gh[0].kap,
                                         2.0 * gh[1].Er / (P->delta * gh[1].rho), gh[1].kap)) {
                     free(gs); free(rho); free(u); free(kap); free(Ep); free(Ec); free(th); free(v);
+                    free(Tt);
                     return 1;
                 }
             }
@@ -627,7 +692,7 @@ int ora_step(const ora_params *P, int nx, int ny, int nz, const double *res, dou
             memcpy(Er, Ec, sizeof(double) * N);
         }
     }
-    free(gs); free(rho); free(u); free(kap); free(Ep); free(Ec); free(th); free(v);
+    free(gs); free(rho); free(u); free(kap); free(Ep); free(Ec); free(th); free(v); free(Tt);
     return 0;
 }
 
@@ -680,8 +745,8 @@ void ora_diag(const ora_params *P, int nx, int ny, int nz, const double *g, cons
             E += 0.5 * gp[i] * c2;
             if (gp[i] < gmin) gmin = gp[i];
         }
-        E += Er[p];
         f_from_g(P, gp, Er[p], f, &m);
+        E += (P->rot_mode == 1) ? 0.5 * P->delta * m.rho * m.R : Er[p];
         for (i = 0; i < Q; i++) {
             if (f[i] <= 0.0) { Hp = NAN; break; }
             Hp += f[i] * log(f[i] / W[i]) - f[i];
