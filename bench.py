@@ -389,7 +389,8 @@ def run_surrogate(args):
             "tubes_handed_to_lbm": int(handed.sum()), "network_windows": int(res["windows"].sum()),
             "windows_total": windows_total, "spot_checks": int(res["checks"].sum()),
             "training": {"data_s": t_data, "train_s": t_train, "steps": args.train_steps,
-                         "loss_first": float(np.mean(hist[:50])), "loss_last": float(np.mean(hist[-200:]))},
+                         "loss_first": float(np.mean(hist[:50])) if hist else None,
+                         "loss_last": float(np.mean(hist[-200:])) if hist else None},
             "autotune": tune, "clocks": {"lbm": clk_lbm.summary(), "surrogate": clk_sur.summary()}}
     print(json.dumps(line))
     R.close()

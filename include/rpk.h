@@ -140,6 +140,19 @@ rpk_status rpk_set_gas(rpk_lattice* lat, double gamma, double eta, double eta_B,
  * then of the high end. Must be called after rpk_set_relax and before
  * rpk_init_fields. */
 rpk_status rpk_set_reservoirs(rpk_lattice* lat, const double* states12);
+/* Rotational solver. mode 0 (default): the conservative form -- the state is
+ * the auxiliary energy E~_R = E_R - (dt/2)(delta rho/2)(theta - theta_R)/tau1,
+ * exchanged inside the collision and transported in flux form (total energy
+ * conserved to round-off). mode 1: the paper's four steps on theta_R (Sec. 5):
+ * backward-Euler half step theta_R <- (theta_R + X theta_T(f))/(1 + X),
+ * X = 3 dt/(2 tau1 (3 + delta)), with theta_T(f) of time t; MacCormack on
+ * u . grad theta_R (forward then backward differences, u of time t); nsub FTCS
+ * sub-steps of (2/(rho delta)) kappa_R lap theta_R; the second half step. The
+ * state is then theta_R, theta_T(f) follows from the printed theta_T(g)
+ * relation, and total energy is conserved only to first order in dt/tau1.
+ * Changing the mode discards the state (initialise again); checkpoints record
+ * it. */
+rpk_status rpk_set_rot_mode(rpk_lattice* lat, int mode);
 
 /* Initial state from hydrodynamic fields (layout above): rho > 0, u (3
  * planes), theta_T > 0, theta_R > 0. f = f^Eq(rho, u, theta_T I), then

@@ -124,6 +124,7 @@ def load_library(path=None):
         "rpk_set_relax": (i, [vp, ctypes.POINTER(Relax)]),
         "rpk_set_gas": (i, [vp, d, d, d, d, d]),
         "rpk_set_reservoirs": (i, [vp, _dp]),
+        "rpk_set_rot_mode": (i, [vp, i]),
         "rpk_init_fields": (i, [vp, vp, vp, vp, vp, i]),
         "rpk_step": (i, [vp, i64]),
         "rpk_read_moments": (i, [vp, vp, vp, vp, vp, vp, i]),
@@ -291,6 +292,12 @@ class Lattice:
     def set_reservoirs(self, states12):
         s = np.ascontiguousarray(states12, dtype=np.float64).reshape(12)
         _check(load_library().rpk_set_reservoirs(self._h, s.ctypes.data_as(_dp)))
+        return self
+
+    def set_rot_mode(self, mode):
+        """'conservative' (default) or 'paper' (the four-step theta_R solver of
+        Sec. 5); discards the state."""
+        _check(load_library().rpk_set_rot_mode(self._h, {"conservative": 0, "paper": 1}[mode]))
         return self
 
     def init_fields(self, rho, u, T, R):

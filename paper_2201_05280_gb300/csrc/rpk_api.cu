@@ -262,6 +262,20 @@ rpk_status rpk_set_reservoirs(rpk_lattice* L, const double* s) {
   return RPK_OK;
 }
 
+rpk_status rpk_set_rot_mode(rpk_lattice* L, int mode) {
+  if (!L) return fail(RPK_ERR_ARG, "lattice is NULL");
+  if (mode != 0 && mode != 1) return fail(RPK_ERR_ARG, "mode must be 0 (conservative) or 1 (paper)");
+  if (mode == L->rot_mode) return RPK_OK;
+  L->rot_mode = mode;
+  L->init_ok = false;  // the stored rotational state changes meaning: initialise again
+  if (L->res_ok) {
+    cudaError_t err = cudaSetDevice(L->device);
+    if (err != cudaSuccess) return cuda_fail(err, "cudaSetDevice");
+    return with_ops(L->grid.precision, [&](auto ops) { return decltype(ops)::ghosts(L); });
+  }
+  return RPK_OK;
+}
+
 static rpk_status ensure_stage(rpk_lattice* L) {
   if (L->stage) return RPK_OK;
   const size_t bytes = sizeof(double) * 7 * (size_t)L->npts;
@@ -416,6 +430,7 @@ struct CkptHeader {
   int64_t steps;
   rpk_relax relax;
   double res[12];
+  int32_t rot_mode, pad;
 };
 }  // namespace
 
@@ -442,7 +457,8 @@ rpk_status rpk_save(rpk_lattice* L, const char* path) {
   FILE* f = fopen(path, "wb");
   if (!f) return fail(RPK_ERR_IO, std::string("cannot open ") + path);
   CkptHeader h{};
-  std::memcpy(h.magic, "RPKCKPT1", 8);
+  std::memcpy(h.magic, "RPKCKPT2", 8);
+  h.rot_mode = L->rot_mode;
   h.abi = RPK_ABI_VERSION;
   h.nx = L->grid.nx; h.ny = L->grid.ny; h.nz = L->grid.nz;
   h.precision = L->grid.precision; h.bc_x = L->grid.bc_x;
@@ -470,8 +486,10 @@ rpk_status rpk_load(rpk_lattice* L, const char* path) {
   if (!f) return fail(RPK_ERR_IO, std::string("cannot open ") + path);
   CkptHeader h{};
   rpk_status st = RPK_OK;
-  if (fread(&h, sizeof(h), 1, f) != 1 || std::memcmp(h.magic, "RPKCKPT1", 8) != 0)
+  if (fread(&h, sizeof(h), 1, f) != 1 || std::memcmp(h.magic, "RPKCKPT2", 8) != 0)
     st = fail(RPK_ERR_IO, "not a checkpoint");
+  else if (h.rot_mode != L->rot_mode)
+    st = fail(RPK_ERR_ARG, "checkpoint rotational mode differs from the lattice (rpk_set_rot_mode)");
   else if (h.nx != L->grid.nx || h.ny != L->grid.ny || h.nz != L->grid.nz ||
            h.precision != L->grid.precision || h.bc_x != L->grid.bc_x)
     st = fail(RPK_ERR_ARG, "checkpoint grid differs from the lattice");

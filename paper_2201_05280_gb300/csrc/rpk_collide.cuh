@@ -13,11 +13,11 @@ namespace rpk {
 // Collision of one gathered point, in place of the paper's explicit update:
 // writes the 41 relaxed populations through `out` (element q at out[q * n3]),
 // returns the moments in m and the exchanged auxiliary rotational energy.
-template <typename Store, typename Real>
+template <typename Store, typename Real, bool kPaper = false>
 __device__ __forceinline__ Real collide_point(const StepConst<Real>& K, const Real (&h)[kQ], Real e,
                                               Store* __restrict__ out, Mom<Real>& m) {
   raw_moments(h, m);
-  recover(m, e, K);
+  recover<Real, kPaper>(m, e, K);
   Herm<Real> H;
   mix_coeffs(m, K, H);
   const int64_t n3 = K.n3;
@@ -30,7 +30,12 @@ __device__ __forceinline__ Real collide_point(const StepConst<Real>& K, const Re
     out[(int64_t)(2 * k + 1) * n3] = from_real<Store, Real>(K.c_keep * h[2 * k + 1] + K.c_relax * (ev + od));
     out[(int64_t)(2 * k + 2) * n3] = from_real<Store, Real>(K.c_keep * h[2 * k + 2] + K.c_relax * (ev - od));
   });
-  return e + K.exc * m.rho * (m.dth - m.dR);
+  // conservative form: the exchanged auxiliary energy; paper mode: theta_R after
+  // the first backward-Euler half step with the time-t theta_T (Sec. 5, step 1)
+  if constexpr (kPaper)
+    return K.ra_keep * m.dR + K.ra_t * m.dT;
+  else
+    return e + K.exc * m.rho * (m.dth - m.dR);
 }
 
 // Device status flags: 1 non-finite moment, 2 rho <= 0, 4 theta_T or theta_R <= 0.
@@ -51,19 +56,22 @@ __device__ __forceinline__ void flag_moments(const Mom<Real>& m, Real theta0,
 //   g' = (1 - 2 beta*) g + 2 beta* f^mix,   in h form: h' = c_keep h + c_relax (f^mix/w - 1)
 //   Er' = Er + dt (delta rho/2)(theta - theta_R)/tau1   (rotational exchange)
 // Writes h', e', rho - 1, u (ring slot of this step) and kappa_R.
-template <typename Store, typename Real, bool kPull, int kBC>
-__global__ void __launch_bounds__(128)
+// FP32/16-bit arithmetic: at most 102 registers, so that five 128-thread blocks
+// per SM keep enough loads in flight.
+template <typename Store, typename Real, bool kPull, int kBC, bool kPaper>
+__global__ void __launch_bounds__(128, sizeof(Real) == 4 ? 5 : 1)
     k_collide(StepConst<Real> K, const Store* __restrict__ pin, Store* __restrict__ pout,
               const Real* __restrict__ e_in, Real* __restrict__ e_out, Real* __restrict__ drho_out,
               Real* __restrict__ u_out, Real* __restrict__ kap_out,
-              const Real* __restrict__ ghost, unsigned* __restrict__ status) {
+              const Real* __restrict__ ghost, unsigned* __restrict__ status,
+              Real* __restrict__ tt_out) {
   PointIdx P;
   if (!point_from_block(K, P)) return;
   const int64_t p = (int64_t)P.s * K.n3 + P.cell;
   Real h[kQ];
   gather<Store, Real, kPull, kBC>(pin, ghost, K, P, h);
   Mom<Real> m;
-  const Real es = collide_point<Store, Real>(K, h, e_in[p],
+  const Real es = collide_point<Store, Real, kPaper>(K, h, e_in[p],
                                              pout + (int64_t)(P.s * kQ) * K.n3 + P.cell, m);
   e_out[p] = es;
   drho_out[p] = m.drho;
@@ -72,6 +80,7 @@ __global__ void __launch_bounds__(128)
   u_out[npts + p] = m.j[1] * m.inv_rho;
   u_out[2 * npts + p] = m.j[2] * m.inv_rho;
   kap_out[p] = K.kapc * m.rho * (K.theta0 + m.dth);
+  if constexpr (kPaper) tt_out[p] = m.dT;  // paper mode: theta_T(f) - theta0 of time t
   flag_moments(m, K.theta0, status);
 }
 

@@ -80,6 +80,12 @@ struct StepConst {
   Real E0;        // delta theta0 / 2
   Real dt;
   Real hsub;      // dt / nsub
+  // paper mode of the rotational solver (Sec. 5, four steps on theta_R):
+  int paper;      // 1: the state holds theta_R - theta0 instead of the auxiliary energy
+  Real ra_keep;   // 1 / (1 + X), X = 3 dt / (2 tau1 (3 + delta)): backward-Euler half step
+  Real ra_t;      // X / (1 + X)
+  Real pa;        // a = delta X / 3: theta_T(g) = theta_T + a (theta_T - theta_R)
+  Real inv_1pa;   // 1 / (1 + a)
 };
 
 // Ghost (reservoir) values, one block of kGhostStride per x end.
@@ -131,24 +137,33 @@ __device__ __forceinline__ void raw_moments(const Real (&h)[kQ], Mom<Real>& m) {
 }
 
 // f-level moments from g (Sec. 5, g/f relations) and the stored auxiliary
-// rotational energy e (deviation).
+// rotational energy e (deviation) -- or, in paper mode, the stored theta_R:
+// then theta_T(f) = (theta_T(g) + a theta_R)/(1 + a) inverts the printed
+// theta_T(g) relation.
 //   theta_T(g) = (tr P - j^2/rho)/(3 rho)
 //   Rt = 2 Er/(delta rho)  (auxiliary rotational temperature)
 //   theta = (3 theta_T(g) + delta Rt)/(3 + delta)   (invariant of the transform)
 //   D = (theta_T(g) - Rt)/(1 + dt/(2 tau1)) = theta_T(f) - theta_R
 //   theta_T(f) = theta + delta D/(3 + delta),  theta_R = theta - 3 D/(3 + delta)
 //   sigma(f) = (P - jj/rho - rho theta_T(g) I)/(1 + dt/(2 tau*) - b dt/(2 tau))
-template <typename Real>
+template <typename Real, bool kPaper = false>
 __device__ __forceinline__ void recover(Mom<Real>& m, Real e, const StepConst<Real>& K) {
   const Real t0 = K.theta0;
   const Real jj = m.j[0] * m.j[0] + m.j[1] * m.j[1] + m.j[2] * m.j[2];
   const Real trdP = m.dP[0] + m.dP[1] + m.dP[2];
   m.dTg = (trdP - jj * m.inv_rho - Real(3) * t0 * m.drho) * m.inv_rho * Real(1.0 / 3.0);
-  const Real dRt = (Real(2) * e - K.delta * t0 * m.drho) * m.inv_rho / K.delta;
-  m.dth = (Real(3) * m.dTg + K.delta * dRt) * K.inv_3pd;
-  const Real D = (m.dTg - dRt) * K.inv_d;
-  m.dT = m.dth + K.delta * D * K.inv_3pd;
-  m.dR = m.dth - Real(3) * D * K.inv_3pd;
+  if constexpr (kPaper) {
+    // paper mode: e is theta_R - theta0 itself
+    m.dR = e;
+    m.dT = (m.dTg + K.pa * m.dR) * K.inv_1pa;
+    m.dth = (Real(3) * m.dT + K.delta * m.dR) * K.inv_3pd;
+  } else {
+    const Real dRt = (Real(2) * e - K.delta * t0 * m.drho) * m.inv_rho / K.delta;
+    m.dth = (Real(3) * m.dTg + K.delta * dRt) * K.inv_3pd;
+    const Real D = (m.dTg - dRt) * K.inv_d;
+    m.dT = m.dth + K.delta * D * K.inv_3pd;
+    m.dR = m.dth - Real(3) * D * K.inv_3pd;
+  }
   const Real iso = m.rho * m.dTg + t0 * m.drho;
   const Real ir = m.inv_rho;
   m.sig[0] = (m.dP[0] - m.j[0] * m.j[0] * ir - iso) * K.inv_sig;

@@ -20,6 +20,7 @@ struct rpk_lattice {
   bool res_ok = false;
   double res[12] = {0};
   int nsub = 1;          // FTCS sub-steps in use
+  int rot_mode = 0;      // 0 conservative rotational transport, 1 the paper's theta_R solver
   int64_t n3 = 0, npts = 0;
   size_t store_elem = 0;  // bytes per stored population
   size_t real_elem = 0;   // bytes per field value

@@ -191,6 +191,69 @@ __global__ void __launch_bounds__(kTBX * kTBY)
   e_next[p] = ec[p] + K.hsub * acc;
 }
 
+// ---------------------------------------------------------------------------
+// Paper mode of the rotational solver (Sec. 5): after the collision has done
+// step 1 (first backward-Euler half step, stored in es), three passes on
+// theta_R - theta0 with u of time t:
+//   k_pm_pred  MacCormack predictor of u . grad theta_R (forward differences)
+//   k_pm_corr  corrector (backward differences)
+//   k_pm_ftcs  FTCS sub-step of (2/(rho delta)) kappa_R lap theta_R; the last
+//              sub-step also applies step 4, the second half step with the
+//              stored time-t theta_T
+template <typename Real, int kBC>
+__device__ __forceinline__ Real pm_nb(const StepConst<Real>& K, const PointIdx& P, const Real* __restrict__ r,
+                                      const Real* __restrict__ ghost, int a, int d) {
+  const int64_t q = axis_nb<kBC>(K, P, a, d);
+  if (kBC == 1 && q < 0) return ghost[(q == -1 ? 0 : kGhostStride) + kGhE];
+  return r[q];
+}
+
+template <typename Real, int kBC>
+__global__ void __launch_bounds__(kTBX * kTBY)
+    k_pm_pred(StepConst<Real> K, const Real* __restrict__ r, const Real* __restrict__ ucur,
+              Real* __restrict__ rp, const Real* __restrict__ ghost) {
+  PointIdx P;
+  if (!point_from_block2d(K, P)) return;
+  const int64_t p = (int64_t)P.s * K.n3 + P.cell, npts = 2 * K.n3;
+  const Real r0 = r[p];
+  Real adv = Real(0);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) adv += ucur[a * npts + p] * (pm_nb<Real, kBC>(K, P, r, ghost, a, +1) - r0);
+  rp[p] = r0 - K.dt * adv;
+}
+
+template <typename Real, int kBC>
+__global__ void __launch_bounds__(kTBX * kTBY)
+    k_pm_corr(StepConst<Real> K, const Real* __restrict__ r, const Real* __restrict__ rp,
+              const Real* __restrict__ ucur, Real* __restrict__ rc, const Real* __restrict__ ghost) {
+  PointIdx P;
+  if (!point_from_block2d(K, P)) return;
+  const int64_t p = (int64_t)P.s * K.n3 + P.cell, npts = 2 * K.n3;
+  const Real q0 = rp[p];
+  Real adv = Real(0);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) adv += ucur[a * npts + p] * (q0 - pm_nb<Real, kBC>(K, P, rp, ghost, a, -1));
+  rc[p] = Real(0.5) * (r[p] + q0 - K.dt * adv);
+}
+
+template <typename Real, int kBC>
+__global__ void __launch_bounds__(kTBX * kTBY)
+    k_pm_ftcs(StepConst<Real> K, const Real* __restrict__ r, const Real* __restrict__ drho,
+              const Real* __restrict__ kap, const Real* __restrict__ tt, Real* __restrict__ rn,
+              const Real* __restrict__ ghost, int last) {
+  PointIdx P;
+  if (!point_from_block2d(K, P)) return;
+  const int64_t p = (int64_t)P.s * K.n3 + P.cell;
+  const Real r0 = r[p];
+  Real lap = Real(0);
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+    lap += pm_nb<Real, kBC>(K, P, r, ghost, a, +1) - Real(2) * r0 + pm_nb<Real, kBC>(K, P, r, ghost, a, -1);
+  Real v = r0 + K.hsub * Real(2) * kap[p] / ((Real(1) + drho[p]) * K.delta) * lap;
+  if (last) v = K.ra_keep * v + K.ra_t * tt[p];
+  rn[p] = v;
+}
+
 // Initial state of one point (Sec. 5): f = f^Eq(rho, u, theta_T I),
 // g = f - (dt/2) Omega(f) with Omega = (f^Eq(rho, u, theta I) - f)/tau1 (the ES
 // term vanishes since sigma = 0), Er = E_R - (dt/2)(delta rho/2)(theta - theta_R)/tau1.
@@ -222,9 +285,11 @@ __device__ __forceinline__ void init_point(const StepConst<Real>& K, Real half_d
     h[2 * k + 1] = fp - half_dt_over_tau1 * (qp - fp);
     h[2 * k + 2] = fm - half_dt_over_tau1 * (qm - fm);
   });
-  // E_R = delta rho theta_R/2 as a deviation from delta theta0/2
-  e = Real(0.5) * K.delta * (rho * dR + K.theta0 * drho) -
-      half_dt_over_tau1 * Real(0.5) * K.delta * rho * (dth - dR);
+  // E_R = delta rho theta_R/2 as a deviation from delta theta0/2 (paper mode:
+  // the state is theta_R - theta0)
+  e = K.paper ? dR
+              : Real(0.5) * K.delta * (rho * dR + K.theta0 * drho) -
+                    half_dt_over_tau1 * Real(0.5) * K.delta * rho * (dth - dR);
 }
 
 // Initial state of every point: writes its own slots (post-stream state), e,
@@ -287,7 +352,10 @@ __global__ void __launch_bounds__(128)
   gather<Store, Real, kPull, kBC>(pin, ghost, K, P, h);
   Mom<Real> m;
   raw_moments(h, m);
-  recover(m, e_in[p], K);
+  if (K.paper)
+    recover<Real, true>(m, e_in[p], K);
+  else
+    recover<Real, false>(m, e_in[p], K);
   if (rho_o) rho_o[p] = 1.0 + (double)m.drho;
   if (u_o) {
     u_o[p] = (double)(m.j[0] * m.inv_rho);
@@ -348,7 +416,16 @@ __global__ void __launch_bounds__(kDiagThreads)
       ek += 0.5 * c2 * w * (hp + hm);
       gmin = fmin(gmin, fmin(w * (1.0 + hp), w * (1.0 + hm)));
     });
-    const double Ee = (double)e_in[p];
+    Mom<Real> m;
+    raw_moments(h, m);
+    if (K.paper)
+      recover<Real, true>(m, e_in[p], K);
+    else
+      recover<Real, false>(m, e_in[p], K);
+    // paper mode holds theta_R: its energy density delta rho theta_R / 2 (deviation)
+    const double Ee = K.paper ? 0.5 * (double)K.delta * ((double)m.rho * ((double)K.theta0 + (double)m.dR) -
+                                                          (double)K.theta0)
+                              : (double)e_in[p];
     acc[0] += 1.0 + dm;
     acc[1] += jx;
     acc[2] += jy;
@@ -358,9 +435,6 @@ __global__ void __launch_bounds__(kDiagThreads)
     acc[6] = fmin(acc[6], gmin);
     // H1 from f = (1 - beta*) g + beta* f^mix, per point in the arithmetic
     // precision of the path, accumulated in FP64
-    Mom<Real> m;
-    raw_moments(h, m);
-    recover(m, e_in[p], K);
     Herm<Real> H;
     mix_coeffs(m, K, H);
     const Real beta = K.beta, keep = Real(1) - K.beta;

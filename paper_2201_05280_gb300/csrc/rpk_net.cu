@@ -311,21 +311,37 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv_tc(TcArgs P) {
       int q0, cnt, lo, len;
       tc_tile(P, tile, q0, cnt, lo, len);
       unsigned char* dst = sB + b * TC_B_BYTES;
-      for (int e = ptid; e < TC_ROWS * (TC_KC / 8); e += 128) {
-        const int r = e % TC_ROWS, c = e / TC_ROWS;
-        const int q = q0 - 2 + r;
-        uint4 packed = make_uint4(0u, 0u, 0u, 0u);
-        if (q >= lo && q < lo + len) {
-          const float4* src = reinterpret_cast<const float4*>(P.X + (int64_t)q * TC_KC + 8 * c);
-          float4 f0 = src[0], f1 = src[1];
+      // 2112 (row, chunk) elements, 17 per thread: loads of a batch of 4 are
+      // issued before any is converted
+      constexpr int kElems = TC_ROWS * (TC_KC / 8), kBatch = 4;
+      for (int e0 = ptid; e0 < kElems; e0 += 128 * kBatch) {
+        float4 f[kBatch][2];
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u) {
+          const int e = e0 + u * 128;
+          const int r = e % TC_ROWS, c = e / TC_ROWS;
+          const int q = q0 - 2 + r;
+          f[u][0] = f[u][1] = make_float4(0.f, 0.f, 0.f, 0.f);
+          if (e < kElems && q >= lo && q < lo + len) {
+            const float4* src = reinterpret_cast<const float4*>(P.X + (int64_t)q * TC_KC + 8 * c);
+            f[u][0] = src[0];
+            f[u][1] = src[1];
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u) {
+          const int e = e0 + u * 128;
+          if (e >= kElems) break;
+          const int r = e % TC_ROWS, c = e / TC_ROWS;
+          float4 f0 = f[u][0], f1 = f[u][1];
           if (P.relu_in) {
             f0.x = fmaxf(f0.x, 0.f), f0.y = fmaxf(f0.y, 0.f), f0.z = fmaxf(f0.z, 0.f), f0.w = fmaxf(f0.w, 0.f);
             f1.x = fmaxf(f1.x, 0.f), f1.y = fmaxf(f1.y, 0.f), f1.z = fmaxf(f1.z, 0.f), f1.w = fmaxf(f1.w, 0.f);
           }
-          packed = make_uint4(pack_bf16(f0.x, f0.y), pack_bf16(f0.z, f0.w), pack_bf16(f1.x, f1.y),
-                              pack_bf16(f1.z, f1.w));
+          *reinterpret_cast<uint4*>(dst + c * TC_B_LBO + r * 16) =
+              make_uint4(pack_bf16(f0.x, f0.y), pack_bf16(f0.z, f0.w), pack_bf16(f1.x, f1.y),
+                         pack_bf16(f1.z, f1.w));
         }
-        *reinterpret_cast<uint4*>(dst + c * TC_B_LBO + r * 16) = packed;
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       mbar_arrive(bar0 + 8 * b);  // B full (128 arrivals)
@@ -392,15 +408,23 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv_tc(TcArgs P) {
               "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
             : "r"(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(b * TC_N + j * 32)));
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        // all loads of the chunk first (out may alias res: each element is read
+        // and then written by this thread), then the stores
+        float add[32];
+        uint32_t drop = 0;  // bit k: masked out
+#pragma unroll
+        for (int k = 0; k < 32; ++k) {
+          const int n = j * 32 + k;
+          const int64_t o = (int64_t)(q0 + n) * TC_M + m;
+          add[k] = (P.res && n < cnt) ? P.res[o] : 0.f;
+          if (P.mask && n < cnt && !(P.mask[o] > 0.f)) drop |= 1u << k;
+        }
 #pragma unroll
         for (int k = 0; k < 32; ++k) {
           const int n = j * 32 + k;
           if (n < cnt) {
-            const int64_t o = (int64_t)(q0 + n) * TC_M + m;
-            float val = __uint_as_float(v[k]) + bm;
-            if (P.mask && !(P.mask[o] > 0.f)) val = 0.f;
-            if (P.res) val += P.res[o];
-            P.out[o] = val;
+            const float val = ((drop >> k) & 1u) ? 0.f : __uint_as_float(v[k]) + bm;
+            P.out[(int64_t)(q0 + n) * TC_M + m] = val + add[k];
           }
         }
       }

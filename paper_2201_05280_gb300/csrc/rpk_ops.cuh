@@ -13,7 +13,8 @@ namespace rpk {
 // Per-launch constants of the step (Sec. 5) for relaxation parameters r on an
 // nx x ny x nz grid with nsub FTCS sub-steps; computed in double, then cast.
 template <typename Real>
-static StepConst<Real> make_step_const(const rpk_relax& r, int nsub, int nx, int ny, int nz) {
+static StepConst<Real> make_step_const(const rpk_relax& r, int nsub, int nx, int ny, int nz,
+                                       int paper = 0) {
   const double tau_s = 1.0 / (1.0 / r.tau + 1.0 / r.tau1);
   const double beta = r.dt / (2.0 * tau_s + r.dt);
   const double B = 1.0 + r.tau / r.tau1;
@@ -38,12 +39,18 @@ static StepConst<Real> make_step_const(const rpk_relax& r, int nsub, int nx, int
   K.E0 = Real(0.5 * r.delta * kTheta0);
   K.dt = Real(r.dt);
   K.hsub = Real(r.dt / std::max(1, nsub));
+  const double X = 3.0 * r.dt / (2.0 * r.tau1 * (3.0 + r.delta));
+  K.paper = paper;
+  K.ra_keep = Real(1.0 / (1.0 + X));
+  K.ra_t = Real(X / (1.0 + X));
+  K.pa = Real(r.delta * X / 3.0);
+  K.inv_1pa = Real(1.0 / (1.0 + r.delta * X / 3.0));
   return K;
 }
 
 template <typename Real>
 static StepConst<Real> make_const(const rpk_lattice* L) {
-  return make_step_const<Real>(L->relax, L->nsub, L->grid.nx, L->grid.ny, L->grid.nz);
+  return make_step_const<Real>(L->relax, L->nsub, L->grid.nx, L->grid.ny, L->grid.nz, L->rot_mode);
 }
 
 static inline dim3 point_grid(const rpk_lattice* L, int bx) {
@@ -62,10 +69,16 @@ static rpk_status collide_launch(rpk_lattice* L, const StepConst<Real>& K) {
   const Store* pin = static_cast<const Store*>(L->pop[L->cur]);
   Store* pout = static_cast<Store*>(L->pop[L->cur ^ 1]);
   Real* ucur = static_cast<Real*>(L->u[L->steps & 1]);
-  k_collide<Store, Real, kPull, kBC><<<point_grid(L, 128), 128, 0, L->stream>>>(
-      K, pin, pout, static_cast<const Real*>(L->e), static_cast<Real*>(L->e_star),
-      static_cast<Real*>(L->drho), ucur, static_cast<Real*>(L->kap),
-      static_cast<const Real*>(L->ghost), L->status);
+  if (L->rot_mode)
+    k_collide<Store, Real, kPull, kBC, true><<<point_grid(L, 128), 128, 0, L->stream>>>(
+        K, pin, pout, static_cast<const Real*>(L->e), static_cast<Real*>(L->e_star),
+        static_cast<Real*>(L->drho), ucur, static_cast<Real*>(L->kap),
+        static_cast<const Real*>(L->ghost), L->status, static_cast<Real*>(L->thbuf));
+  else
+    k_collide<Store, Real, kPull, kBC, false><<<point_grid(L, 128), 128, 0, L->stream>>>(
+        K, pin, pout, static_cast<const Real*>(L->e), static_cast<Real*>(L->e_star),
+        static_cast<Real*>(L->drho), ucur, static_cast<Real*>(L->kap),
+        static_cast<const Real*>(L->ghost), L->status, nullptr);
   return check_launch("k_collide");
 }
 
@@ -87,6 +100,21 @@ static rpk_status transport_launch(rpk_lattice* L, const StepConst<Real>& K) {
   const dim3 tgrid((unsigned)((L->grid.nx + kTBX - 1) / kTBX),
                    (unsigned)((L->grid.ny + kTBY - 1) / kTBY), (unsigned)(2 * L->grid.nz));
   RPK_CUDA(timing_begin(L));
+  if (L->rot_mode) {
+    // paper mode: MacCormack on theta_R, FTCS sub-steps, the last with the
+    // second relaxation half step (th holds the time-t theta_T)
+    k_pm_pred<Real, kBC><<<tgrid, tb, 0, L->stream>>>(K, es, ucur, ea, gh);
+    k_pm_corr<Real, kBC><<<tgrid, tb, 0, L->stream>>>(K, es, ea, ucur, eb, gh);
+    const Real* src = eb;
+    for (int k = 0; k < L->nsub; ++k) {
+      Real* dst = (k == L->nsub - 1) ? e : (src == eb ? ea : eb);
+      k_pm_ftcs<Real, kBC><<<tgrid, tb, 0, L->stream>>>(K, src, drho, kap, th, dst, gh,
+                                                         k == L->nsub - 1);
+      src = dst;
+    }
+    RPK_CUDA(timing_end(L, RPK_KC_TRANSPORT, 2 + L->nsub));
+    return check_launch("rotational transport (paper mode)");
+  }
   k_mac_pred<Real, kBC><<<tgrid, tb, 0, L->stream>>>(K, es, ucur, uprev, ea, v, gh);
   k_mac_corr<Real, kBC><<<tgrid, tb, 0, L->stream>>>(K, es, ea, v, drho, eb, th, gh);
   // first FTCS sub-step from the stored theta_R; further sub-steps end in e
