@@ -262,6 +262,14 @@ def run_batch(args):
                        "eta_B_over_eta": [0.3, 2.0], "rotational_diffusion": args.diffusion},
             "autotune": tune, "gpu_launches": 1, "all_finite": finite,
             "clocks": clk.summary()}
+    # populations read once and written once per point update; the tube's
+    # other fields stay in shared memory for the whole run
+    peak, src = load_peaks()
+    gbs = updates * 41 * 2 * 4 / (ms * 1e-3) / 1e9
+    line["roofline"] = {"bound": "hbm", "kernel": "k_batch (one persistent launch)",
+                        "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
+                        "peak_source": src, "algorithmic_bytes_per_point_update": 328,
+                        "traffic": None}
     print(json.dumps(line))
     bt.close()
     return 0
