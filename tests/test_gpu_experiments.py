@@ -1,4 +1,4 @@
-"""Two of the paper's validation experiments run on the GPU path (FP32), with
+"""Three of the paper's validation experiments run on the GPU path (FP32), with
 synthetic inputs as the paper describes them.
 
 E1 (Sec. 6, sound speed, Table 2): a pressure wave p = p0 (1 + eps cos x) on a
@@ -100,3 +100,37 @@ def test_e2_sound_absorption_gives_the_landau_numbers_of_table3(row):
     Pr, la = _table("landau_table3.txt")[row]
     got = _landau(Pr)
     assert abs(got / la - 1) < 0.05, (Pr, got, la)
+
+
+def test_e3_acoustic_pulse_matches_the_linearised_euler_solution():
+    from scipy.integrate import quad
+    from scipy.special import j0
+    n, nz = 256, 4
+    b = 0.1 * n / 2  # [-1, 1] spans n cells
+    alpha, eps, gamma = np.log(2) / b ** 2, 1e-3, 1.4
+    cs = np.sqrt(gamma * T0)
+    eta, etaB, kap = PM.gas_from_nondim(gamma, 0.005, 0.6, 0.71)
+    lat = rpk.Lattice(n, n, nz, precision="f32")
+    lat.set_gas(gamma, eta, etaB, kap)
+    f = I.uniform(n, n, nz, T0)
+    X = I.positions(n, n, nz)
+    g = np.exp(-alpha * ((X[0] - n / 2) ** 2 + (X[1] - n / 2) ** 2))
+    p, rho = T0 * (1 + eps * g), 1 + eps * g / gamma
+    f["rho"], f["T"] = rho, p / rho
+    f["R"] = f["T"].copy()
+    lat.init_fields(f["rho"], f["u"], f["T"], f["R"])
+    t = int(round(0.25 * n / cs))
+    lat.step(t)
+    m = lat.read_moments()
+    pp = m["rho"] * m["T"] - T0
+    line = (np.abs(X[1] - n / 2) < 1e-9) & (X[2] == X[2].min())
+    xs = X[0][line] - n / 2
+
+    def exact(r):
+        fn = lambda xi: np.exp(-xi * xi / (4 * alpha)) * np.cos(cs * xi * t) * j0(xi * r) * xi
+        return T0 * eps / (2 * alpha) * quad(fn, 0, 12 * np.sqrt(alpha), limit=400)[0]
+
+    ref = np.array([exact(abs(x)) for x in xs])
+    err = np.abs(pp[line] - ref).max() / (eps * T0)
+    assert err < 0.01, err
+    lat.close()
