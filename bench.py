@@ -405,6 +405,23 @@ def run_surrogate(args):
     return 0
 
 
+def max_over_ranks(x, dist, device="cuda"):
+    """The largest value of x over all ranks (x itself without a process group):
+    the job's time is its slowest rank's."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_mlups(world, npts, steps, ms):
+    """Whole-job throughput of `world` replicas of npts points each over `steps`
+    steps in `ms` milliseconds (the slowest rank's)."""
+    return world * npts * steps / (ms * 1e-3) / 1e6
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -501,13 +518,9 @@ def main():
         barrier()
     ktimes = lat.timing_read()
     lat.timing(False)
-    ms = e0.elapsed_time(e1)
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(e0.elapsed_time(e1), dist)
     diag = lat.diagnostics()
-    value = world * npts * args.steps / (ms * 1e-3) / 1e6
+    value = job_mlups(world, npts, args.steps, ms)
 
     # end to end through the public API with pinned host buffers
     e2e = None
@@ -527,11 +540,7 @@ def main():
         lat2.step(args.steps)
         lat2.read_moments(outs)
         barrier()
-        wall = time.perf_counter() - t0
-        if dist is not None:
-            t = torch.tensor([wall], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            wall = float(t.item())
+        wall = max_over_ranks(time.perf_counter() - t0, dist)
         lat2.close()
         h2d = 6 * npts * 8
         d2h = 7 * npts * 8
