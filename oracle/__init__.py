@@ -50,12 +50,14 @@ class Params(ctypes.Structure):
                 ("tau1", ctypes.c_double), ("b", ctypes.c_double),
                 ("kr", ctypes.c_double), ("dt", ctypes.c_double),
                 ("nsub", ctypes.c_int), ("bcx", ctypes.c_int), ("diff", ctypes.c_int),
-                ("rot_mode", ctypes.c_int)]
+                ("rot_mode", ctypes.c_int), ("bcy", ctypes.c_int),
+                ("wall", ctypes.c_double * 8)]
 
     def __repr__(self):
         return ("Params(delta=%g, tau=%g, tau1=%g, b=%g, kr=%g, dt=%g, nsub=%d, bcx=%d, diff=%d, "
-                "rot_mode=%d)" % (self.delta, self.tau, self.tau1, self.b, self.kr, self.dt,
-                                  self.nsub, self.bcx, self.diff, self.rot_mode))
+                "rot_mode=%d, bcy=%d, wall=%s)" % (self.delta, self.tau, self.tau1, self.b, self.kr,
+                                                   self.dt, self.nsub, self.bcx, self.diff,
+                                                   self.rot_mode, self.bcy, list(self.wall)))
 
 
 _lib = None
@@ -158,13 +160,22 @@ def target(rho, u, Lam):
     return f
 
 
-def make_params(delta, tau, tau1, b=0.0, kr=0.0, dt=1.0, nsub=1, bcx=0, diff=0, rot_mode=0):
+def make_params(delta, tau, tau1, b=0.0, kr=0.0, dt=1.0, nsub=1, bcx=0, diff=0, rot_mode=0,
+                walls=None):
     """diff = 0: FTCS sub-steps of the rotational diffusion (Sec. 5); 1: one
     backward-Euler step per sublattice line (variant for quasi-1-D tubes).
     rot_mode = 0: conservative form on the auxiliary energy Er; 1: the paper's
-    four-step theta_R solver (Sec. 5), the state then holds theta_R."""
-    return Params(float(delta), float(tau), float(tau1), float(b), float(kr), float(dt),
-                  int(nsub), int(bcx), int(diff), int(rot_mode))
+    four-step theta_R solver (Sec. 5), the state then holds theta_R.
+    walls: None (periodic in y) or 8 numbers, ux, uy, uz, theta of the low-y
+    and then of the high-y diffuse wall (uy must be 0)."""
+    P = Params(float(delta), float(tau), float(tau1), float(b), float(kr), float(dt),
+               int(nsub), int(bcx), int(diff), int(rot_mode), 0)
+    if walls is not None:
+        w = np.asarray(walls, dtype=np.float64).reshape(8)
+        P.bcy = 1
+        for k in range(8):
+            P.wall[k] = float(w[k])
+    return P
 
 
 def diffuse_be_line(delta, dt, rho, kap, Er, thl, kl, thr, kr):
@@ -238,7 +249,9 @@ class State:
         rc = _load().ora_step(ctypes.byref(self.P), self.nx, self.ny, self.nz, _ptr(res),
                               _ptr(self.g), _ptr(self.Er), _ptr(self.uprev), int(n))
         if rc == 2:
-            raise ValueError("the backward-Euler diffusion variant needs ny = nz = 1 and bcx = 1")
+            raise ValueError("unsupported setting: the backward-Euler diffusion variant needs "
+                             "ny = nz = 1 and bcx = 1; y walls need ny >= 2, zero normal wall "
+                             "velocity, periodic x and the conservative rotational form")
         if rc != 0:
             raise MemoryError("oracle step could not allocate its work arrays")
         self.t += int(n)

@@ -27,6 +27,8 @@
  *                    (the paper leaves the solver free, end of Sec. 5)
  *   diagnostics      Sec. 4 (conservation laws, eq. ConservedMomEq; H1 of the
  *                    H-theorem paragraph with k = -delta/2)
+ *   diffuse walls    Sec. 6 (the diffusive wall the paper cites for its Couette
+ *                    and cavity flows; the reading is stated at wall_density)
  *
  * Grid layout shared with the library's public interface: a scalar field has
  * 2*nx*ny*nz entries indexed p = ((s*nz + z)*ny + y)*nx + x, s = 0 for the
@@ -65,6 +67,9 @@ typedef struct {
                      step (variant for quasi-1-D tubes: ny = nz = 1, bcx = 1) */
     int rot_mode; /* 0: conservative form, the state holds Er (auxiliary energy density);
                      1: the paper's theta_R solver (Sec. 5, four steps), the state holds theta_R */
+    int bcy;      /* 0: periodic in y; 1: diffuse walls normal to y (Sec. 6, startup and
+                     thermal Couette flows), see wall_fluxes below */
+    double wall[8]; /* bcy = 1: ux, uy, uz, theta of the low-y wall, then of the high-y wall */
 } ora_params;
 
 static void put(int i, double cx, double cy, double cz, double w)
@@ -398,7 +403,8 @@ static int floor_div2(int a) { return (a >= 0) ? a / 2 : -((1 - a) / 2); }
  * sublattice s' is the parity of 2*idx + s - 2c (the same on all axes, since a
  * velocity is either all-integer or all-half-integer) and its index is
  * (2*idx + s - 2c - s')/2. Returns the point index, or -1 / -2 when the source
- * lies beyond the low / high x end (only with bcx = 1).
+ * lies beyond the low / high x end (only with bcx = 1), or -3 / -4 when it lies
+ * beyond the low / high y wall (only with bcy = 1).
  */
 static long pull_source(const ora_params *P, const grid *G, int s, int x, int y, int z, int i)
 {
@@ -414,13 +420,18 @@ static long pull_source(const ora_params *P, const grid *G, int s, int x, int y,
     } else {
         src[0] = wrap(src[0], n[0]);
     }
+    if (P->bcy == 1) {
+        if (src[1] < 0) return -3;
+        if (src[1] >= n[1]) return -4;
+    }
     src[1] = wrap(src[1], n[1]);
     src[2] = wrap(src[2], n[2]);
     return pidx(G, sp, src[0], src[1], src[2]);
 }
 
 /* Axis neighbour on the same sublattice: d = +1 or -1 along axis a. Returns -1
- * / -2 for a reservoir ghost beyond the low / high x end (bcx = 1 only). */
+ * / -2 for a reservoir ghost beyond the low / high x end (bcx = 1 only) and
+ * -3 / -4 for the low / high y wall (bcy = 1 only). */
 static long axis_nb(const ora_params *P, const grid *G, long p, int a, int d)
 {
     int x = (int)(p % G->nx);
@@ -432,6 +443,10 @@ static long axis_nb(const ora_params *P, const grid *G, long p, int a, int d)
     if (a == 0 && P->bcx == 1) {
         if (idx[0] < 0) return -1;
         if (idx[0] >= n[0]) return -2;
+    }
+    if (a == 1 && P->bcy == 1) {
+        if (idx[1] < 0) return -3;
+        if (idx[1] >= n[1]) return -4;
     }
     idx[a] = wrap(idx[a], n[a]);
     return pidx(G, s, idx[0], idx[1], idx[2]);
@@ -458,6 +473,80 @@ static void make_ghost(const ora_params *P, const double *st, ghost *gh)
     gh->rho = st[0];
     gh->u[0] = st[1]; gh->u[1] = st[2]; gh->u[2] = st[3];
     gh->kap = kappa_R(P, st[0], theta);
+}
+
+/*
+ * Diffuse walls (bcy = 1). The paper runs its Couette and cavity flows (Sec. 6)
+ * with the diffusive wall of Ansumali & Karlin (2002), which it cites but does
+ * not write out; this is that boundary condition in the following reading.
+ * The walls are planes normal to y half way between layers of points: at
+ * y = -1/4 and at y = ny - 1/4 in sublattice-spacing units (the layers sit at
+ * y + s/2). A population whose pull source lies beyond a wall is not taken
+ * from the lattice: the wall emits it as rho_w f^eq_i(1, u_w, theta_w), the
+ * discrete Gaussian of the wall's velocity and temperature (full
+ * accommodation), with rho_w set per (x, z) column so that the wall emits
+ * into the column exactly the mass that left the column through it in the
+ * same step:
+ *   rho_w = (sum of the column's post-collision populations whose destination
+ *            lies beyond the wall)
+ *         / (sum of f^eq_i(1, u_w, theta_w) over the column's entries that
+ *            the wall emits).
+ * Mass is conserved exactly; momentum and energy are exchanged with the wall.
+ * The rotational energy sees the walls as Dirichlet boundaries at
+ * theta_R = theta_w (the internal energy is accommodated as well): the
+ * diffusive flux through the wall face of point p is
+ * kappa_R(p) (theta_w - theta_R(p)) / d, d the distance from p to the wall
+ * (1/4 or 3/4), and the advective flux through a wall is zero (the walls slide
+ * tangentially: uy = 0).
+ */
+
+/* y index (not wrapped) of the destination of population i leaving a point on
+ * sublattice s in layer y; the destination sublattice is the parity of
+ * s + 2c, the same on all axes. */
+static int dest_y(int s, int y, int i)
+{
+    const int c2 = (int)lround(2.0 * C[i][1]);
+    const int sd = (s + c2) & 1;
+    return floor_div2(2 * y + s + c2 - sd);
+}
+
+/* Distance from point p (sublattice s) to the low (w = 0) or high (w = 1) y
+ * wall when p is in the layer next to that wall. */
+static double wall_distance(int s, int w)
+{
+    return w == 0 ? (2.0 * s + 1.0) / 4.0 : (3.0 - 2.0 * s) / 4.0;
+}
+
+/* rw[w * nx * nz + z * nx + x]: rho_w of wall w for column (x, z), from the
+ * post-collision populations gs; gw[w] is f^eq(1, u_w, theta_w). */
+static int wall_density(const ora_params *P, const grid *G, const double *gs, double gw[2][Q],
+                        double *rw)
+{
+    const long ncol = (long)G->nx * G->nz;
+    double *out = (double *)calloc(2 * ncol, sizeof(double));
+    double *in = (double *)calloc(2 * ncol, sizeof(double));
+    long p, k;
+    int i;
+    if (!out || !in) {
+        free(out); free(in);
+        return 1;
+    }
+    for (p = 0; p < G->npts; p++) {
+        const int x = (int)(p % G->nx), y = (int)((p / G->nx) % G->ny);
+        const int z = (int)((p / ((long)G->nx * G->ny)) % G->nz), s = (int)(p / G->n3);
+        const long col = (long)z * G->nx + x;
+        for (i = 0; i < Q; i++) {
+            const int yd = dest_y(s, y, i);
+            const long q = pull_source(P, G, s, x, y, z, i);
+            if (yd < 0) out[col] += gs[p * Q + i];
+            if (yd >= G->ny) out[ncol + col] += gs[p * Q + i];
+            if (q == -3) in[col] += gw[0][i];
+            if (q == -4) in[ncol + col] += gw[1][i];
+        }
+    }
+    for (k = 0; k < 2 * ncol; k++) rw[k] = out[k] / in[k];
+    free(out); free(in);
+    return 0;
 }
 
 int ora_init(const ora_params *P, int nx, int ny, int nz, const double *rho, const double *u,
@@ -553,21 +642,40 @@ int ora_step(const ora_params *P, int nx, int ny, int nz, const double *res, dou
     double *th = (double *)malloc(sizeof(double) * N);
     double *v = (double *)malloc(sizeof(double) * 3 * N);
     double *Tt = (double *)malloc(sizeof(double) * N);
-    ghost gh[2];
+    double *rw = (double *)malloc(sizeof(double) * 2 * nx * nz);
+    double gw[2][Q];
+    ghost gh[4];
     long p, t;
     int i, a, k;
-    if (!gs || !rho || !u || !kap || !Ep || !Ec || !th || !v || !Tt) {
+    if (!gs || !rho || !u || !kap || !Ep || !Ec || !th || !v || !Tt || !rw) {
         free(gs); free(rho); free(u); free(kap); free(Ep); free(Ec); free(th); free(v); free(Tt);
+        free(rw);
         return 1;
     }
     need_lattice();
-    if ((P->diff == 1 && (ny != 1 || nz != 1 || P->bcx != 1)) || (P->diff == 1 && P->rot_mode == 1)) {
+    if ((P->diff == 1 && (ny != 1 || nz != 1 || P->bcx != 1)) || (P->diff == 1 && P->rot_mode == 1) ||
+        (P->bcy == 1 && (ny < 2 || P->bcx == 1 || P->rot_mode == 1 || P->diff == 1 ||
+                         P->wall[1] != 0.0 || P->wall[5] != 0.0))) {
         free(gs); free(rho); free(u); free(kap); free(Ep); free(Ec); free(th); free(v); free(Tt);
+        free(rw);
         return 2;
     }
     if (P->bcx == 1) {
         make_ghost(P, res, &gh[0]);
         make_ghost(P, res + 6, &gh[1]);
+    }
+    if (P->bcy == 1) {
+        for (k = 0; k < 2; k++) {
+            const double *wl = P->wall + 4 * k;
+            double Lam[9];
+            for (a = 0; a < 9; a++) Lam[a] = (a % 4 == 0) ? wl[3] : 0.0;
+            ora_target(1.0, wl, Lam, gw[k]);
+            /* transport ghost: only u (the zero normal velocity) is read */
+            gh[2 + k].rho = 1.0;
+            gh[2 + k].Er = 0.5 * P->delta * wl[3];
+            gh[2 + k].kap = 0.0;
+            for (a = 0; a < 3; a++) gh[2 + k].u[a] = wl[a];
+        }
     }
     for (t = 0; t < nsteps; t++) {
         /* 1. collision and rotational exchange */
@@ -580,13 +688,23 @@ int ora_step(const ora_params *P, int nx, int ny, int nz, const double *res, dou
             kap[p] = kappa_R(P, m.rho, m.theta);
             Tt[p] = m.T;
         }
-        /* 2. pull streaming */
+        /* 2. pull streaming; the walls emit rho_w f^eq(1, u_w, theta_w) */
+        if (P->bcy == 1 && wall_density(P, &G, gs, gw, rw)) {
+            free(gs); free(rho); free(u); free(kap); free(Ep); free(Ec); free(th); free(v); free(Tt);
+            free(rw);
+            return 1;
+        }
         for (p = 0; p < N; p++) {
             int x = (int)(p % nx), y = (int)((p / nx) % ny), z = (int)((p / ((long)nx * ny)) % nz);
             int s = (int)(p / G.n3);
             for (i = 0; i < Q; i++) {
                 long q = pull_source(P, &G, s, x, y, z, i);
-                g[p * Q + i] = (q >= 0) ? gs[q * Q + i] : gh[-1 - q].g[i];
+                if (q >= 0)
+                    g[p * Q + i] = gs[q * Q + i];
+                else if (q >= -2)
+                    g[p * Q + i] = gh[-1 - q].g[i];
+                else
+                    g[p * Q + i] = rw[(q == -3 ? 0 : (long)nx * nz) + (long)z * nx + x] * gw[-3 - q][i];
             }
         }
         if (P->rot_mode == 1) {
@@ -667,7 +785,7 @@ int ora_step(const ora_params *P, int nx, int ny, int nz, const double *res, dou
                                         2.0 * gh[0].Er / (P->delta * gh[0].rho), gh[0].kap,
                                         2.0 * gh[1].Er / (P->delta * gh[1].rho), gh[1].kap)) {
                     free(gs); free(rho); free(u); free(kap); free(Ep); free(Ec); free(th); free(v);
-                    free(Tt);
+                    free(Tt); free(rw);
                     return 1;
                 }
             }
@@ -685,6 +803,15 @@ int ora_step(const ora_params *P, int nx, int ny, int nz, const double *res, dou
                     double thm = (qm >= 0) ? th[qm] : 2.0 * gh[-1 - qm].Er / (P->delta * gh[-1 - qm].rho);
                     double kp = (qp >= 0) ? kap[qp] : gh[-1 - qp].kap;
                     double km = (qm >= 0) ? kap[qm] : gh[-1 - qm].kap;
+                    if (qp <= -3 || qm <= -3) {
+                        /* wall: face coefficient kappa_R(p), gradient over the
+                         * distance d to the wall, as a ghost value on the axis
+                         * neighbour (at distance 1 - d beyond the wall) */
+                        const int w = (qp <= -3) ? 1 : 0, s = (int)(p / G.n3);
+                        const double d = wall_distance(s, w), thw = P->wall[4 * w + 3];
+                        const double gv = thw + (thw - th[p]) * (1.0 - d) / d;
+                        if (w == 1) { thp = gv; kp = kap[p]; } else { thm = gv; km = kap[p]; }
+                    }
                     acc += 0.5 * (kap[p] + kp) * (thp - th[p]) - 0.5 * (kap[p] + km) * (th[p] - thm);
                 }
                 Ec[p] = Er[p] + h * acc;
@@ -693,6 +820,7 @@ int ora_step(const ora_params *P, int nx, int ny, int nz, const double *res, dou
         }
     }
     free(gs); free(rho); free(u); free(kap); free(Ep); free(Ec); free(th); free(v); free(Tt);
+    free(rw);
     return 0;
 }
 

@@ -1,0 +1,247 @@
+"""Pins of the oracle's diffuse walls (y = -1/4 and y = ny - 1/4; the boundary
+condition the paper cites for its Sec. 6 Couette and cavity flows):
+
+  * a state that equals both walls' equilibrium (moving tangentially) is fixed;
+  * mass is conserved to round-off with different, moving, heated walls;
+  * the emitted populations of one step equal rho_w f^eq(1, u_w, theta_w) with
+    rho_w from a brute-force count of the leaving and entering entries;
+  * the mirror y -> ny - 1/2 - y (swapping the sublattices and the walls) maps
+    one step onto the step of the mirrored state;
+  * startup Couette flow follows the series solution printed in Sec. 6;
+  * steady conduction between walls at different temperatures is linear,
+    with the rotational temperature equal to the translational one;
+and planted mistakes in the wall code each fail one of these."""
+import numpy as np
+import pytest
+
+import oracle as O
+import rpk_inputs as I
+from oracle import params as PM
+
+T0 = O.THETA0
+
+
+def _params(nu=0.1, lam=0.6, Pr=0.71, walls=None, kr=None):
+    d, tau, tau1, b, k_r = PM.relax_from_gas(1.4, *PM.gas_from_nondim(1.4, nu, lam, Pr), 0.0)
+    if kr is not None:
+        k_r = kr
+    return O.make_params(d, tau, tau1, b, k_r, 1.0, 1, walls=walls)
+
+
+def _state(P, nx, ny, nz, f):
+    return O.State(P, nx, ny, nz).init_fields(f["rho"], f["u"], f["T"], f["R"])
+
+
+def _layers(ny):
+    """physical y of every point of an nx = nz = 1 grid, measured from the low wall"""
+    return I.positions(1, ny, 1)[1] + 0.25
+
+
+# ---------------------------------------------------------------------------
+# pins
+
+
+def pin_fixed_point():
+    u = np.array([0.05, 0.0, 0.02])
+    P = _params(walls=list(u) + [0.31] + list(u) + [0.31])
+    f = I.uniform(3, 4, 2, 0.31)
+    f["rho"] = f["rho"] * 1.1
+    f["u"] += u[:, None]
+    S = _state(P, 3, 4, 2, f)
+    F0 = S.fields()
+    S.step(5)
+    F1 = S.fields()
+    return max(float(np.abs(F1[k] - F0[k]).max()) for k in ("rho", "u", "T", "R"))
+
+
+def pin_mass():
+    rng = np.random.default_rng(1)
+    nx, ny, nz = 3, 6, 2
+    n = 2 * nx * ny * nz
+    P = _params(walls=[0, 0, 0, 0.28, 0.06, 0, -0.03, 0.31])
+    f = I.uniform(nx, ny, nz, T0)
+    f["rho"] = 1 + 0.05 * rng.uniform(-1, 1, n)
+    f["u"] = 0.03 * rng.uniform(-1, 1, (3, n))
+    f["T"] = T0 * (1 + 0.05 * rng.uniform(-1, 1, n))
+    f["R"] = T0 * (1 + 0.05 * rng.uniform(-1, 1, n))
+    S = _state(P, nx, ny, nz, f)
+    d0 = S.diag()
+    S.step(20)
+    d1 = S.diag()
+    return abs(d1["M"] - d0["M"]) / d0["M"], abs(d1["E"] - d0["E"])
+
+
+def pin_emission():
+    """One step from layer-wise equilibria at the walls' temperature and at
+    rest: the collision leaves them unchanged, so the populations leaving
+    through the low wall are rho(layer) f^eq_i(1, 0, theta_w) and the wall must
+    emit rho_w f^eq_i(1, u_w, theta_w) into every entry whose source lies below
+    it. Returns the largest error over those entries of the low-wall column."""
+    ny, thw = 4, 0.30
+    uw = np.array([0.04, 0.0, -0.02])
+    P = _params(walls=list(uw) + [thw, 0, 0, 0, thw])
+    c, _ = O.lattice()
+    Y2 = 2 * np.arange(ny)[None, :] + np.arange(2)[:, None]     # (s, y) -> 2 * physical y
+    rho_l = 1.0 + 0.03 * np.sin(0.7 * Y2 + 0.3)                 # density of each layer
+    f = I.uniform(1, ny, 1, thw)
+    f["rho"] = rho_l.reshape(-1)
+    S = _state(P, 1, ny, 1, f)
+    S.step(1)
+    feq0 = O.target(1.0, np.zeros(3), thw * np.eye(3))
+    feqw = O.target(1.0, uw, thw * np.eye(3))
+    c2 = np.rint(2 * c[:, 1]).astype(int)
+    leave = sum(rho_l[s, y] * feq0[i] for i in range(41) for s in range(2) for y in range(ny)
+                if 2 * y + s + c2[i] < 0)
+    entries = [(s, y, i) for i in range(41) for s in range(2) for y in range(ny)
+               if 2 * y + s - c2[i] < 0]
+    rho_w = leave / sum(feqw[i] for (_, _, i) in entries)
+    g = S.g.reshape(2, ny, 41)
+    return max(abs(g[s, y, i] - rho_w * feqw[i]) for (s, y, i) in entries)
+
+
+def pin_mirror():
+    """One step of a run and of its mirror image: the populations must map
+    onto each other (population i at point (s, y) <-> the y-reflected velocity
+    at (1 - s, ny - 1 - y)). One step, because MacCormack's forward predictor
+    and backward corrector are not mirror symmetric: over several steps the
+    rotational energy, and through it everything, differs at O(dt^2)."""
+    rng = np.random.default_rng(7)
+    ny = 6
+    wb, wt = [0.03, 0, 0.0, 0.29], [-0.02, 0, 0.01, 0.30]
+    f = I.uniform(1, ny, 1, T0)
+    n = 2 * ny
+    f["rho"] = 1 + 0.05 * rng.uniform(-1, 1, n)
+    f["u"] = 0.03 * rng.uniform(-1, 1, (3, n))
+    f["T"] = T0 * (1 + 0.04 * rng.uniform(-1, 1, n))
+    f["R"] = T0 * (1 + 0.04 * rng.uniform(-1, 1, n))
+    # point (s, y) <-> (1 - s, ny - 1 - y): physical y -> ny - 1/2 - y
+    perm = np.array([(1 - s) * ny + (ny - 1 - y) for s in range(2) for y in range(ny)])
+    fm = {k: (v[..., perm].copy()) for k, v in f.items()}
+    fm["u"][1] *= -1
+    A = _state(_params(walls=wb + wt), 1, ny, 1, f).step(1)
+    B = _state(_params(walls=wt + wb), 1, ny, 1, fm).step(1)
+    c, _ = O.lattice()
+    cm = c * np.array([1, -1, 1])
+    mi = np.array([int(np.argmin(np.abs(c - cm[i]).sum(1))) for i in range(41)])
+    return float(np.abs(B.g[perm][:, mi] - A.g).max())
+
+
+def _series(yL, ts):
+    # Sec. 6: startup Couette flow, top plate at y = L started impulsively
+    k = np.arange(1, 400)[:, None]
+    return yL - (2 / np.pi) * np.sum(np.exp(-(k * np.pi) ** 2 * ts) / k * np.sin(k * np.pi * (1 - yL)), axis=0)
+
+
+def pin_couette(times=(0.1, 0.2, 0.5)):
+    ny, U, nu = 16, 0.02, 0.05
+    S = _state(_params(nu=nu, walls=[0, 0, 0, T0, U, 0, 0, T0]), 1, ny, 1, I.uniform(1, ny, 1, T0))
+    y, L = _layers(ny), ny
+    errs = []
+    for ts in times:
+        S.step(int(round(ts * L * L / nu)) - S.t)
+        errs.append(float(np.abs(S.fields()["u"][0] / U - _series(y / L, S.t * nu / L ** 2)).max()))
+    return errs
+
+
+def pin_conduction(kr=None):
+    """steady conduction between walls at theta0 -+ eps (linear regime), from
+    straight-line fits of theta on each sublattice in the interior: the mean
+    slope against 2 eps theta0 / L, the mean value at mid-channel, the
+    difference of the two sublattices' values there, and max |theta_T -
+    theta_R| in the interior, all in units of eps theta0."""
+    ny, nu, Pr, eps = 16, 0.1, 0.71, 2e-4
+    dT = eps * T0
+    P = _params(nu=nu, Pr=Pr, walls=[0, 0, 0, T0 - dT, 0, 0, 0, T0 + dT], kr=kr)
+    S = _state(P, 1, ny, 1, I.uniform(1, ny, 1, T0))
+    L = ny
+    S.step(int(3 * L * L / (nu / Pr)))
+    F = S.fields()
+    d = P.delta
+    th = ((3 * F["T"] + d * F["R"]) / (3 + d) - T0) / dT
+    y = _layers(ny)
+    inner = (y > 3) & (y < L - 3)
+    fits = [np.polyfit(y[inner & (np.arange(2 * ny) // ny == s)],
+                       th[inner & (np.arange(2 * ny) // ny == s)], 1) for s in range(2)]
+    slope = 0.5 * (fits[0][0] + fits[1][0])
+    at = [np.polyval(p, L / 2) for p in fits]
+    TR = float(np.abs((F["T"] - F["R"])[inner]).max() / dT)
+    return slope * L / 2, 0.5 * (at[0] + at[1]), at[0] - at[1], TR
+
+
+# ---------------------------------------------------------------------------
+# tests
+
+
+def test_state_equal_to_both_walls_is_fixed():
+    assert pin_fixed_point() < 1e-13
+
+
+def test_walls_conserve_mass():
+    dm, dE = pin_mass()
+    assert dm < 1e-13
+    assert dE > 1e-6  # heated walls exchange energy
+
+
+def test_one_step_emission_matches_brute_force():
+    assert pin_emission() < 1e-15
+
+
+def test_mirror_maps_a_step_onto_the_mirrored_step():
+    assert pin_mirror() < 1e-14
+
+
+def test_startup_couette_follows_the_series_solution():
+    # bar: 2% of the plate speed (measured 1.4%, 1.0%, 0.8%: kinetic slip and the
+    # first layers' Knudsen layer at L = 16)
+    errs = pin_couette()
+    assert max(errs) < 0.02, errs
+
+
+def _conduction_ok(slope, mid, off, TR):
+    # temperature jump at the walls: the slope falls short of 2 eps/L by ~1%;
+    # the two sublattices settle ~0.01 eps theta0 apart (a discrete effect of
+    # the half-way wall, shrinking as 1/L; 0.04 and 0.07 for a ghost at the
+    # wall's mirror point or swapped wall distances)
+    return 0.97 < slope < 1.0 and abs(mid) < 2e-3 and abs(off) < 0.02 and TR < 2e-3
+
+
+def test_steady_conduction_is_linear_between_the_wall_temperatures():
+    r = pin_conduction()
+    assert _conduction_ok(*r), r
+
+
+# planted mistakes in the wall code: (name, original, mistake, pin that must fail)
+WALL_MUTANTS = [
+    ("no mass balance", "rw[k] = out[k] / in[k];", "rw[k] = 1.0;", "mass"),
+    ("destination in the wrong direction", "return floor_div2(2 * y + s + c2 - sd);",
+     "return floor_div2(2 * y + s - c2 - sd);", "mass"),
+    ("leaving flux of the other wall", "if (yd < 0) out[col] += gs[p * Q + i];",
+     "if (yd < 0) out[ncol + col] += gs[p * Q + i];", "emission"),
+    ("wall distances of the sublattices swapped",
+     "return w == 0 ? (2.0 * s + 1.0) / 4.0 : (3.0 - 2.0 * s) / 4.0;",
+     "return w == 0 ? (3.0 - 2.0 * s) / 4.0 : (2.0 * s + 1.0) / 4.0;", "conduction"),
+    ("ghost at the mirror point of the wall", "const double gv = thw + (thw - th[p]) * (1.0 - d) / d;",
+     "const double gv = thw + (thw - th[p]);", "conduction"),
+    ("wall emits at the lattice temperature", "for (a = 0; a < 9; a++) Lam[a] = (a % 4 == 0) ? wl[3] : 0.0;",
+     "for (a = 0; a < 9; a++) Lam[a] = (a % 4 == 0) ? THETA0 : 0.0;", "fixed"),
+]
+
+
+def _fails(pin):
+    if pin == "mass":
+        dm, _ = pin_mass()
+        return not dm < 1e-13
+    if pin == "emission":
+        return not pin_emission() < 1e-15
+    if pin == "fixed":
+        return not pin_fixed_point() < 1e-13
+    return not _conduction_ok(*pin_conduction())
+
+
+@pytest.mark.parametrize("name,orig,bad,pin", WALL_MUTANTS, ids=[m[0] for m in WALL_MUTANTS])
+def test_planted_wall_mistake_fails_a_pin(tmp_path, name, orig, bad, pin):
+    src = O.source()
+    assert src.count(orig) == 1, name
+    lib = O.compile_variant(src.replace(orig, bad), str(tmp_path / "mutant.so"))
+    with O.using_library(lib):
+        assert _fails(pin), name
