@@ -62,7 +62,8 @@ typedef enum {
 enum { RPK_F64 = 0, RPK_F32 = 1, RPK_F16DEV = 2, RPK_BF16DEV = 3 };
 
 /* Boundary in x: periodic, or fixed equilibrium reservoirs beyond both ends
- * (rpk_set_reservoirs). y and z are always periodic. */
+ * (rpk_set_reservoirs). y is periodic unless rpk_set_walls puts diffuse walls
+ * there; z is always periodic. */
 enum { RPK_BC_PERIODIC = 0, RPK_BC_RESERVOIR = 1 };
 
 typedef struct {
@@ -153,6 +154,29 @@ rpk_status rpk_set_reservoirs(rpk_lattice* lat, const double* states12);
  * Changing the mode discards the state (initialise again); checkpoints record
  * it. */
 rpk_status rpk_set_rot_mode(rpk_lattice* lat, int mode);
+
+/* Diffuse walls normal to y (the diffusive wall condition of Ansumali & Karlin
+ * that Sec. 6 cites for its Couette and cavity flows; the paper does not write
+ * it out, this is the library's reading). walls8 = ux, uy, uz, theta of the
+ * low-y wall, then of the high-y wall (uy must be 0: the walls slide; theta >
+ * 0); NULL makes y periodic again. The walls are the planes y = -1/4 and
+ * y = ny - 1/4 in sublattice-spacing units, half way between layers of points
+ * (which sit at y + s/2), so the channel height is ny.
+ *   Kinetic part: a population whose pull source lies beyond a wall is emitted
+ *   by the wall as rho_w f^eq(1, u_w, theta_w), the discrete Gaussian of the
+ *   wall's velocity and temperature, with rho_w per (x, z) column and wall set
+ *   so that the wall emits into the column exactly the mass that left the
+ *   column through it in the same step: mass is conserved to round-off.
+ *   Rotational energy: Dirichlet theta_R = theta_w; the diffusive flux through
+ *   the wall face of a point at distance d (1/4 or 3/4) from the wall is
+ *   kappa_R(p)(theta_w - theta_R(p))/d; no advective flux through a wall.
+ * Requires ny >= 2, bc_x = RPK_BC_PERIODIC and rotational mode 0
+ * (RPK_ERR_STATE otherwise; rpk_set_rot_mode(1) is refused while walls are
+ * on). Takes effect at the next step or moment read; the automatic nsub of
+ * rpk_init_fields accounts for the stiffer near-wall diffusion (one face with
+ * coefficient 4 kappa_R) and for the wall temperatures. Checkpoints record the
+ * walls. Synchronises the lattice's stream. */
+rpk_status rpk_set_walls(rpk_lattice* lat, const double* walls8);
 
 /* Initial state from hydrodynamic fields (layout above): rho > 0, u (3
  * planes), theta_T > 0, theta_R > 0. f = f^Eq(rho, u, theta_T I), then

@@ -125,6 +125,7 @@ def load_library(path=None):
         "rpk_set_gas": (i, [vp, d, d, d, d, d]),
         "rpk_set_reservoirs": (i, [vp, _dp]),
         "rpk_set_rot_mode": (i, [vp, i]),
+        "rpk_set_walls": (i, [vp, _dp]),
         "rpk_init_fields": (i, [vp, vp, vp, vp, vp, i]),
         "rpk_step": (i, [vp, i64]),
         "rpk_read_moments": (i, [vp, vp, vp, vp, vp, vp, i]),
@@ -292,6 +293,19 @@ class Lattice:
     def set_reservoirs(self, states12):
         s = np.ascontiguousarray(states12, dtype=np.float64).reshape(12)
         _check(load_library().rpk_set_reservoirs(self._h, s.ctypes.data_as(_dp)))
+        return self
+
+    def set_walls(self, low=None, high=None):
+        """Diffuse walls normal to y at y = -1/4 and y = ny - 1/4 (rpk_set_walls):
+        low and high are (ux, uy, uz, theta) of each wall, uy = 0; no arguments
+        makes y periodic again."""
+        if low is None and high is None:
+            _check(load_library().rpk_set_walls(self._h, None))
+            return self
+        w = np.ascontiguousarray(np.concatenate([np.ravel(low), np.ravel(high)]), dtype=np.float64)
+        if w.size != 8:
+            raise ValueError("each wall is (ux, uy, uz, theta)")
+        _check(load_library().rpk_set_walls(self._h, w.ctypes.data_as(_dp)))
         return self
 
     def set_rot_mode(self, mode):

@@ -133,12 +133,19 @@ rpk_status rpk_map_gas(double gamma, double eta, double eta_B, double kappa, dou
   return validate_relax(out);
 }
 
-int rpk_auto_nsub(const rpk_relax* r, double theta_max, int ndim) {
-  if (!r || !(r->k_r > 0.0) || ndim <= 0 || !(theta_max > 0.0)) return 1;
+// FTCS sub-steps for a diffusion number D per sub-step with `diag` times D on
+// the diagonal of the explicit update (2 ndim in the interior).
+static int nsub_for_diagonal(const rpk_relax* r, double theta_max, double diag) {
+  if (!r || !(r->k_r > 0.0) || !(diag > 0.0) || !(theta_max > 0.0)) return 1;
   const double B = 1.0 + r->tau / r->tau1;
   const double D = 5.0 * r->k_r * r->tau * (1.25 * theta_max) / (r->delta * B);
-  const double n = std::ceil(2.0 * ndim * D * r->dt / 0.9);
+  const double n = std::ceil(diag * D * r->dt / 0.9);
   return (int)std::max(1.0, std::min(n, 4096.0));
+}
+
+int rpk_auto_nsub(const rpk_relax* r, double theta_max, int ndim) {
+  if (ndim <= 0) return 1;
+  return nsub_for_diagonal(r, theta_max, 2.0 * ndim);
 }
 
 static void free_all(rpk_lattice* L) {
@@ -147,7 +154,7 @@ static void free_all(rpk_lattice* L) {
   L->events.clear();
   void* ptrs[] = {L->pop[0], L->pop[1], L->e,       L->e_star, L->e_a,    L->e_b,
                   L->vbuf,   L->thbuf,  L->drho,    L->kap,    L->u[0],   L->u[1],
-                  L->ghost,  L->status, L->diag_partial, L->diag_out, L->stage};
+                  L->ghost,  L->status, L->diag_partial, L->diag_out, L->stage, L->wrho};
   int prev = -1;
   cudaGetDevice(&prev);
   if (prev != L->device) cudaSetDevice(L->device);
@@ -190,6 +197,7 @@ rpk_status rpk_create(const rpk_grid* grid, void* cuda_stream, rpk_lattice** out
                 {&L->drho, fb}, {&L->kap, fb},
                 {&L->u[0], 3 * fb}, {&L->u[1], 3 * fb},
                 {&L->ghost, 2 * kGhostStride * L->real_elem},
+                {&L->wrho, 2 * (size_t)grid->nx * grid->nz * L->real_elem},
                 {(void**)&L->status, sizeof(unsigned)},
                 {(void**)&L->diag_partial, sizeof(double) * kDiagVals * kDiagBlocks},
                 {(void**)&L->diag_out, sizeof(double) * 16}};
@@ -206,6 +214,8 @@ rpk_status rpk_create(const rpk_grid* grid, void* cuda_stream, rpk_lattice** out
   }
   err = cudaMemsetAsync(L->status, 0, sizeof(unsigned), L->stream);
   if (err == cudaSuccess) err = cudaMemsetAsync(L->ghost, 0, 2 * kGhostStride * L->real_elem, L->stream);
+  if (err == cudaSuccess)
+    err = cudaMemsetAsync(L->wrho, 0, 2 * (size_t)grid->nx * grid->nz * L->real_elem, L->stream);
   if (err == cudaSuccess) err = cudaStreamSynchronize(L->stream);
   if (err != cudaSuccess) {
     free_all(L);
@@ -230,6 +240,11 @@ rpk_status rpk_set_relax(rpk_lattice* L, const rpk_relax* r) {
   L->relax = *r;
   L->relax_ok = true;
   if (r->nsub > 0) L->nsub = r->nsub;
+  if (L->res_ok || L->walls) {
+    // the boundary tables hold e and kappa_R, which depend on the parameters
+    RPK_CUDA(cudaSetDevice(L->device));
+    return with_ops(L->grid.precision, [&](auto ops) { return decltype(ops)::ghosts(L); });
+  }
   return RPK_OK;
 }
 
@@ -262,10 +277,31 @@ rpk_status rpk_set_reservoirs(rpk_lattice* L, const double* s) {
   return RPK_OK;
 }
 
+rpk_status rpk_set_walls(rpk_lattice* L, const double* w) {
+  if (!L) return fail(RPK_ERR_ARG, "lattice is NULL");
+  if (!w) {
+    L->walls = false;
+    return RPK_OK;
+  }
+  if (L->grid.ny < 2) return fail(RPK_ERR_STATE, "walls need ny >= 2");
+  if (L->grid.bc_x != RPK_BC_PERIODIC) return fail(RPK_ERR_STATE, "walls need a periodic x boundary");
+  if (L->rot_mode != 0) return fail(RPK_ERR_STATE, "walls need the conservative rotational form (mode 0)");
+  if (!L->relax_ok) return fail(RPK_ERR_STATE, "set the relaxation parameters first");
+  for (int k = 0; k < 8; ++k)
+    if (!std::isfinite(w[k])) return fail(RPK_ERR_PARAM, "wall state not finite");
+  if (w[1] != 0.0 || w[5] != 0.0) return fail(RPK_ERR_PARAM, "walls slide tangentially: uy must be 0");
+  if (!(w[3] > 0.0) || !(w[7] > 0.0)) return fail(RPK_ERR_PARAM, "wall temperatures must be > 0");
+  std::memcpy(L->wall, w, sizeof(L->wall));
+  L->walls = true;
+  RPK_CUDA(cudaSetDevice(L->device));
+  return with_ops(L->grid.precision, [&](auto ops) { return decltype(ops)::ghosts(L); });
+}
+
 rpk_status rpk_set_rot_mode(rpk_lattice* L, int mode) {
   if (!L) return fail(RPK_ERR_ARG, "lattice is NULL");
   if (mode != 0 && mode != 1) return fail(RPK_ERR_ARG, "mode must be 0 (conservative) or 1 (paper)");
   if (mode == L->rot_mode) return RPK_OK;
+  if (mode == 1 && L->walls) return fail(RPK_ERR_STATE, "the paper-mode solver has no wall boundary");
   L->rot_mode = mode;
   L->init_ok = false;  // the stored rotational state changes meaning: initialise again
   if (L->res_ok) {
@@ -327,9 +363,15 @@ rpk_status rpk_init_fields(rpk_lattice* L, const double* rho, const double* u,
     RPK_CUDA(cudaMemcpyAsync(part.data(), L->diag_partial, nb * sizeof(double),
                              cudaMemcpyDeviceToHost, L->stream));
     RPK_CUDA(cudaStreamSynchronize(L->stream));
-    const double tmax = *std::max_element(part.begin(), part.end());
+    double tmax = *std::max_element(part.begin(), part.end());
     if (!(tmax > 0.0) || !std::isfinite(tmax)) return fail(RPK_ERR_PARAM, "fields need theta > 0");
-    L->nsub = rpk_auto_nsub(&L->relax, tmax, active_dims(L->grid));
+    if (L->walls) {
+      // a point next to a wall has one face of coefficient 4 kappa_R (distance 1/4)
+      tmax = std::max(tmax, std::max(L->wall[3], L->wall[7]));
+      L->nsub = nsub_for_diagonal(&L->relax, tmax, 2.0 * active_dims(L->grid) + 3.0);
+    } else {
+      L->nsub = rpk_auto_nsub(&L->relax, tmax, active_dims(L->grid));
+    }
   } else {
     L->nsub = L->relax.nsub;
   }
@@ -430,7 +472,8 @@ struct CkptHeader {
   int64_t steps;
   rpk_relax relax;
   double res[12];
-  int32_t rot_mode, pad;
+  int32_t rot_mode, walls;
+  double wall[8];
 };
 }  // namespace
 
@@ -457,8 +500,10 @@ rpk_status rpk_save(rpk_lattice* L, const char* path) {
   FILE* f = fopen(path, "wb");
   if (!f) return fail(RPK_ERR_IO, std::string("cannot open ") + path);
   CkptHeader h{};
-  std::memcpy(h.magic, "RPKCKPT2", 8);
+  std::memcpy(h.magic, "RPKCKPT3", 8);
   h.rot_mode = L->rot_mode;
+  h.walls = L->walls;
+  std::memcpy(h.wall, L->wall, sizeof(h.wall));
   h.abi = RPK_ABI_VERSION;
   h.nx = L->grid.nx; h.ny = L->grid.ny; h.nz = L->grid.nz;
   h.precision = L->grid.precision; h.bc_x = L->grid.bc_x;
@@ -486,8 +531,10 @@ rpk_status rpk_load(rpk_lattice* L, const char* path) {
   if (!f) return fail(RPK_ERR_IO, std::string("cannot open ") + path);
   CkptHeader h{};
   rpk_status st = RPK_OK;
-  if (fread(&h, sizeof(h), 1, f) != 1 || std::memcmp(h.magic, "RPKCKPT2", 8) != 0)
+  if (fread(&h, sizeof(h), 1, f) != 1 || std::memcmp(h.magic, "RPKCKPT3", 8) != 0)
     st = fail(RPK_ERR_IO, "not a checkpoint");
+  else if (h.walls && (h.rot_mode != 0 || h.bc_x != RPK_BC_PERIODIC || h.ny < 2))
+    st = fail(RPK_ERR_IO, "inconsistent checkpoint");
   else if (h.rot_mode != L->rot_mode)
     st = fail(RPK_ERR_ARG, "checkpoint rotational mode differs from the lattice (rpk_set_rot_mode)");
   else if (h.nx != L->grid.nx || h.ny != L->grid.ny || h.nz != L->grid.nz ||
@@ -513,7 +560,9 @@ rpk_status rpk_load(rpk_lattice* L, const char* path) {
   L->cur = 0;
   std::memcpy(L->res, h.res, sizeof(L->res));
   L->res_ok = h.res_ok != 0;
-  if (L->res_ok) {
+  L->walls = h.walls != 0;
+  std::memcpy(L->wall, h.wall, sizeof(L->wall));
+  if (L->res_ok || L->walls) {
     st = with_ops(L->grid.precision, [&](auto ops) { return decltype(ops)::ghosts(L); });
     if (st != RPK_OK) return st;
   }

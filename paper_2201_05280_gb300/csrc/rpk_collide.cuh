@@ -64,12 +64,12 @@ __global__ void __launch_bounds__(128, sizeof(Real) == 4 ? 5 : 1)
               const Real* __restrict__ e_in, Real* __restrict__ e_out, Real* __restrict__ drho_out,
               Real* __restrict__ u_out, Real* __restrict__ kap_out,
               const Real* __restrict__ ghost, unsigned* __restrict__ status,
-              Real* __restrict__ tt_out) {
+              Real* __restrict__ tt_out, const Real* __restrict__ wcol) {
   PointIdx P;
   if (!point_from_block(K, P)) return;
   const int64_t p = (int64_t)P.s * K.n3 + P.cell;
   Real h[kQ];
-  gather<Store, Real, kPull, kBC>(pin, ghost, K, P, h);
+  gather<Store, Real, kPull, kBC>(pin, ghost, K, P, h, wcol);
   Mom<Real> m;
   const Real es = collide_point<Store, Real, kPaper>(K, h, e_in[p],
                                              pout + (int64_t)(P.s * kQ) * K.n3 + P.cell, m);

@@ -88,7 +88,8 @@ struct StepConst {
   Real inv_1pa;   // 1 / (1 + a)
 };
 
-// Ghost (reservoir) values, one block of kGhostStride per x end.
+// Ghost values, one block of kGhostStride per x end (reservoirs) or per y wall
+// (walls: h of f^eq(1, u_w, theta_w), its e, rho - 1 = 0, u_w, kappa_R).
 constexpr int kGhostStride = 48;
 enum { kGhE = 41, kGhDrho = 42, kGhU = 43, kGhKap = 46 };
 
@@ -308,10 +309,15 @@ __device__ __forceinline__ bool point_from_block(const StepConst<Real>& K, Point
 // from sublattice 0 at index x comes from sublattice 1 at x - (c > 0 ? 1 : 0)
 // per axis, and from sublattice 1 it comes from sublattice 0 at
 // x + (c < 0 ? 1 : 0)). kBC = 1: sources beyond the x ends read the reservoir.
+// kBC = 2: sources beyond a y wall (y = -1/4, y = ny - 1/4) are emitted by the
+// wall, g = rho_w f^eq(1, u_w, theta_w), i.e. h = d + hw + d hw with
+// d = rho_w - 1 of the point's (x, z) column (wcol[(wall * nz + z) * nx + x])
+// and hw the wall's table entry.
 template <typename Store, typename Real, bool kPull, int kBC>
 __device__ __forceinline__ void gather(const Store* __restrict__ pin,
                                        const Real* __restrict__ ghost, const StepConst<Real>& K,
-                                       const PointIdx& P, Real (&h)[kQ]) {
+                                       const PointIdx& P, Real (&h)[kQ],
+                                       const Real* __restrict__ wcol = nullptr) {
   const int64_t n3 = K.n3;
   if constexpr (!kPull) {
     const Store* base = pin + (int64_t)(P.s * kQ) * n3 + P.cell;
@@ -320,13 +326,14 @@ __device__ __forceinline__ void gather(const Store* __restrict__ pin,
   } else {
     const int nx = K.nx, ny = K.ny, nz = K.nz;
     int xw[5], yw[5], zw[5];
-    bool xin[5];
+    bool xin[5], yin[5];
 #pragma unroll
     for (int k = 0; k < 5; ++k) {
       xw[k] = wrap_near(P.x + k - 2, nx);
       yw[k] = wrap_near(P.y + k - 2, ny);
       zw[k] = wrap_near(P.z + k - 2, nz);
       xin[k] = (P.x + k - 2 >= 0) && (P.x + k - 2 < nx);
+      yin[k] = (P.y + k - 2 >= 0) && (P.y + k - 2 < ny);
     }
     // half-velocity source offsets: c > 0 -> s - 1, c < 0 -> s
     const int s = P.s;
@@ -334,6 +341,7 @@ __device__ __forceinline__ void gather(const Store* __restrict__ pin,
     const int yhp = s ? yw[2] : yw[1], yhm = s ? yw[3] : yw[2];
     const int zhp = s ? zw[2] : zw[1], zhm = s ? zw[3] : zw[2];
     const bool xinhp = s ? xin[2] : xin[1], xinhm = s ? xin[3] : xin[2];
+    const bool yinhp = s ? yin[2] : yin[1], yinhm = s ? yin[3] : yin[2];
     const Store* same = pin + (int64_t)(s * kQ) * n3;
     const Store* other = pin + (int64_t)((1 - s) * kQ) * n3;
     h[0] = to_real<Store, Real>(same[P.cell]);
@@ -349,12 +357,14 @@ __device__ __forceinline__ void gather(const Store* __restrict__ pin,
         ys = v.y > 0 ? yhp : yhm;
         zs = v.z > 0 ? zhp : zhm;
         if constexpr (kBC == 1) inside = v.x > 0 ? xinhp : xinhm;
+        if constexpr (kBC == 2) inside = v.y > 0 ? yinhp : yinhm;
         base = other;
       } else {
         xs = xw[2 - v.x / 2];
         ys = yw[2 - v.y / 2];
         zs = zw[2 - v.z / 2];
         if constexpr (kBC == 1) inside = xin[2 - v.x / 2];
+        if constexpr (kBC == 2) inside = yin[2 - v.y / 2];
         base = same;
       }
       const int64_t cell = ((int64_t)zs * ny + ys) * nx + xs;
@@ -364,9 +374,65 @@ __device__ __forceinline__ void gather(const Store* __restrict__ pin,
           return;
         }
       }
+      if constexpr (kBC == 2 && v.y != 0) {
+        if (!inside) {
+          const int w = v.y > 0 ? 0 : 1;  // source below the low wall / above the high wall
+          const Real d = wcol[((int64_t)w * nz + P.z) * nx + P.x];
+          const Real hw = ghost[w * kGhostStride + q];
+          h[q] = d + hw + d * hw;
+          return;
+        }
+      }
       h[q] = to_real<Store, Real>(base[(int64_t)q * n3 + cell]);
     });
   }
+}
+
+// rho_w - 1 of every (x, z) column at both y walls, from the post-collision
+// populations pin that the next pull reads: the column's populations whose
+// destination lies beyond the wall (the |2 c_y| layers next to it, for each
+// velocity pointing at the wall) carry the mass M_out = sum w (1 + h); the wall
+// emits rho_w f^eq(1, u_w, theta_w) into |2 c_y| entries of the column for each
+// velocity pointing away from it, mass rho_w D with D = sum |2 c_y| w (1 + hw).
+// rho_w - 1 = (A + sum w h) / D, A = sum |2 c_y| w - D = -sum |2 c_y| w hw (the
+// weights of c and -c are equal), so that the deviation keeps its precision.
+// One thread per (column, wall); wcol[(wall * nz + z) * nx + x].
+template <typename Store, typename Real>
+__global__ void __launch_bounds__(128)
+    k_wall_rho(StepConst<Real> K, const Store* __restrict__ pin, const Real* __restrict__ ghost,
+               Real* __restrict__ wcol) {
+  const int64_t ncol = (int64_t)K.nx * K.nz;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 2 * ncol) return;
+  const int w = t >= ncol ? 1 : 0;
+  const int64_t c = t - w * ncol;
+  const int x = (int)(c % K.nx), z = (int)(c / K.nx);
+  const int ny = K.ny;
+  const int64_t n3 = K.n3;
+  const Real* hw = ghost + w * kGhostStride;
+  Real D = Real(0), A = Real(0), S = Real(0);
+  static_for<kQ - 1>([&](auto qc) {
+    constexpr int q = decltype(qc)::value + 1;
+    constexpr Vel2 v = vel2(q);
+    if constexpr (v.y != 0) {
+      constexpr int n = v.y > 0 ? v.y : -v.y;
+      const Real wq = Real(weight(q));
+      if ((w == 0) == (v.y > 0)) {
+        // emitted by this wall
+        D += Real(n) * wq * (Real(1) + hw[q]);
+        A -= Real(n) * wq * hw[q];
+      } else {
+        // leaving through this wall: layers 2y + s = 0 .. n-1 (low) or 2ny-1 .. 2ny-n (high)
+#pragma unroll
+        for (int k = 0; k < n; ++k) {
+          const int Y2 = w == 0 ? k : 2 * ny - 1 - k;
+          const int s = Y2 & 1, y = Y2 >> 1;
+          S += wq * to_real<Store, Real>(pin[(int64_t)(s * kQ + q) * n3 + ((int64_t)z * ny + y) * K.nx + x]);
+        }
+      }
+    }
+  });
+  wcol[t] = (A + S) / D;
 }
 
 }  // namespace rpk

@@ -24,7 +24,7 @@ __device__ __forceinline__ bool point_from_block2d(const StepConst<Real>& K, Poi
 }
 
 // Axis neighbour on the same sublattice, or -1 / -2 for the low / high x
-// reservoir when kBC == 1.
+// reservoir when kBC == 1, or -3 / -4 for the low / high y wall when kBC == 2.
 template <int kBC, typename Real>
 __device__ __forceinline__ int64_t axis_nb(const StepConst<Real>& K, const PointIdx& P, int axis,
                                            int d) {
@@ -37,11 +37,36 @@ __device__ __forceinline__ int64_t axis_nb(const StepConst<Real>& K, const Point
     }
     x = wrap_near(x, K.nx);
   } else if (axis == 1) {
-    y = wrap_near(y + d, K.ny);
+    y += d;
+    if (kBC == 2) {
+      if (y < 0) return -3;
+      if (y >= K.ny) return -4;
+    }
+    y = wrap_near(y, K.ny);
   } else {
     z = wrap_near(z + d, K.nz);
   }
   return (int64_t)P.s * K.n3 + ((int64_t)z * K.ny + y) * K.nx + x;
+}
+
+// Ghost block of a negative axis_nb result: low end / low wall first.
+template <typename Real>
+__device__ __forceinline__ const Real* ghost_block(const Real* __restrict__ ghost, int64_t q) {
+  return ghost + ((q == -1 || q == -3) ? 0 : kGhostStride);
+}
+
+// Wall ghost of theta_R - theta0 for the diffusion: the face flux to the wall
+// is kappa_R(p)(theta_w - theta_R(p))/d, d the distance from the point to the
+// wall (1/4 for sublattice 0 at the low wall and sublattice 1 at the high
+// wall, 3/4 otherwise), written as the value theta_w + (theta_w - theta_p)(1 - d)/d
+// on the axis neighbour (whose face coefficient is then kappa_R(p)).
+template <typename Real>
+__device__ __forceinline__ Real wall_theta(const StepConst<Real>& K, const Real* __restrict__ g,
+                                           int64_t q, int s, Real thp) {
+  const Real thw = (Real(2) * g[kGhE] - K.delta * K.theta0 * g[kGhDrho]) /
+                   (K.delta * (Real(1) + g[kGhDrho]));
+  const Real r = ((q == -3) == (s == 0)) ? Real(3) : Real(1.0 / 3.0);
+  return thw + (thw - thp) * r;
 }
 
 // advecting velocity: second-order extrapolation to t + dt/2
@@ -74,9 +99,12 @@ __global__ void __launch_bounds__(128)
       const int64_t q = axis_nb<kBC>(K, P, a, d);
       Real thq, kq;
       if (kBC == 1 && q < 0) {
-        const Real* g = ghost + (q == -1 ? 0 : kGhostStride);
+        const Real* g = ghost_block(ghost, q);
         thq = dthR(g[kGhE], g[kGhDrho]);
         kq = g[kGhKap];
+      } else if (kBC == 2 && q < 0) {
+        thq = wall_theta(K, ghost_block(ghost, q), q, P.s, th);
+        kq = kp;
       } else {
         thq = dthR(e[q], drho[q]);
         kq = kap[q];
@@ -114,8 +142,8 @@ __global__ void __launch_bounds__(kTBX * kTBY)
     v[a * npts + p] = vp;
     const int64_t q = axis_nb<kBC>(K, P, a, +1);
     Real eq, vq;
-    if (kBC == 1 && q < 0) {
-      const Real* g = ghost + (q == -1 ? 0 : kGhostStride);
+    if (kBC != 0 && q < 0) {
+      const Real* g = ghost_block(ghost, q);  // a wall has zero normal velocity: no flux
       eq = g[kGhE];
       vq = g[kGhU + a];
     } else {
@@ -143,8 +171,8 @@ __global__ void __launch_bounds__(kTBX * kTBY)
     const Real vp = v[a * npts + p];
     const int64_t q = axis_nb<kBC>(K, P, a, -1);
     Real eq, vq;
-    if (kBC == 1 && q < 0) {
-      const Real* g = ghost + (q == -1 ? 0 : kGhostStride);
+    if (kBC != 0 && q < 0) {
+      const Real* g = ghost_block(ghost, q);  // a wall has zero normal velocity: no flux
       eq = g[kGhE];
       vq = g[kGhU + a];
     } else {
@@ -178,9 +206,12 @@ __global__ void __launch_bounds__(kTBX * kTBY)
       const int64_t q = axis_nb<kBC>(K, P, a, d);
       Real thq, kq;
       if (kBC == 1 && q < 0) {
-        const Real* g = ghost + (q == -1 ? 0 : kGhostStride);
+        const Real* g = ghost_block(ghost, q);
         thq = (Real(2) * g[kGhE] - t0d * g[kGhDrho]) / (K.delta * (Real(1) + g[kGhDrho]));
         kq = g[kGhKap];
+      } else if (kBC == 2 && q < 0) {
+        thq = wall_theta(K, ghost_block(ghost, q), q, P.s, thp);
+        kq = kp;
       } else {
         thq = th[q];
         kq = kap[q];
@@ -203,6 +234,7 @@ __global__ void __launch_bounds__(kTBX * kTBY)
 template <typename Real, int kBC>
 __device__ __forceinline__ Real pm_nb(const StepConst<Real>& K, const PointIdx& P, const Real* __restrict__ r,
                                       const Real* __restrict__ ghost, int a, int d) {
+  static_assert(kBC != 2, "the paper-mode solver has no wall boundary");
   const int64_t q = axis_nb<kBC>(K, P, a, d);
   if (kBC == 1 && q < 0) return ghost[(q == -1 ? 0 : kGhostStride) + kGhE];
   return r[q];
@@ -343,13 +375,14 @@ template <typename Store, typename Real, bool kPull, int kBC>
 __global__ void __launch_bounds__(128)
     k_moments(StepConst<Real> K, const Store* __restrict__ pin, const Real* __restrict__ e_in,
               const Real* __restrict__ ghost, double* __restrict__ rho_o, double* __restrict__ u_o,
-              double* __restrict__ T_o, double* __restrict__ R_o, double* __restrict__ E_o) {
+              double* __restrict__ T_o, double* __restrict__ R_o, double* __restrict__ E_o,
+              const Real* __restrict__ wcol) {
   PointIdx P;
   if (!point_from_block(K, P)) return;
   const int64_t npts = 2 * K.n3;
   const int64_t p = (int64_t)P.s * K.n3 + P.cell;
   Real h[kQ];
-  gather<Store, Real, kPull, kBC>(pin, ghost, K, P, h);
+  gather<Store, Real, kPull, kBC>(pin, ghost, K, P, h, wcol);
   Mom<Real> m;
   raw_moments(h, m);
   if (K.paper)
@@ -386,7 +419,8 @@ __device__ __forceinline__ double warp_min(double v) {
 template <typename Store, typename Real, bool kPull, int kBC>
 __global__ void __launch_bounds__(kDiagThreads)
     k_diag(StepConst<Real> K, const Store* __restrict__ pin, const Real* __restrict__ e_in,
-           const Real* __restrict__ ghost, double* __restrict__ partial) {
+           const Real* __restrict__ ghost, double* __restrict__ partial,
+           const Real* __restrict__ wcol) {
   double acc[kDiagVals - 1] = {0, 0, 0, 0, 0, 0, INFINITY};
   const int64_t npts = 2 * K.n3;
   const double t0 = (double)K.theta0;
@@ -399,7 +433,7 @@ __global__ void __launch_bounds__(kDiagThreads)
     P.y = (int)((P.cell / K.nx) % K.ny);
     P.z = (int)(P.cell / ((int64_t)K.nx * K.ny));
     Real h[kQ];
-    gather<Store, Real, kPull, kBC>(pin, ghost, K, P, h);
+    gather<Store, Real, kPull, kBC>(pin, ghost, K, P, h, wcol);
     // conserved sums in FP64 from the stored values
     double dm = kWeightRest * (double)h[0], jx = 0, jy = 0, jz = 0, ek = 0;
     double gmin = kWeightRest * (1.0 + (double)h[0]);

@@ -64,21 +64,36 @@ static inline rpk_status check_launch(const char* what) {
   return RPK_OK;
 }
 
+// rho_w - 1 of every column at both walls from the current (post-collision)
+// populations; precedes every pull when the walls are on.
+template <typename Store, typename Real>
+static rpk_status wall_launch(rpk_lattice* L, const StepConst<Real>& K) {
+  const int64_t n = 2 * (int64_t)L->grid.nx * L->grid.nz;
+  k_wall_rho<Store, Real><<<(unsigned)((n + 127) / 128), 128, 0, L->stream>>>(
+      K, static_cast<const Store*>(L->pop[L->cur]), static_cast<const Real*>(L->ghost),
+      static_cast<Real*>(L->wrho));
+  return check_launch("k_wall_rho");
+}
+
 template <typename Store, typename Real, bool kPull, int kBC>
 static rpk_status collide_launch(rpk_lattice* L, const StepConst<Real>& K) {
   const Store* pin = static_cast<const Store*>(L->pop[L->cur]);
   Store* pout = static_cast<Store*>(L->pop[L->cur ^ 1]);
   Real* ucur = static_cast<Real*>(L->u[L->steps & 1]);
-  if (L->rot_mode)
-    k_collide<Store, Real, kPull, kBC, true><<<point_grid(L, 128), 128, 0, L->stream>>>(
-        K, pin, pout, static_cast<const Real*>(L->e), static_cast<Real*>(L->e_star),
-        static_cast<Real*>(L->drho), ucur, static_cast<Real*>(L->kap),
-        static_cast<const Real*>(L->ghost), L->status, static_cast<Real*>(L->thbuf));
-  else
-    k_collide<Store, Real, kPull, kBC, false><<<point_grid(L, 128), 128, 0, L->stream>>>(
-        K, pin, pout, static_cast<const Real*>(L->e), static_cast<Real*>(L->e_star),
-        static_cast<Real*>(L->drho), ucur, static_cast<Real*>(L->kap),
-        static_cast<const Real*>(L->ghost), L->status, nullptr);
+  const Real* wcol = static_cast<const Real*>(L->wrho);
+  if constexpr (kBC != 2) {
+    if (L->rot_mode) {
+      k_collide<Store, Real, kPull, kBC, true><<<point_grid(L, 128), 128, 0, L->stream>>>(
+          K, pin, pout, static_cast<const Real*>(L->e), static_cast<Real*>(L->e_star),
+          static_cast<Real*>(L->drho), ucur, static_cast<Real*>(L->kap),
+          static_cast<const Real*>(L->ghost), L->status, static_cast<Real*>(L->thbuf), wcol);
+      return check_launch("k_collide");
+    }
+  }
+  k_collide<Store, Real, kPull, kBC, false><<<point_grid(L, 128), 128, 0, L->stream>>>(
+      K, pin, pout, static_cast<const Real*>(L->e), static_cast<Real*>(L->e_star),
+      static_cast<Real*>(L->drho), ucur, static_cast<Real*>(L->kap),
+      static_cast<const Real*>(L->ghost), L->status, nullptr, wcol);
   return check_launch("k_collide");
 }
 
@@ -100,20 +115,22 @@ static rpk_status transport_launch(rpk_lattice* L, const StepConst<Real>& K) {
   const dim3 tgrid((unsigned)((L->grid.nx + kTBX - 1) / kTBX),
                    (unsigned)((L->grid.ny + kTBY - 1) / kTBY), (unsigned)(2 * L->grid.nz));
   RPK_CUDA(timing_begin(L));
-  if (L->rot_mode) {
-    // paper mode: MacCormack on theta_R, FTCS sub-steps, the last with the
-    // second relaxation half step (th holds the time-t theta_T)
-    k_pm_pred<Real, kBC><<<tgrid, tb, 0, L->stream>>>(K, es, ucur, ea, gh);
-    k_pm_corr<Real, kBC><<<tgrid, tb, 0, L->stream>>>(K, es, ea, ucur, eb, gh);
-    const Real* src = eb;
-    for (int k = 0; k < L->nsub; ++k) {
-      Real* dst = (k == L->nsub - 1) ? e : (src == eb ? ea : eb);
-      k_pm_ftcs<Real, kBC><<<tgrid, tb, 0, L->stream>>>(K, src, drho, kap, th, dst, gh,
-                                                         k == L->nsub - 1);
-      src = dst;
+  if constexpr (kBC != 2) {
+    if (L->rot_mode) {
+      // paper mode: MacCormack on theta_R, FTCS sub-steps, the last with the
+      // second relaxation half step (th holds the time-t theta_T)
+      k_pm_pred<Real, kBC><<<tgrid, tb, 0, L->stream>>>(K, es, ucur, ea, gh);
+      k_pm_corr<Real, kBC><<<tgrid, tb, 0, L->stream>>>(K, es, ea, ucur, eb, gh);
+      const Real* src = eb;
+      for (int k = 0; k < L->nsub; ++k) {
+        Real* dst = (k == L->nsub - 1) ? e : (src == eb ? ea : eb);
+        k_pm_ftcs<Real, kBC><<<tgrid, tb, 0, L->stream>>>(K, src, drho, kap, th, dst, gh,
+                                                           k == L->nsub - 1);
+        src = dst;
+      }
+      RPK_CUDA(timing_end(L, RPK_KC_TRANSPORT, 2 + L->nsub));
+      return check_launch("rotational transport (paper mode)");
     }
-    RPK_CUDA(timing_end(L, RPK_KC_TRANSPORT, 2 + L->nsub));
-    return check_launch("rotational transport (paper mode)");
   }
   k_mac_pred<Real, kBC><<<tgrid, tb, 0, L->stream>>>(K, es, ucur, uprev, ea, v, gh);
   k_mac_corr<Real, kBC><<<tgrid, tb, 0, L->stream>>>(K, es, ea, v, drho, eb, th, gh);
@@ -134,16 +151,25 @@ template <typename Store, typename Real>
 rpk_status Ops<Store, Real>::step(rpk_lattice* L, int64_t n) {
   const StepConst<Real> K = make_const<Real>(L);
   const bool res = L->grid.bc_x == RPK_BC_RESERVOIR;
+  const bool walls = L->walls;
   for (int64_t t = 0; t < n; ++t) {
     rpk_status st;
     RPK_CUDA(timing_begin(L));
+    const bool wall_pull = walls && !L->streamed;
+    if (wall_pull) {
+      st = wall_launch<Store, Real>(L, K);
+      if (st != RPK_OK) return st;
+    }
     if (L->streamed)
       st = res ? collide_launch<Store, Real, false, 1>(L, K) : collide_launch<Store, Real, false, 0>(L, K);
+    else if (walls)
+      st = collide_launch<Store, Real, true, 2>(L, K);
     else
       st = res ? collide_launch<Store, Real, true, 1>(L, K) : collide_launch<Store, Real, true, 0>(L, K);
     if (st != RPK_OK) return st;
-    RPK_CUDA(timing_end(L, RPK_KC_COLLIDE, 1));
-    st = res ? transport_launch<Real, 1>(L, K) : transport_launch<Real, 0>(L, K);
+    RPK_CUDA(timing_end(L, RPK_KC_COLLIDE, wall_pull ? 2 : 1));
+    st = walls ? transport_launch<Real, 2>(L, K)
+               : (res ? transport_launch<Real, 1>(L, K) : transport_launch<Real, 0>(L, K));
     if (st != RPK_OK) return st;
     L->cur ^= 1;
     L->streamed = false;
@@ -169,7 +195,18 @@ rpk_status Ops<Store, Real>::ghosts(rpk_lattice* L) {
   const StepConst<Real> K = make_const<Real>(L);
   const Real hdt = Real(0.5 * L->relax.dt / L->relax.tau1);
   double* dst = L->diag_out;  // 12 doubles of staging (diag_out holds 16)
-  RPK_CUDA(cudaMemcpyAsync(dst, L->res, 12 * sizeof(double), cudaMemcpyHostToDevice, L->stream));
+  // reservoirs: their states; walls: rho = 1 at the wall's velocity, theta_T = theta_R = theta_w
+  double st12[12];
+  if (L->walls) {
+    for (int w = 0; w < 2; ++w) {
+      const double* wl = L->wall + 4 * w;
+      const double s6[6] = {1.0, wl[0], wl[1], wl[2], wl[3], wl[3]};
+      for (int k = 0; k < 6; ++k) st12[6 * w + k] = s6[k];
+    }
+  } else {
+    for (int k = 0; k < 12; ++k) st12[k] = L->res[k];
+  }
+  RPK_CUDA(cudaMemcpyAsync(dst, st12, 12 * sizeof(double), cudaMemcpyHostToDevice, L->stream));
   k_ghost<Real><<<1, 32, 0, L->stream>>>(K, hdt, dst, static_cast<Real*>(L->ghost));
   rpk_status st = check_launch("k_ghost");
   if (st != RPK_OK) return st;
@@ -184,14 +221,20 @@ rpk_status Ops<Store, Real>::moments(rpk_lattice* L, double* rho, double* u, dou
   const Store* pin = static_cast<const Store*>(L->pop[L->cur]);
   const Real* e = static_cast<const Real*>(L->e);
   const Real* gh = static_cast<const Real*>(L->ghost);
+  const Real* wcol = static_cast<const Real*>(L->wrho);
   const dim3 grid = point_grid(L, 128);
   const bool res = L->grid.bc_x == RPK_BC_RESERVOIR;
-  if (L->streamed)
-    k_moments<Store, Real, false, 0><<<grid, 128, 0, L->stream>>>(K, pin, e, gh, rho, u, T, R, E);
-  else if (res)
-    k_moments<Store, Real, true, 1><<<grid, 128, 0, L->stream>>>(K, pin, e, gh, rho, u, T, R, E);
-  else
-    k_moments<Store, Real, true, 0><<<grid, 128, 0, L->stream>>>(K, pin, e, gh, rho, u, T, R, E);
+  if (L->streamed) {
+    k_moments<Store, Real, false, 0><<<grid, 128, 0, L->stream>>>(K, pin, e, gh, rho, u, T, R, E, wcol);
+  } else if (L->walls) {
+    rpk_status st = wall_launch<Store, Real>(L, K);
+    if (st != RPK_OK) return st;
+    k_moments<Store, Real, true, 2><<<grid, 128, 0, L->stream>>>(K, pin, e, gh, rho, u, T, R, E, wcol);
+  } else if (res) {
+    k_moments<Store, Real, true, 1><<<grid, 128, 0, L->stream>>>(K, pin, e, gh, rho, u, T, R, E, wcol);
+  } else {
+    k_moments<Store, Real, true, 0><<<grid, 128, 0, L->stream>>>(K, pin, e, gh, rho, u, T, R, E, wcol);
+  }
   return check_launch("k_moments");
 }
 
@@ -203,13 +246,19 @@ rpk_status Ops<Store, Real>::diag(rpk_lattice* L, double out[8]) {
   const Real* gh = static_cast<const Real*>(L->ghost);
   const int64_t need = (L->npts + kDiagThreads - 1) / kDiagThreads;
   const int nblk = (int)std::max<int64_t>(1, std::min<int64_t>(kDiagBlocks, need));
+  const Real* wcol = static_cast<const Real*>(L->wrho);
   const bool res = L->grid.bc_x == RPK_BC_RESERVOIR;
-  if (L->streamed)
-    k_diag<Store, Real, false, 0><<<nblk, kDiagThreads, 0, L->stream>>>(K, pin, e, gh, L->diag_partial);
-  else if (res)
-    k_diag<Store, Real, true, 1><<<nblk, kDiagThreads, 0, L->stream>>>(K, pin, e, gh, L->diag_partial);
-  else
-    k_diag<Store, Real, true, 0><<<nblk, kDiagThreads, 0, L->stream>>>(K, pin, e, gh, L->diag_partial);
+  if (L->streamed) {
+    k_diag<Store, Real, false, 0><<<nblk, kDiagThreads, 0, L->stream>>>(K, pin, e, gh, L->diag_partial, wcol);
+  } else if (L->walls) {
+    rpk_status sw = wall_launch<Store, Real>(L, K);
+    if (sw != RPK_OK) return sw;
+    k_diag<Store, Real, true, 2><<<nblk, kDiagThreads, 0, L->stream>>>(K, pin, e, gh, L->diag_partial, wcol);
+  } else if (res) {
+    k_diag<Store, Real, true, 1><<<nblk, kDiagThreads, 0, L->stream>>>(K, pin, e, gh, L->diag_partial, wcol);
+  } else {
+    k_diag<Store, Real, true, 0><<<nblk, kDiagThreads, 0, L->stream>>>(K, pin, e, gh, L->diag_partial, wcol);
+  }
   rpk_status st = check_launch("k_diag");
   if (st != RPK_OK) return st;
   k_diag_final<<<1, 1024, 0, L->stream>>>(L->diag_partial, nblk, L->diag_out);
