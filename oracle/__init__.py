@@ -51,7 +51,7 @@ class Params(ctypes.Structure):
                 ("kr", ctypes.c_double), ("dt", ctypes.c_double),
                 ("nsub", ctypes.c_int), ("bcx", ctypes.c_int), ("diff", ctypes.c_int),
                 ("rot_mode", ctypes.c_int), ("bcy", ctypes.c_int),
-                ("wall", ctypes.c_double * 8)]
+                ("wall", ctypes.c_double * 8), ("xwall", ctypes.c_double * 8)]
 
     def __repr__(self):
         return ("Params(delta=%g, tau=%g, tau1=%g, b=%g, kr=%g, dt=%g, nsub=%d, bcx=%d, diff=%d, "
@@ -161,13 +161,14 @@ def target(rho, u, Lam):
 
 
 def make_params(delta, tau, tau1, b=0.0, kr=0.0, dt=1.0, nsub=1, bcx=0, diff=0, rot_mode=0,
-                walls=None):
+                walls=None, xwalls=None):
     """diff = 0: FTCS sub-steps of the rotational diffusion (Sec. 5); 1: one
     backward-Euler step per sublattice line (variant for quasi-1-D tubes).
     rot_mode = 0: conservative form on the auxiliary energy Er; 1: the paper's
     four-step theta_R solver (Sec. 5), the state then holds theta_R.
     walls: None (periodic in y) or 8 numbers, ux, uy, uz, theta of the low-y
-    and then of the high-y diffuse wall (uy must be 0)."""
+    and then of the high-y diffuse wall (uy must be 0). xwalls: the same for
+    diffuse walls normal to x (ux must be 0; sets bcx = 2)."""
     P = Params(float(delta), float(tau), float(tau1), float(b), float(kr), float(dt),
                int(nsub), int(bcx), int(diff), int(rot_mode), 0)
     if walls is not None:
@@ -175,6 +176,11 @@ def make_params(delta, tau, tau1, b=0.0, kr=0.0, dt=1.0, nsub=1, bcx=0, diff=0, 
         P.bcy = 1
         for k in range(8):
             P.wall[k] = float(w[k])
+    if xwalls is not None:
+        w = np.asarray(xwalls, dtype=np.float64).reshape(8)
+        P.bcx = 2
+        for k in range(8):
+            P.xwall[k] = float(w[k])
     return P
 
 
@@ -250,8 +256,9 @@ class State:
                               _ptr(self.g), _ptr(self.Er), _ptr(self.uprev), int(n))
         if rc == 2:
             raise ValueError("unsupported setting: the backward-Euler diffusion variant needs "
-                             "ny = nz = 1 and bcx = 1; y walls need ny >= 2, zero normal wall "
-                             "velocity, periodic x and the conservative rotational form")
+                             "ny = nz = 1 and bcx = 1; walls need at least 2 cells across, "
+                             "zero normal wall velocity, no x reservoirs and the conservative "
+                             "rotational form")
         if rc != 0:
             raise MemoryError("oracle step could not allocate its work arrays")
         self.t += int(n)

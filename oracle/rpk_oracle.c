@@ -62,7 +62,8 @@ typedef struct {
     double kr;    /* kappa_R / kappa_T (Sec. 4, conductivity paragraph) */
     double dt;    /* time step (1 in lattice units) */
     int nsub;     /* FTCS sub-steps of the rotational diffusion per time step */
-    int bcx;      /* 0: periodic in x; 1: fixed reservoirs beyond both x ends */
+    int bcx;      /* 0: periodic in x; 1: fixed reservoirs beyond both x ends; 2: diffuse
+                     walls normal to x (xwall) */
     int diff;     /* rotational diffusion: 0 FTCS sub-steps (Sec. 5); 1 one backward-Euler
                      step (variant for quasi-1-D tubes: ny = nz = 1, bcx = 1) */
     int rot_mode; /* 0: conservative form, the state holds Er (auxiliary energy density);
@@ -70,6 +71,7 @@ typedef struct {
     int bcy;      /* 0: periodic in y; 1: diffuse walls normal to y (Sec. 6, startup and
                      thermal Couette flows), see wall_fluxes below */
     double wall[8]; /* bcy = 1: ux, uy, uz, theta of the low-y wall, then of the high-y wall */
+    double xwall[8]; /* bcx = 2: ux, uy, uz, theta of the low-x wall, then of the high-x wall */
 } ora_params;
 
 static void put(int i, double cx, double cy, double cz, double w)
@@ -403,8 +405,9 @@ static int floor_div2(int a) { return (a >= 0) ? a / 2 : -((1 - a) / 2); }
  * sublattice s' is the parity of 2*idx + s - 2c (the same on all axes, since a
  * velocity is either all-integer or all-half-integer) and its index is
  * (2*idx + s - 2c - s')/2. Returns the point index, or -1 / -2 when the source
- * lies beyond the low / high x end (only with bcx = 1), or -3 / -4 when it lies
- * beyond the low / high y wall (only with bcy = 1).
+ * lies beyond the low / high x end (only with bcx = 1), -3 / -4 when it lies
+ * beyond the low / high y wall (bcy = 1; also when it lies beyond an x wall as
+ * well), -5 / -6 beyond the low / high x wall (bcx = 2).
  */
 static long pull_source(const ora_params *P, const grid *G, int s, int x, int y, int z, int i)
 {
@@ -414,15 +417,18 @@ static long pull_source(const ora_params *P, const grid *G, int s, int x, int y,
         int pos2 = 2 * idx[a] + s - (int)lround(2.0 * C[i][a]);
         src[a] = floor_div2(pos2 - sp);
     }
+    if (P->bcy == 1) { /* checked first: a y wall emits what comes from beyond it and an x wall */
+        if (src[1] < 0) return -3;
+        if (src[1] >= n[1]) return -4;
+    }
     if (P->bcx == 1) {
         if (src[0] < 0) return -1;
         if (src[0] >= n[0]) return -2;
+    } else if (P->bcx == 2) {
+        if (src[0] < 0) return -5;
+        if (src[0] >= n[0]) return -6;
     } else {
         src[0] = wrap(src[0], n[0]);
-    }
-    if (P->bcy == 1) {
-        if (src[1] < 0) return -3;
-        if (src[1] >= n[1]) return -4;
     }
     src[1] = wrap(src[1], n[1]);
     src[2] = wrap(src[2], n[2]);
@@ -430,8 +436,9 @@ static long pull_source(const ora_params *P, const grid *G, int s, int x, int y,
 }
 
 /* Axis neighbour on the same sublattice: d = +1 or -1 along axis a. Returns -1
- * / -2 for a reservoir ghost beyond the low / high x end (bcx = 1 only) and
- * -3 / -4 for the low / high y wall (bcy = 1 only). */
+ * / -2 for a reservoir ghost beyond the low / high x end (bcx = 1 only),
+ * -3 / -4 for the low / high y wall (bcy = 1 only) and -5 / -6 for the low /
+ * high x wall (bcx = 2 only). */
 static long axis_nb(const ora_params *P, const grid *G, long p, int a, int d)
 {
     int x = (int)(p % G->nx);
@@ -443,6 +450,10 @@ static long axis_nb(const ora_params *P, const grid *G, long p, int a, int d)
     if (a == 0 && P->bcx == 1) {
         if (idx[0] < 0) return -1;
         if (idx[0] >= n[0]) return -2;
+    }
+    if (a == 0 && P->bcx == 2) {
+        if (idx[0] < 0) return -5;
+        if (idx[0] >= n[0]) return -6;
     }
     if (a == 1 && P->bcy == 1) {
         if (idx[1] < 0) return -3;
@@ -492,6 +503,9 @@ static void make_ghost(const ora_params *P, const double *st, ghost *gh)
  *         / (sum of f^eq_i(1, u_w, theta_w) over the column's entries that
  *            the wall emits).
  * Mass is conserved exactly; momentum and energy are exchanged with the wall.
+ * Walls normal to x (bcx = 2, for the square cavity of Sec. 6) are the same
+ * with the axes exchanged, at x = -1/4 and x = nx - 1/4; where a population
+ * crosses an x wall and a y wall (the corners) the y wall owns it.
  * The rotational energy sees the walls as Dirichlet boundaries at
  * theta_R = theta_w (the internal energy is accommodated as well): the
  * diffusive flux through the wall face of point p is
@@ -500,14 +514,14 @@ static void make_ghost(const ora_params *P, const double *st, ghost *gh)
  * tangentially: uy = 0).
  */
 
-/* y index (not wrapped) of the destination of population i leaving a point on
- * sublattice s in layer y; the destination sublattice is the parity of
- * s + 2c, the same on all axes. */
-static int dest_y(int s, int y, int i)
+/* Index along axis a (not wrapped) of the destination of population i leaving
+ * a point on sublattice s with index idx on that axis; the destination
+ * sublattice is the parity of s + 2c, the same on all axes. */
+static int dest_index(int s, int idx, int i, int a)
 {
-    const int c2 = (int)lround(2.0 * C[i][1]);
+    const int c2 = (int)lround(2.0 * C[i][a]);
     const int sd = (s + c2) & 1;
-    return floor_div2(2 * y + s + c2 - sd);
+    return floor_div2(2 * idx + s + c2 - sd);
 }
 
 /* Distance from point p (sublattice s) to the low (w = 0) or high (w = 1) y
@@ -517,14 +531,27 @@ static double wall_distance(int s, int w)
     return w == 0 ? (2.0 * s + 1.0) / 4.0 : (3.0 - 2.0 * s) / 4.0;
 }
 
-/* rw[w * nx * nz + z * nx + x]: rho_w of wall w for column (x, z), from the
- * post-collision populations gs; gw[w] is f^eq(1, u_w, theta_w). */
-static int wall_density(const ora_params *P, const grid *G, const double *gs, double gw[2][Q],
+/* Walls w = 0, 1 (low, high y) own the columns (x, z), walls w = 2, 3 (low,
+ * high x) the columns (y, z); wall_slot gives the index of wall w's column
+ * holding the point (x, y, z) in the arrays of wall_density. */
+static long wall_slot(const grid *G, int w, int x, int y, int z)
+{
+    const long ny_cols = (long)G->nx * G->nz, nx_cols = (long)G->ny * G->nz;
+    if (w < 2) return w * ny_cols + (long)z * G->nx + x;
+    return 2 * ny_cols + (w - 2) * nx_cols + (long)z * G->ny + y;
+}
+
+/* rw[wall_slot(w, ...)]: rho_w of wall w for each of its columns, from the
+ * post-collision populations gs; gw[w] is f^eq(1, u_w, theta_w). A population
+ * whose destination (source) lies beyond a y wall belongs to that y wall even
+ * if it lies beyond an x wall as well (the corners); the x walls take the
+ * rest. */
+static int wall_density(const ora_params *P, const grid *G, const double *gs, double gw[4][Q],
                         double *rw)
 {
-    const long ncol = (long)G->nx * G->nz;
-    double *out = (double *)calloc(2 * ncol, sizeof(double));
-    double *in = (double *)calloc(2 * ncol, sizeof(double));
+    const long nslot = 2 * (long)G->nx * G->nz + 2 * (long)G->ny * G->nz;
+    double *out = (double *)calloc(nslot, sizeof(double));
+    double *in = (double *)calloc(nslot, sizeof(double));
     long p, k;
     int i;
     if (!out || !in) {
@@ -534,17 +561,19 @@ static int wall_density(const ora_params *P, const grid *G, const double *gs, do
     for (p = 0; p < G->npts; p++) {
         const int x = (int)(p % G->nx), y = (int)((p / G->nx) % G->ny);
         const int z = (int)((p / ((long)G->nx * G->ny)) % G->nz), s = (int)(p / G->n3);
-        const long col = (long)z * G->nx + x;
         for (i = 0; i < Q; i++) {
-            const int yd = dest_y(s, y, i);
+            const int yd = dest_index(s, y, i, 1), xd = dest_index(s, x, i, 0);
             const long q = pull_source(P, G, s, x, y, z, i);
-            if (yd < 0) out[col] += gs[p * Q + i];
-            if (yd >= G->ny) out[ncol + col] += gs[p * Q + i];
-            if (q == -3) in[col] += gw[0][i];
-            if (q == -4) in[ncol + col] += gw[1][i];
+            int wo = -1;
+            if (P->bcy == 1 && yd < 0) wo = 0;
+            else if (P->bcy == 1 && yd >= G->ny) wo = 1;
+            else if (P->bcx == 2 && xd < 0) wo = 2;
+            else if (P->bcx == 2 && xd >= G->nx) wo = 3;
+            if (wo >= 0) out[wall_slot(G, wo, x, y, z)] += gs[p * Q + i];
+            if (q <= -3) in[wall_slot(G, (int)(-3 - q), x, y, z)] += gw[-3 - q][i];
         }
     }
-    for (k = 0; k < 2 * ncol; k++) rw[k] = out[k] / in[k];
+    for (k = 0; k < nslot; k++) rw[k] = (in[k] > 0.0) ? out[k] / in[k] : 0.0;
     free(out); free(in);
     return 0;
 }
@@ -642,9 +671,9 @@ int ora_step(const ora_params *P, int nx, int ny, int nz, const double *res, dou
     double *th = (double *)malloc(sizeof(double) * N);
     double *v = (double *)malloc(sizeof(double) * 3 * N);
     double *Tt = (double *)malloc(sizeof(double) * N);
-    double *rw = (double *)malloc(sizeof(double) * 2 * nx * nz);
-    double gw[2][Q];
-    ghost gh[4];
+    double *rw = (double *)malloc(sizeof(double) * (2 * (long)nx * nz + 2 * (long)ny * nz));
+    double gw[4][Q];
+    ghost gh[6];
     long p, t;
     int i, a, k;
     if (!gs || !rho || !u || !kap || !Ep || !Ec || !th || !v || !Tt || !rw) {
@@ -655,7 +684,9 @@ int ora_step(const ora_params *P, int nx, int ny, int nz, const double *res, dou
     need_lattice();
     if ((P->diff == 1 && (ny != 1 || nz != 1 || P->bcx != 1)) || (P->diff == 1 && P->rot_mode == 1) ||
         (P->bcy == 1 && (ny < 2 || P->bcx == 1 || P->rot_mode == 1 || P->diff == 1 ||
-                         P->wall[1] != 0.0 || P->wall[5] != 0.0))) {
+                         P->wall[1] != 0.0 || P->wall[5] != 0.0)) ||
+        (P->bcx == 2 && (nx < 2 || P->rot_mode == 1 || P->diff == 1 ||
+                         P->xwall[0] != 0.0 || P->xwall[4] != 0.0))) {
         free(gs); free(rho); free(u); free(kap); free(Ep); free(Ec); free(th); free(v); free(Tt);
         free(rw);
         return 2;
@@ -664,18 +695,18 @@ int ora_step(const ora_params *P, int nx, int ny, int nz, const double *res, dou
         make_ghost(P, res, &gh[0]);
         make_ghost(P, res + 6, &gh[1]);
     }
-    if (P->bcy == 1) {
-        for (k = 0; k < 2; k++) {
-            const double *wl = P->wall + 4 * k;
-            double Lam[9];
-            for (a = 0; a < 9; a++) Lam[a] = (a % 4 == 0) ? wl[3] : 0.0;
-            ora_target(1.0, wl, Lam, gw[k]);
-            /* transport ghost: only u (the zero normal velocity) is read */
-            gh[2 + k].rho = 1.0;
-            gh[2 + k].Er = 0.5 * P->delta * wl[3];
-            gh[2 + k].kap = 0.0;
-            for (a = 0; a < 3; a++) gh[2 + k].u[a] = wl[a];
-        }
+    for (k = 0; k < 4; k++) {
+        /* walls 0, 1: y (bcy = 1); walls 2, 3: x (bcx = 2) */
+        const double *wl = (k < 2) ? P->wall + 4 * k : P->xwall + 4 * (k - 2);
+        double Lam[9];
+        if ((k < 2 && P->bcy != 1) || (k >= 2 && P->bcx != 2)) continue;
+        for (a = 0; a < 9; a++) Lam[a] = (a % 4 == 0) ? wl[3] : 0.0;
+        ora_target(1.0, wl, Lam, gw[k]);
+        /* transport ghost: only u (the zero normal velocity) is read */
+        gh[2 + k].rho = 1.0;
+        gh[2 + k].Er = 0.5 * P->delta * wl[3];
+        gh[2 + k].kap = 0.0;
+        for (a = 0; a < 3; a++) gh[2 + k].u[a] = wl[a];
     }
     for (t = 0; t < nsteps; t++) {
         /* 1. collision and rotational exchange */
@@ -689,7 +720,7 @@ int ora_step(const ora_params *P, int nx, int ny, int nz, const double *res, dou
             Tt[p] = m.T;
         }
         /* 2. pull streaming; the walls emit rho_w f^eq(1, u_w, theta_w) */
-        if (P->bcy == 1 && wall_density(P, &G, gs, gw, rw)) {
+        if ((P->bcy == 1 || P->bcx == 2) && wall_density(P, &G, gs, gw, rw)) {
             free(gs); free(rho); free(u); free(kap); free(Ep); free(Ec); free(th); free(v); free(Tt);
             free(rw);
             return 1;
@@ -704,7 +735,7 @@ int ora_step(const ora_params *P, int nx, int ny, int nz, const double *res, dou
                 else if (q >= -2)
                     g[p * Q + i] = gh[-1 - q].g[i];
                 else
-                    g[p * Q + i] = rw[(q == -3 ? 0 : (long)nx * nz) + (long)z * nx + x] * gw[-3 - q][i];
+                    g[p * Q + i] = rw[wall_slot(&G, (int)(-3 - q), x, y, z)] * gw[-3 - q][i];
             }
         }
         if (P->rot_mode == 1) {
@@ -807,10 +838,12 @@ int ora_step(const ora_params *P, int nx, int ny, int nz, const double *res, dou
                         /* wall: face coefficient kappa_R(p), gradient over the
                          * distance d to the wall, as a ghost value on the axis
                          * neighbour (at distance 1 - d beyond the wall) */
-                        const int w = (qp <= -3) ? 1 : 0, s = (int)(p / G.n3);
-                        const double d = wall_distance(s, w), thw = P->wall[4 * w + 3];
+                        const long qw = (qp <= -3) ? qp : qm;
+                        const int w = (int)(-3 - qw), side = w & 1, s = (int)(p / G.n3);
+                        const double *wl = (w < 2) ? P->wall : P->xwall;
+                        const double d = wall_distance(s, side), thw = wl[4 * side + 3];
                         const double gv = thw + (thw - th[p]) * (1.0 - d) / d;
-                        if (w == 1) { thp = gv; kp = kap[p]; } else { thm = gv; km = kap[p]; }
+                        if (side == 1) { thp = gv; kp = kap[p]; } else { thm = gv; km = kap[p]; }
                     }
                     acc += 0.5 * (kap[p] + kp) * (thp - th[p]) - 0.5 * (kap[p] + km) * (th[p] - thm);
                 }

@@ -10,6 +10,10 @@ condition the paper cites for its Sec. 6 Couette and cavity flows):
   * startup Couette flow follows the series solution printed in Sec. 6;
   * steady conduction between walls at different temperatures is linear,
     with the rotational temperature equal to the translational one;
+  * walls normal to x equal the transposed run with walls normal to y;
+  * with walls on x and y the corner entries follow a brute-force count
+    (the y walls own what crosses both), the state equal to all four walls is
+    fixed and mass is conserved;
 and planted mistakes in the wall code each fail one of these."""
 import numpy as np
 import pytest
@@ -21,11 +25,11 @@ from oracle import params as PM
 T0 = O.THETA0
 
 
-def _params(nu=0.1, lam=0.6, Pr=0.71, walls=None, kr=None):
+def _params(nu=0.1, lam=0.6, Pr=0.71, walls=None, kr=None, xwalls=None):
     d, tau, tau1, b, k_r = PM.relax_from_gas(1.4, *PM.gas_from_nondim(1.4, nu, lam, Pr), 0.0)
     if kr is not None:
         k_r = kr
-    return O.make_params(d, tau, tau1, b, k_r, 1.0, 1, walls=walls)
+    return O.make_params(d, tau, tau1, b, k_r, 1.0, 1, walls=walls, xwalls=xwalls)
 
 
 def _state(P, nx, ny, nz, f):
@@ -168,6 +172,115 @@ def pin_conduction(kr=None):
     return slope * L / 2, 0.5 * (at[0] + at[1]), at[0] - at[1], TR
 
 
+def pin_transpose():
+    """A run with walls normal to x equals the transposed run with walls normal
+    to y (x <-> y is a symmetry of the lattice and of every step), 10 steps of
+    a random 3-D state. Returns the largest field difference."""
+    rng = np.random.default_rng(11)
+    nxa, nya, nz = 6, 4, 2
+    n = 2 * nxa * nya * nz
+    fa = I.uniform(nxa, nya, nz, T0)
+    fa["rho"] = 1 + 0.05 * rng.uniform(-1, 1, n)
+    fa["u"] = 0.03 * rng.uniform(-1, 1, (3, n))
+    fa["T"] = T0 * (1 + 0.04 * rng.uniform(-1, 1, n))
+    fa["R"] = T0 * (1 + 0.04 * rng.uniform(-1, 1, n))
+    xw = [0, 0.03, -0.01, 0.29, 0, -0.02, 0.02, 0.30]
+    yw = [0.03, 0, -0.01, 0.29, -0.02, 0, 0.02, 0.30]
+    # point (s, z, y, x) of A <-> (s, z, x, y) of B
+    idx = np.arange(n).reshape(2, nz, nya, nxa)
+    perm = idx.transpose(0, 1, 3, 2).reshape(-1)      # B point order -> A point index
+    fb = {k: (v[..., perm].copy()) for k, v in fa.items()}
+    fb["u"] = fb["u"][[1, 0, 2]]
+    A = _state(_params(xwalls=xw), nxa, nya, nz, fa).step(10).fields()
+    B = _state(_params(walls=yw), nya, nxa, nz, fb).step(10).fields()
+    err = max(float(np.abs(B[k] - A[k][perm]).max()) for k in ("rho", "T", "R", "Erot"))
+    return max(err, float(np.abs(B["u"] - A["u"][[1, 0, 2]][:, perm]).max()))
+
+
+def pin_corners():
+    """One step from layer-wise equilibria at the walls' common temperature,
+    at rest, with all four walls (x and y) on a 4 x 4 x 1 grid: every entry
+    whose source lies beyond a wall holds rho_w f^eq(1, u_w, theta_w), rho_w
+    from a brute-force count per wall column, the y walls owning the
+    corners. Returns the largest error."""
+    nx = ny = 4
+    thw = 0.30
+    yw = [[0.04, 0, -0.02, thw], [-0.03, 0, 0.01, thw]]
+    xw = [[0, 0.02, 0.03, thw], [0, -0.01, -0.02, thw]]
+    P = _params(walls=yw[0] + yw[1], xwalls=xw[0] + xw[1])
+    c, _ = O.lattice()
+    c2 = np.rint(2 * c).astype(int)
+    rng = np.random.default_rng(5)
+    rho = 1.0 + 0.03 * rng.uniform(-1, 1, (2, ny, nx))
+    f = I.uniform(nx, ny, 1, thw)
+    f["rho"] = rho.reshape(-1)
+    S = _state(P, nx, ny, 1, f).step(1)
+    feq0 = O.target(1.0, np.zeros(3), thw * np.eye(3))
+    feqw = [O.target(1.0, np.array(w[:3]), thw * np.eye(3)) for w in (yw[0], yw[1], xw[0], xw[1])]
+
+    def owner(X2, Y2):
+        if Y2 < 0:
+            return 0
+        if Y2 >= 2 * ny:
+            return 1
+        if X2 < 0:
+            return 2
+        if X2 >= 2 * nx:
+            return 3
+        return -1
+
+    out, ent = {}, {}
+    for s_ in range(2):
+        for y in range(ny):
+            for x in range(nx):
+                col = {0: x, 1: x, 2: y, 3: y}
+                for i in range(41):
+                    X2, Y2 = 2 * x + s_, 2 * y + s_
+                    w = owner(X2 + c2[i, 0], Y2 + c2[i, 1])
+                    if w >= 0:
+                        out[(w, col[w])] = out.get((w, col[w]), 0.0) + rho[s_, y, x] * feq0[i]
+                    w = owner(X2 - c2[i, 0], Y2 - c2[i, 1])
+                    if w >= 0:
+                        ent.setdefault((w, col[w]), []).append((s_, y, x, i))
+    g = S.g.reshape(2, ny, nx, 41)
+    err = 0.0
+    for key, entries in ent.items():
+        w = key[0]
+        rho_w = out[key] / sum(feqw[w][i] for (_, _, _, i) in entries)
+        for (s_, y, x, i) in entries:
+            err = max(err, abs(g[s_, y, x, i] - rho_w * feqw[w][i]))
+    return err
+
+
+def pin_all_walls_fixed_and_mass():
+    """All four walls sliding along z at the fluid's velocity and temperature:
+    the uniform state is fixed; then mass is conserved with four different
+    walls on a random 3-D state."""
+    u = [0, 0, 0.03]
+    w = u + [0.31]
+    P = _params(walls=w + w, xwalls=w + w)
+    f = I.uniform(4, 5, 2, 0.31, rho=1.1, u=u)
+    S = _state(P, 4, 5, 2, f)
+    F0 = S.fields()
+    S.step(5)
+    F1 = S.fields()
+    fixed = max(float(np.abs(F1[k] - F0[k]).max()) for k in ("rho", "u", "T", "R"))
+    rng = np.random.default_rng(3)
+    nx, ny, nz = 5, 4, 2
+    n = 2 * nx * ny * nz
+    P = _params(walls=[0.02, 0, 0, 0.28, -0.03, 0, 0.01, 0.31],
+                xwalls=[0, 0.01, 0.02, 0.30, 0, -0.02, 0, 0.29])
+    f = I.uniform(nx, ny, nz, T0)
+    f["rho"] = 1 + 0.05 * rng.uniform(-1, 1, n)
+    f["u"] = 0.03 * rng.uniform(-1, 1, (3, n))
+    f["T"] = T0 * (1 + 0.05 * rng.uniform(-1, 1, n))
+    f["R"] = T0 * (1 + 0.05 * rng.uniform(-1, 1, n))
+    S = _state(P, nx, ny, nz, f)
+    m0 = S.diag()["M"]
+    S.step(20)
+    return fixed, abs(S.diag()["M"] - m0) / m0
+
+
 # ---------------------------------------------------------------------------
 # tests
 
@@ -210,13 +323,27 @@ def test_steady_conduction_is_linear_between_the_wall_temperatures():
     assert _conduction_ok(*r), r
 
 
+def test_x_walls_equal_transposed_y_walls():
+    assert pin_transpose() < 1e-12
+
+
+def test_corner_emission_matches_brute_force():
+    assert pin_corners() < 1e-15
+
+
+def test_all_four_walls_fixed_point_and_mass():
+    fixed, dm = pin_all_walls_fixed_and_mass()
+    assert fixed < 1e-13 and dm < 1e-13, (fixed, dm)
+
+
 # planted mistakes in the wall code: (name, original, mistake, pin that must fail)
 WALL_MUTANTS = [
-    ("no mass balance", "rw[k] = out[k] / in[k];", "rw[k] = 1.0;", "mass"),
-    ("destination in the wrong direction", "return floor_div2(2 * y + s + c2 - sd);",
-     "return floor_div2(2 * y + s - c2 - sd);", "mass"),
-    ("leaving flux of the other wall", "if (yd < 0) out[col] += gs[p * Q + i];",
-     "if (yd < 0) out[ncol + col] += gs[p * Q + i];", "emission"),
+    ("no mass balance", "rw[k] = (in[k] > 0.0) ? out[k] / in[k] : 0.0;",
+     "rw[k] = (in[k] > 0.0) ? 1.0 : 0.0;", "mass"),
+    ("destination in the wrong direction", "return floor_div2(2 * idx + s + c2 - sd);",
+     "return floor_div2(2 * idx + s - c2 - sd);", "mass"),
+    ("leaving flux of the other wall", "if (P->bcy == 1 && yd < 0) wo = 0;",
+     "if (P->bcy == 1 && yd < 0) wo = 1;", "emission"),
     ("wall distances of the sublattices swapped",
      "return w == 0 ? (2.0 * s + 1.0) / 4.0 : (3.0 - 2.0 * s) / 4.0;",
      "return w == 0 ? (3.0 - 2.0 * s) / 4.0 : (2.0 * s + 1.0) / 4.0;", "conduction"),
@@ -224,6 +351,12 @@ WALL_MUTANTS = [
      "const double gv = thw + (thw - th[p]);", "conduction"),
     ("wall emits at the lattice temperature", "for (a = 0; a < 9; a++) Lam[a] = (a % 4 == 0) ? wl[3] : 0.0;",
      "for (a = 0; a < 9; a++) Lam[a] = (a % 4 == 0) ? THETA0 : 0.0;", "fixed"),
+    ("corner leaving owned by the x wall", "if (P->bcy == 1 && yd < 0) wo = 0;",
+     "if (P->bcy == 1 && yd < 0 && !(P->bcx == 2 && xd < 0)) wo = 0;", "corners"),
+    ("x wall ghost on the y-wall temperatures", "const double *wl = (w < 2) ? P->wall : P->xwall;",
+     "const double *wl = P->wall;", "transpose"),
+    ("x walls emit from the y walls' columns", "return 2 * ny_cols + (w - 2) * nx_cols + (long)z * G->ny + y;",
+     "return 2 * ny_cols + (w - 2) * nx_cols + (long)z * G->ny + x % G->ny;", "corners"),
 ]
 
 
@@ -235,6 +368,10 @@ def _fails(pin):
         return not pin_emission() < 1e-15
     if pin == "fixed":
         return not pin_fixed_point() < 1e-13
+    if pin == "corners":
+        return not pin_corners() < 1e-15
+    if pin == "transpose":
+        return not pin_transpose() < 1e-12
     return not _conduction_ok(*pin_conduction())
 
 
