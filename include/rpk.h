@@ -62,8 +62,9 @@ typedef enum {
 enum { RPK_F64 = 0, RPK_F32 = 1, RPK_F16DEV = 2, RPK_BF16DEV = 3 };
 
 /* Boundary in x: periodic, or fixed equilibrium reservoirs beyond both ends
- * (rpk_set_reservoirs). y is periodic unless rpk_set_walls puts diffuse walls
- * there; z is always periodic. */
+ * (rpk_set_reservoirs); a periodic x becomes walled with rpk_set_x_walls. y is
+ * periodic unless rpk_set_walls puts diffuse walls there; z is always
+ * periodic. */
 enum { RPK_BC_PERIODIC = 0, RPK_BC_RESERVOIR = 1 };
 
 typedef struct {
@@ -177,6 +178,16 @@ rpk_status rpk_set_rot_mode(rpk_lattice* lat, int mode);
  * coefficient 4 kappa_R) and for the wall temperatures. Checkpoints record the
  * walls. Synchronises the lattice's stream. */
 rpk_status rpk_set_walls(rpk_lattice* lat, const double* walls8);
+/* Diffuse walls normal to x, for the square cavity of Sec. 6: the same
+ * condition as rpk_set_walls with x and y exchanged, at x = -1/4 and
+ * x = nx - 1/4. walls8 = ux, uy, uz, theta of the low-x wall, then of the
+ * high-x wall (ux must be 0; theta > 0); NULL makes x periodic again. With
+ * walls on both axes, a population whose pull source lies beyond a y wall and
+ * an x wall (a corner) is emitted by the y wall, and each x wall balances the
+ * mass of the entries the y walls leave to it. Requires nx >= 2,
+ * bc_x = RPK_BC_PERIODIC (the x walls take the reservoirs' place) and
+ * rotational mode 0; otherwise as rpk_set_walls. */
+rpk_status rpk_set_x_walls(rpk_lattice* lat, const double* walls8);
 
 /* Initial state from hydrodynamic fields (layout above): rho > 0, u (3
  * planes), theta_T > 0, theta_R > 0. f = f^Eq(rho, u, theta_T I), then

@@ -126,6 +126,7 @@ def load_library(path=None):
         "rpk_set_reservoirs": (i, [vp, _dp]),
         "rpk_set_rot_mode": (i, [vp, i]),
         "rpk_set_walls": (i, [vp, _dp]),
+        "rpk_set_x_walls": (i, [vp, _dp]),
         "rpk_init_fields": (i, [vp, vp, vp, vp, vp, i]),
         "rpk_step": (i, [vp, i64]),
         "rpk_read_moments": (i, [vp, vp, vp, vp, vp, vp, i]),
@@ -306,6 +307,19 @@ class Lattice:
         if w.size != 8:
             raise ValueError("each wall is (ux, uy, uz, theta)")
         _check(load_library().rpk_set_walls(self._h, w.ctypes.data_as(_dp)))
+        return self
+
+    def set_x_walls(self, low=None, high=None):
+        """Diffuse walls normal to x at x = -1/4 and x = nx - 1/4
+        (rpk_set_x_walls): low and high are (ux, uy, uz, theta), ux = 0; no
+        arguments makes x periodic again."""
+        if low is None and high is None:
+            _check(load_library().rpk_set_x_walls(self._h, None))
+            return self
+        w = np.ascontiguousarray(np.concatenate([np.ravel(low), np.ravel(high)]), dtype=np.float64)
+        if w.size != 8:
+            raise ValueError("each wall is (ux, uy, uz, theta)")
+        _check(load_library().rpk_set_x_walls(self._h, w.ctypes.data_as(_dp)))
         return self
 
     def set_rot_mode(self, mode):

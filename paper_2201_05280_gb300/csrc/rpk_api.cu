@@ -196,8 +196,8 @@ rpk_status rpk_create(const rpk_grid* grid, void* cuda_stream, rpk_lattice** out
                 {&L->e_a, fb}, {&L->e_b, fb}, {&L->vbuf, 3 * fb}, {&L->thbuf, fb},
                 {&L->drho, fb}, {&L->kap, fb},
                 {&L->u[0], 3 * fb}, {&L->u[1], 3 * fb},
-                {&L->ghost, 2 * kGhostStride * L->real_elem},
-                {&L->wrho, 2 * (size_t)grid->nx * grid->nz * L->real_elem},
+                {&L->ghost, kGhostBlocks * kGhostStride * L->real_elem},
+                {&L->wrho, (2 * (size_t)grid->nx * grid->nz + 2 * (size_t)grid->ny * grid->nz) * L->real_elem},
                 {(void**)&L->status, sizeof(unsigned)},
                 {(void**)&L->diag_partial, sizeof(double) * kDiagVals * kDiagBlocks},
                 {(void**)&L->diag_out, sizeof(double) * 16}};
@@ -213,9 +213,12 @@ rpk_status rpk_create(const rpk_grid* grid, void* cuda_stream, rpk_lattice** out
     L->bytes_held += r.bytes;
   }
   err = cudaMemsetAsync(L->status, 0, sizeof(unsigned), L->stream);
-  if (err == cudaSuccess) err = cudaMemsetAsync(L->ghost, 0, 2 * kGhostStride * L->real_elem, L->stream);
   if (err == cudaSuccess)
-    err = cudaMemsetAsync(L->wrho, 0, 2 * (size_t)grid->nx * grid->nz * L->real_elem, L->stream);
+    err = cudaMemsetAsync(L->ghost, 0, kGhostBlocks * kGhostStride * L->real_elem, L->stream);
+  if (err == cudaSuccess)
+    err = cudaMemsetAsync(L->wrho, 0,
+                          (2 * (size_t)grid->nx * grid->nz + 2 * (size_t)grid->ny * grid->nz) * L->real_elem,
+                          L->stream);
   if (err == cudaSuccess) err = cudaStreamSynchronize(L->stream);
   if (err != cudaSuccess) {
     free_all(L);
@@ -240,7 +243,7 @@ rpk_status rpk_set_relax(rpk_lattice* L, const rpk_relax* r) {
   L->relax = *r;
   L->relax_ok = true;
   if (r->nsub > 0) L->nsub = r->nsub;
-  if (L->res_ok || L->walls) {
+  if (L->res_ok || L->walls || L->xwalls) {
     // the boundary tables hold e and kappa_R, which depend on the parameters
     RPK_CUDA(cudaSetDevice(L->device));
     return with_ops(L->grid.precision, [&](auto ops) { return decltype(ops)::ghosts(L); });
@@ -297,11 +300,32 @@ rpk_status rpk_set_walls(rpk_lattice* L, const double* w) {
   return with_ops(L->grid.precision, [&](auto ops) { return decltype(ops)::ghosts(L); });
 }
 
+rpk_status rpk_set_x_walls(rpk_lattice* L, const double* w) {
+  if (!L) return fail(RPK_ERR_ARG, "lattice is NULL");
+  if (!w) {
+    L->xwalls = false;
+    return RPK_OK;
+  }
+  if (L->grid.nx < 2) return fail(RPK_ERR_STATE, "x walls need nx >= 2");
+  if (L->grid.bc_x != RPK_BC_PERIODIC) return fail(RPK_ERR_STATE, "x walls replace the x reservoirs: use bc_x = periodic");
+  if (L->rot_mode != 0) return fail(RPK_ERR_STATE, "walls need the conservative rotational form (mode 0)");
+  if (!L->relax_ok) return fail(RPK_ERR_STATE, "set the relaxation parameters first");
+  for (int k = 0; k < 8; ++k)
+    if (!std::isfinite(w[k])) return fail(RPK_ERR_PARAM, "wall state not finite");
+  if (w[0] != 0.0 || w[4] != 0.0) return fail(RPK_ERR_PARAM, "walls slide tangentially: ux must be 0");
+  if (!(w[3] > 0.0) || !(w[7] > 0.0)) return fail(RPK_ERR_PARAM, "wall temperatures must be > 0");
+  std::memcpy(L->xwall, w, sizeof(L->xwall));
+  L->xwalls = true;
+  RPK_CUDA(cudaSetDevice(L->device));
+  return with_ops(L->grid.precision, [&](auto ops) { return decltype(ops)::ghosts(L); });
+}
+
 rpk_status rpk_set_rot_mode(rpk_lattice* L, int mode) {
   if (!L) return fail(RPK_ERR_ARG, "lattice is NULL");
   if (mode != 0 && mode != 1) return fail(RPK_ERR_ARG, "mode must be 0 (conservative) or 1 (paper)");
   if (mode == L->rot_mode) return RPK_OK;
-  if (mode == 1 && L->walls) return fail(RPK_ERR_STATE, "the paper-mode solver has no wall boundary");
+  if (mode == 1 && (L->walls || L->xwalls))
+    return fail(RPK_ERR_STATE, "the paper-mode solver has no wall boundary");
   L->rot_mode = mode;
   L->init_ok = false;  // the stored rotational state changes meaning: initialise again
   if (L->res_ok) {
@@ -365,10 +389,13 @@ rpk_status rpk_init_fields(rpk_lattice* L, const double* rho, const double* u,
     RPK_CUDA(cudaStreamSynchronize(L->stream));
     double tmax = *std::max_element(part.begin(), part.end());
     if (!(tmax > 0.0) || !std::isfinite(tmax)) return fail(RPK_ERR_PARAM, "fields need theta > 0");
-    if (L->walls) {
-      // a point next to a wall has one face of coefficient 4 kappa_R (distance 1/4)
-      tmax = std::max(tmax, std::max(L->wall[3], L->wall[7]));
-      L->nsub = nsub_for_diagonal(&L->relax, tmax, 2.0 * active_dims(L->grid) + 3.0);
+    if (L->walls || L->xwalls) {
+      // a point next to a wall has one face of coefficient 4 kappa_R (distance
+      // 1/4) per wall axis
+      if (L->walls) tmax = std::max(tmax, std::max(L->wall[3], L->wall[7]));
+      if (L->xwalls) tmax = std::max(tmax, std::max(L->xwall[3], L->xwall[7]));
+      L->nsub = nsub_for_diagonal(&L->relax, tmax,
+                                  2.0 * active_dims(L->grid) + 3.0 * ((int)L->walls + (int)L->xwalls));
     } else {
       L->nsub = rpk_auto_nsub(&L->relax, tmax, active_dims(L->grid));
     }
@@ -474,6 +501,8 @@ struct CkptHeader {
   double res[12];
   int32_t rot_mode, walls;
   double wall[8];
+  int32_t xwalls, pad;
+  double xwall[8];
 };
 }  // namespace
 
@@ -500,10 +529,12 @@ rpk_status rpk_save(rpk_lattice* L, const char* path) {
   FILE* f = fopen(path, "wb");
   if (!f) return fail(RPK_ERR_IO, std::string("cannot open ") + path);
   CkptHeader h{};
-  std::memcpy(h.magic, "RPKCKPT3", 8);
+  std::memcpy(h.magic, "RPKCKPT4", 8);
   h.rot_mode = L->rot_mode;
   h.walls = L->walls;
   std::memcpy(h.wall, L->wall, sizeof(h.wall));
+  h.xwalls = L->xwalls;
+  std::memcpy(h.xwall, L->xwall, sizeof(h.xwall));
   h.abi = RPK_ABI_VERSION;
   h.nx = L->grid.nx; h.ny = L->grid.ny; h.nz = L->grid.nz;
   h.precision = L->grid.precision; h.bc_x = L->grid.bc_x;
@@ -531,9 +562,10 @@ rpk_status rpk_load(rpk_lattice* L, const char* path) {
   if (!f) return fail(RPK_ERR_IO, std::string("cannot open ") + path);
   CkptHeader h{};
   rpk_status st = RPK_OK;
-  if (fread(&h, sizeof(h), 1, f) != 1 || std::memcmp(h.magic, "RPKCKPT3", 8) != 0)
+  if (fread(&h, sizeof(h), 1, f) != 1 || std::memcmp(h.magic, "RPKCKPT4", 8) != 0)
     st = fail(RPK_ERR_IO, "not a checkpoint");
-  else if (h.walls && (h.rot_mode != 0 || h.bc_x != RPK_BC_PERIODIC || h.ny < 2))
+  else if ((h.walls && (h.rot_mode != 0 || h.bc_x != RPK_BC_PERIODIC || h.ny < 2)) ||
+           (h.xwalls && (h.rot_mode != 0 || h.bc_x != RPK_BC_PERIODIC || h.nx < 2)))
     st = fail(RPK_ERR_IO, "inconsistent checkpoint");
   else if (h.rot_mode != L->rot_mode)
     st = fail(RPK_ERR_ARG, "checkpoint rotational mode differs from the lattice (rpk_set_rot_mode)");
@@ -562,7 +594,9 @@ rpk_status rpk_load(rpk_lattice* L, const char* path) {
   L->res_ok = h.res_ok != 0;
   L->walls = h.walls != 0;
   std::memcpy(L->wall, h.wall, sizeof(L->wall));
-  if (L->res_ok || L->walls) {
+  L->xwalls = h.xwalls != 0;
+  std::memcpy(L->xwall, h.xwall, sizeof(L->xwall));
+  if (L->res_ok || L->walls || L->xwalls) {
     st = with_ops(L->grid.precision, [&](auto ops) { return decltype(ops)::ghosts(L); });
     if (st != RPK_OK) return st;
   }

@@ -88,9 +88,15 @@ struct StepConst {
   Real inv_1pa;   // 1 / (1 + a)
 };
 
-// Ghost values, one block of kGhostStride per x end (reservoirs) or per y wall
-// (walls: h of f^eq(1, u_w, theta_w), its e, rho - 1 = 0, u_w, kappa_R).
+// Ghost values, one block of kGhostStride per x end (reservoirs, blocks 0, 1)
+// or per wall (low / high y wall in blocks 0, 1, low / high x wall in blocks
+// 2, 3: h of f^eq(1, u_w, theta_w), its e, rho - 1 = 0, u_w, kappa_R).
 constexpr int kGhostStride = 48;
+constexpr int kGhostBlocks = 4;
+
+// Boundary kinds of the templated kernels (kBC): 0 periodic; 1 x reservoirs;
+// otherwise a mask of diffuse walls, kWallY normal to y and kWallX normal to x.
+constexpr int kWallY = 2, kWallX = 4;
 enum { kGhE = 41, kGhDrho = 42, kGhU = 43, kGhKap = 46 };
 
 // ---------------------------------------------------------------------------
@@ -309,10 +315,13 @@ __device__ __forceinline__ bool point_from_block(const StepConst<Real>& K, Point
 // from sublattice 0 at index x comes from sublattice 1 at x - (c > 0 ? 1 : 0)
 // per axis, and from sublattice 1 it comes from sublattice 0 at
 // x + (c < 0 ? 1 : 0)). kBC = 1: sources beyond the x ends read the reservoir.
-// kBC = 2: sources beyond a y wall (y = -1/4, y = ny - 1/4) are emitted by the
-// wall, g = rho_w f^eq(1, u_w, theta_w), i.e. h = d + hw + d hw with
+// kBC & kWallY: sources beyond a y wall (y = -1/4, y = ny - 1/4) are emitted by
+// the wall, g = rho_w f^eq(1, u_w, theta_w), i.e. h = d + hw + d hw with
 // d = rho_w - 1 of the point's (x, z) column (wcol[(wall * nz + z) * nx + x])
-// and hw the wall's table entry.
+// and hw the wall's table entry. kBC & kWallX: the same for the x walls
+// (x = -1/4, x = nx - 1/4) with the (y, z) columns at
+// wcol[2 nx nz + (wall * nz + z) * ny + y]; a source beyond both a y and an x
+// wall belongs to the y wall.
 template <typename Store, typename Real, bool kPull, int kBC>
 __device__ __forceinline__ void gather(const Store* __restrict__ pin,
                                        const Real* __restrict__ ghost, const StepConst<Real>& K,
@@ -350,35 +359,44 @@ __device__ __forceinline__ void gather(const Store* __restrict__ pin,
       constexpr Vel2 v = vel2(q);
       constexpr bool half = (v.x & 1) != 0;
       int xs, ys, zs;
-      [[maybe_unused]] bool inside = true;
+      [[maybe_unused]] bool insx = true, insy = true;
       const Store* base;
       if constexpr (half) {
         xs = v.x > 0 ? xhp : xhm;
         ys = v.y > 0 ? yhp : yhm;
         zs = v.z > 0 ? zhp : zhm;
-        if constexpr (kBC == 1) inside = v.x > 0 ? xinhp : xinhm;
-        if constexpr (kBC == 2) inside = v.y > 0 ? yinhp : yinhm;
+        insx = v.x > 0 ? xinhp : xinhm;
+        insy = v.y > 0 ? yinhp : yinhm;
         base = other;
       } else {
         xs = xw[2 - v.x / 2];
         ys = yw[2 - v.y / 2];
         zs = zw[2 - v.z / 2];
-        if constexpr (kBC == 1) inside = xin[2 - v.x / 2];
-        if constexpr (kBC == 2) inside = yin[2 - v.y / 2];
+        insx = xin[2 - v.x / 2];
+        insy = yin[2 - v.y / 2];
         base = same;
       }
       const int64_t cell = ((int64_t)zs * ny + ys) * nx + xs;
       if constexpr (kBC == 1) {
-        if (!inside) {
+        if (!insx) {
           h[q] = ghost[(v.x > 0 ? 0 : kGhostStride) + q];
           return;
         }
       }
-      if constexpr (kBC == 2 && v.y != 0) {
-        if (!inside) {
+      if constexpr ((kBC & kWallY) && v.y != 0) {
+        if (!insy) {
           const int w = v.y > 0 ? 0 : 1;  // source below the low wall / above the high wall
           const Real d = wcol[((int64_t)w * nz + P.z) * nx + P.x];
           const Real hw = ghost[w * kGhostStride + q];
+          h[q] = d + hw + d * hw;
+          return;
+        }
+      }
+      if constexpr ((kBC & kWallX) && v.x != 0) {
+        if (!insx) {
+          const int w = v.x > 0 ? 0 : 1;
+          const Real d = wcol[2 * (int64_t)nx * nz + ((int64_t)w * nz + P.z) * ny + P.y];
+          const Real hw = ghost[(2 + w) * kGhostStride + q];
           h[q] = d + hw + d * hw;
           return;
         }
@@ -388,51 +406,73 @@ __device__ __forceinline__ void gather(const Store* __restrict__ pin,
   }
 }
 
-// rho_w - 1 of every (x, z) column at both y walls, from the post-collision
-// populations pin that the next pull reads: the column's populations whose
-// destination lies beyond the wall (the |2 c_y| layers next to it, for each
-// velocity pointing at the wall) carry the mass M_out = sum w (1 + h); the wall
-// emits rho_w f^eq(1, u_w, theta_w) into |2 c_y| entries of the column for each
-// velocity pointing away from it, mass rho_w D with D = sum |2 c_y| w (1 + hw).
-// rho_w - 1 = (A + sum w h) / D, A = sum |2 c_y| w - D = -sum |2 c_y| w hw (the
-// weights of c and -c are equal), so that the deviation keeps its precision.
-// One thread per (column, wall); wcol[(wall * nz + z) * nx + x].
-template <typename Store, typename Real>
+// rho_w - 1 of every wall column, from the post-collision populations pin that
+// the next pull reads. For a wall and one of its columns: the column's
+// populations whose destination lies beyond the wall carry the mass
+// M_out = sum w (1 + h); the wall emits rho_w f^eq(1, u_w, theta_w) into the
+// column's entries whose source lies beyond it, mass rho_w D with
+// D = sum w (1 + hw). rho_w - 1 = (M_out - D) / D, accumulated as
+// (sum_out w - sum_in w) + sum_out w h - sum_in w hw so that the deviation keeps
+// its precision (the weights of c and -c are equal). A velocity with |2 c_a| = n
+// along the wall normal a has its n layers next to the wall in play. Where
+// both kinds of walls are on, a population crossing a y wall belongs to it
+// even if it crosses an x wall too, so the x walls count only entries whose
+// other end stays inside in y.
+// One thread per (wall, column): y walls first (slots [0, 2 nx nz), columns
+// (x, z)), then x walls (slots 2 nx nz + [0, 2 ny nz), columns (y, z)).
+template <typename Store, typename Real, int kBC>
 __global__ void __launch_bounds__(128)
     k_wall_rho(StepConst<Real> K, const Store* __restrict__ pin, const Real* __restrict__ ghost,
                Real* __restrict__ wcol) {
-  const int64_t ncol = (int64_t)K.nx * K.nz;
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= 2 * ncol) return;
+  const int64_t ny_cols = (int64_t)K.nx * K.nz, nx_cols = (int64_t)K.ny * K.nz;
+  const int64_t ybase = (kBC & kWallY) ? 2 * ny_cols : 0;
+  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= ybase + ((kBC & kWallX) ? 2 * nx_cols : 0)) return;
+  const bool xwall = t >= ybase;
+  int64_t slot = t;
+  if (xwall) {
+    t -= ybase;
+    slot = 2 * ny_cols + t;
+  }
+  const int64_t ncol = xwall ? nx_cols : ny_cols;
   const int w = t >= ncol ? 1 : 0;
   const int64_t c = t - w * ncol;
-  const int x = (int)(c % K.nx), z = (int)(c / K.nx);
-  const int ny = K.ny;
+  const int nx = K.nx, ny = K.ny;
+  // column coordinates: (x, z) for a y wall, (y, z) for an x wall
+  const int ca = (int)(c % (xwall ? ny : nx)), z = (int)(c / (xwall ? ny : nx));
+  const int nn = xwall ? nx : ny;  // cells along the wall normal
   const int64_t n3 = K.n3;
-  const Real* hw = ghost + w * kGhostStride;
-  Real D = Real(0), A = Real(0), S = Real(0);
+  const Real* hw = ghost + ((xwall ? 2 : 0) + w) * kGhostStride;
+  Real base = Real(0), A = Real(0), D = Real(0), S = Real(0);
   static_for<kQ - 1>([&](auto qc) {
     constexpr int q = decltype(qc)::value + 1;
     constexpr Vel2 v = vel2(q);
-    if constexpr (v.y != 0) {
-      constexpr int n = v.y > 0 ? v.y : -v.y;
-      const Real wq = Real(weight(q));
-      if ((w == 0) == (v.y > 0)) {
-        // emitted by this wall
-        D += Real(n) * wq * (Real(1) + hw[q]);
-        A -= Real(n) * wq * hw[q];
+    const int vn = xwall ? v.x : v.y;  // doubled velocity along the normal
+    const int vt = xwall ? v.y : 0;    // along y, for the corner rule of the x walls
+    if (vn == 0) return;
+    const int n = vn > 0 ? vn : -vn;
+    const Real wq = Real(weight(q));
+    const bool emitted = (w == 0) == (vn > 0);
+    for (int k = 0; k < n; ++k) {
+      const int L2 = w == 0 ? k : 2 * nn - 1 - k;  // 2 * index + s along the normal
+      const int s = L2 & 1, i = L2 >> 1;
+      if ((kBC & kWallY) && xwall) {
+        // the other end of the trajectory must stay inside in y
+        const int Y2 = 2 * ca + s + (emitted ? -vt : vt);
+        if (Y2 < 0 || Y2 >= 2 * ny) continue;
+      }
+      if (emitted) {
+        D += wq * (Real(1) + hw[q]);
+        A -= wq * hw[q];
+        base -= wq;
       } else {
-        // leaving through this wall: layers 2y + s = 0 .. n-1 (low) or 2ny-1 .. 2ny-n (high)
-#pragma unroll
-        for (int k = 0; k < n; ++k) {
-          const int Y2 = w == 0 ? k : 2 * ny - 1 - k;
-          const int s = Y2 & 1, y = Y2 >> 1;
-          S += wq * to_real<Store, Real>(pin[(int64_t)(s * kQ + q) * n3 + ((int64_t)z * ny + y) * K.nx + x]);
-        }
+        const int x = xwall ? i : ca, y = xwall ? ca : i;
+        S += wq * to_real<Store, Real>(pin[(int64_t)(s * kQ + q) * n3 + ((int64_t)z * ny + y) * nx + x]);
+        base += wq;
       }
     }
   });
-  wcol[t] = (A + S) / D;
+  wcol[slot] = (base + A + S) / D;
 }
 
 }  // namespace rpk

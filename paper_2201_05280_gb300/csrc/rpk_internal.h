@@ -36,10 +36,12 @@ struct rpk_lattice {
   void* drho = nullptr;
   void* kap = nullptr;
   void* u[2] = {nullptr, nullptr};  // ring: u(t) and u(t-1), 3 planes each
-  void* ghost = nullptr;            // reservoir or wall table (Real, 2 x 48)
+  void* ghost = nullptr;            // reservoir and wall table (Real, 4 x 48)
   bool walls = false;               // diffuse walls normal to y (rpk_set_walls)
-  double wall[8] = {0};             // ux, uy, uz, theta of the low and the high wall
-  void* wrho = nullptr;             // rho_w - 1 per wall and (x, z) column (Real, 2 nx nz)
+  double wall[8] = {0};             // ux, uy, uz, theta of the low and the high y wall
+  bool xwalls = false;              // diffuse walls normal to x (rpk_set_x_walls)
+  double xwall[8] = {0};            // ux, uy, uz, theta of the low and the high x wall
+  void* wrho = nullptr;             // rho_w - 1 per wall column (Real, 2 nx nz + 2 ny nz)
   unsigned* status = nullptr;
   double* diag_partial = nullptr;
   double* diag_out = nullptr;

@@ -24,7 +24,8 @@ __device__ __forceinline__ bool point_from_block2d(const StepConst<Real>& K, Poi
 }
 
 // Axis neighbour on the same sublattice, or -1 / -2 for the low / high x
-// reservoir when kBC == 1, or -3 / -4 for the low / high y wall when kBC == 2.
+// reservoir (kBC == 1), -3 / -4 for the low / high y wall (kBC & kWallY),
+// -5 / -6 for the low / high x wall (kBC & kWallX).
 template <int kBC, typename Real>
 __device__ __forceinline__ int64_t axis_nb(const StepConst<Real>& K, const PointIdx& P, int axis,
                                            int d) {
@@ -35,10 +36,14 @@ __device__ __forceinline__ int64_t axis_nb(const StepConst<Real>& K, const Point
       if (x < 0) return -1;
       if (x >= K.nx) return -2;
     }
+    if (kBC & kWallX) {
+      if (x < 0) return -5;
+      if (x >= K.nx) return -6;
+    }
     x = wrap_near(x, K.nx);
   } else if (axis == 1) {
     y += d;
-    if (kBC == 2) {
+    if (kBC & kWallY) {
       if (y < 0) return -3;
       if (y >= K.ny) return -4;
     }
@@ -49,23 +54,25 @@ __device__ __forceinline__ int64_t axis_nb(const StepConst<Real>& K, const Point
   return (int64_t)P.s * K.n3 + ((int64_t)z * K.ny + y) * K.nx + x;
 }
 
-// Ghost block of a negative axis_nb result: low end / low wall first.
+// Ghost block of a negative axis_nb result: -1, -3 -> 0; -2, -4 -> 1; -5 -> 2; -6 -> 3.
 template <typename Real>
 __device__ __forceinline__ const Real* ghost_block(const Real* __restrict__ ghost, int64_t q) {
-  return ghost + ((q == -1 || q == -3) ? 0 : kGhostStride);
+  const int b = q >= -4 ? (int)((-1 - q) & 1) : (int)(-3 - q);
+  return ghost + b * kGhostStride;
 }
 
 // Wall ghost of theta_R - theta0 for the diffusion: the face flux to the wall
 // is kappa_R(p)(theta_w - theta_R(p))/d, d the distance from the point to the
-// wall (1/4 for sublattice 0 at the low wall and sublattice 1 at the high
-// wall, 3/4 otherwise), written as the value theta_w + (theta_w - theta_p)(1 - d)/d
+// wall (1/4 for sublattice 0 at a low wall and sublattice 1 at a high wall,
+// 3/4 otherwise), written as the value theta_w + (theta_w - theta_p)(1 - d)/d
 // on the axis neighbour (whose face coefficient is then kappa_R(p)).
 template <typename Real>
 __device__ __forceinline__ Real wall_theta(const StepConst<Real>& K, const Real* __restrict__ g,
                                            int64_t q, int s, Real thp) {
   const Real thw = (Real(2) * g[kGhE] - K.delta * K.theta0 * g[kGhDrho]) /
                    (K.delta * (Real(1) + g[kGhDrho]));
-  const Real r = ((q == -3) == (s == 0)) ? Real(3) : Real(1.0 / 3.0);
+  const bool low = (q == -3 || q == -5);
+  const Real r = (low == (s == 0)) ? Real(3) : Real(1.0 / 3.0);
   return thw + (thw - thp) * r;
 }
 
@@ -102,7 +109,7 @@ __global__ void __launch_bounds__(128)
         const Real* g = ghost_block(ghost, q);
         thq = dthR(g[kGhE], g[kGhDrho]);
         kq = g[kGhKap];
-      } else if (kBC == 2 && q < 0) {
+      } else if ((kBC & (kWallX | kWallY)) && q < 0) {
         thq = wall_theta(K, ghost_block(ghost, q), q, P.s, th);
         kq = kp;
       } else {
@@ -209,7 +216,7 @@ __global__ void __launch_bounds__(kTBX * kTBY)
         const Real* g = ghost_block(ghost, q);
         thq = (Real(2) * g[kGhE] - t0d * g[kGhDrho]) / (K.delta * (Real(1) + g[kGhDrho]));
         kq = g[kGhKap];
-      } else if (kBC == 2 && q < 0) {
+      } else if ((kBC & (kWallX | kWallY)) && q < 0) {
         thq = wall_theta(K, ghost_block(ghost, q), q, P.s, thp);
         kq = kp;
       } else {
@@ -234,7 +241,7 @@ __global__ void __launch_bounds__(kTBX * kTBY)
 template <typename Real, int kBC>
 __device__ __forceinline__ Real pm_nb(const StepConst<Real>& K, const PointIdx& P, const Real* __restrict__ r,
                                       const Real* __restrict__ ghost, int a, int d) {
-  static_assert(kBC != 2, "the paper-mode solver has no wall boundary");
+  static_assert(kBC <= 1, "the paper-mode solver has no wall boundary");
   const int64_t q = axis_nb<kBC>(K, P, a, d);
   if (kBC == 1 && q < 0) return ghost[(q == -1 ? 0 : kGhostStride) + kGhE];
   return r[q];

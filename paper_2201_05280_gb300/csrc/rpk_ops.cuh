@@ -64,15 +64,30 @@ static inline rpk_status check_launch(const char* what) {
   return RPK_OK;
 }
 
-// rho_w - 1 of every column at both walls from the current (post-collision)
-// populations; precedes every pull when the walls are on.
-template <typename Store, typename Real>
-static rpk_status wall_launch(rpk_lattice* L, const StepConst<Real>& K) {
-  const int64_t n = 2 * (int64_t)L->grid.nx * L->grid.nz;
-  k_wall_rho<Store, Real><<<(unsigned)((n + 127) / 128), 128, 0, L->stream>>>(
+// Walls in use: kWallY and / or kWallX.
+static inline int wall_mask(const rpk_lattice* L) {
+  return (L->walls ? kWallY : 0) | (L->xwalls ? kWallX : 0);
+}
+
+// rho_w - 1 of every wall column from the current (post-collision)
+// populations; precedes every pull when walls are on.
+template <typename Store, typename Real, int kBC>
+static rpk_status wall_launch_t(rpk_lattice* L, const StepConst<Real>& K) {
+  const int64_t n = ((kBC & kWallY) ? 2 * (int64_t)L->grid.nx * L->grid.nz : 0) +
+                    ((kBC & kWallX) ? 2 * (int64_t)L->grid.ny * L->grid.nz : 0);
+  k_wall_rho<Store, Real, kBC><<<(unsigned)((n + 127) / 128), 128, 0, L->stream>>>(
       K, static_cast<const Store*>(L->pop[L->cur]), static_cast<const Real*>(L->ghost),
       static_cast<Real*>(L->wrho));
   return check_launch("k_wall_rho");
+}
+
+template <typename Store, typename Real>
+static rpk_status wall_launch(rpk_lattice* L, const StepConst<Real>& K) {
+  switch (wall_mask(L)) {
+    case kWallY: return wall_launch_t<Store, Real, kWallY>(L, K);
+    case kWallX: return wall_launch_t<Store, Real, kWallX>(L, K);
+    default: return wall_launch_t<Store, Real, kWallY | kWallX>(L, K);
+  }
 }
 
 template <typename Store, typename Real, bool kPull, int kBC>
@@ -81,7 +96,7 @@ static rpk_status collide_launch(rpk_lattice* L, const StepConst<Real>& K) {
   Store* pout = static_cast<Store*>(L->pop[L->cur ^ 1]);
   Real* ucur = static_cast<Real*>(L->u[L->steps & 1]);
   const Real* wcol = static_cast<const Real*>(L->wrho);
-  if constexpr (kBC != 2) {
+  if constexpr (kBC <= 1) {
     if (L->rot_mode) {
       k_collide<Store, Real, kPull, kBC, true><<<point_grid(L, 128), 128, 0, L->stream>>>(
           K, pin, pout, static_cast<const Real*>(L->e), static_cast<Real*>(L->e_star),
@@ -115,7 +130,7 @@ static rpk_status transport_launch(rpk_lattice* L, const StepConst<Real>& K) {
   const dim3 tgrid((unsigned)((L->grid.nx + kTBX - 1) / kTBX),
                    (unsigned)((L->grid.ny + kTBY - 1) / kTBY), (unsigned)(2 * L->grid.nz));
   RPK_CUDA(timing_begin(L));
-  if constexpr (kBC != 2) {
+  if constexpr (kBC <= 1) {
     if (L->rot_mode) {
       // paper mode: MacCormack on theta_R, FTCS sub-steps, the last with the
       // second relaxation half step (th holds the time-t theta_T)
@@ -151,25 +166,35 @@ template <typename Store, typename Real>
 rpk_status Ops<Store, Real>::step(rpk_lattice* L, int64_t n) {
   const StepConst<Real> K = make_const<Real>(L);
   const bool res = L->grid.bc_x == RPK_BC_RESERVOIR;
-  const bool walls = L->walls;
+  const int wm = wall_mask(L);
   for (int64_t t = 0; t < n; ++t) {
     rpk_status st;
     RPK_CUDA(timing_begin(L));
-    const bool wall_pull = walls && !L->streamed;
+    const bool wall_pull = wm && !L->streamed;
     if (wall_pull) {
       st = wall_launch<Store, Real>(L, K);
       if (st != RPK_OK) return st;
     }
     if (L->streamed)
       st = res ? collide_launch<Store, Real, false, 1>(L, K) : collide_launch<Store, Real, false, 0>(L, K);
-    else if (walls)
-      st = collide_launch<Store, Real, true, 2>(L, K);
+    else if (wm == kWallY)
+      st = collide_launch<Store, Real, true, kWallY>(L, K);
+    else if (wm == kWallX)
+      st = collide_launch<Store, Real, true, kWallX>(L, K);
+    else if (wm)
+      st = collide_launch<Store, Real, true, kWallY | kWallX>(L, K);
     else
       st = res ? collide_launch<Store, Real, true, 1>(L, K) : collide_launch<Store, Real, true, 0>(L, K);
     if (st != RPK_OK) return st;
     RPK_CUDA(timing_end(L, RPK_KC_COLLIDE, wall_pull ? 2 : 1));
-    st = walls ? transport_launch<Real, 2>(L, K)
-               : (res ? transport_launch<Real, 1>(L, K) : transport_launch<Real, 0>(L, K));
+    if (wm == kWallY)
+      st = transport_launch<Real, kWallY>(L, K);
+    else if (wm == kWallX)
+      st = transport_launch<Real, kWallX>(L, K);
+    else if (wm)
+      st = transport_launch<Real, kWallY | kWallX>(L, K);
+    else
+      st = res ? transport_launch<Real, 1>(L, K) : transport_launch<Real, 0>(L, K);
     if (st != RPK_OK) return st;
     L->cur ^= 1;
     L->streamed = false;
@@ -194,21 +219,32 @@ template <typename Store, typename Real>
 rpk_status Ops<Store, Real>::ghosts(rpk_lattice* L) {
   const StepConst<Real> K = make_const<Real>(L);
   const Real hdt = Real(0.5 * L->relax.dt / L->relax.tau1);
-  double* dst = L->diag_out;  // 12 doubles of staging (diag_out holds 16)
-  // reservoirs: their states; walls: rho = 1 at the wall's velocity, theta_T = theta_R = theta_w
-  double st12[12];
+  double* dst = L->diag_partial;  // 24 doubles of staging
+  // blocks 0, 1: the reservoirs' states or the y walls; blocks 2, 3: the x
+  // walls. A wall's state: rho = 1 at its velocity, theta_T = theta_R = theta_w.
+  double st24[24] = {0};
+  auto wall_state = [&](const double* wl, double* out6) {
+    const double s6[6] = {1.0, wl[0], wl[1], wl[2], wl[3], wl[3]};
+    for (int k = 0; k < 6; ++k) out6[k] = s6[k];
+  };
+  const double rest[4] = {0.0, 0.0, 0.0, kTheta0};  // fills blocks nothing reads
   if (L->walls) {
-    for (int w = 0; w < 2; ++w) {
-      const double* wl = L->wall + 4 * w;
-      const double s6[6] = {1.0, wl[0], wl[1], wl[2], wl[3], wl[3]};
-      for (int k = 0; k < 6; ++k) st12[6 * w + k] = s6[k];
-    }
+    wall_state(L->wall, st24);
+    wall_state(L->wall + 4, st24 + 6);
+  } else if (L->grid.bc_x == RPK_BC_RESERVOIR) {
+    for (int k = 0; k < 12; ++k) st24[k] = L->res[k];
   } else {
-    for (int k = 0; k < 12; ++k) st12[k] = L->res[k];
+    wall_state(rest, st24);
+    wall_state(rest, st24 + 6);
   }
-  RPK_CUDA(cudaMemcpyAsync(dst, st12, 12 * sizeof(double), cudaMemcpyHostToDevice, L->stream));
+  wall_state(L->xwalls ? L->xwall : rest, st24 + 12);
+  wall_state(L->xwalls ? L->xwall + 4 : rest, st24 + 18);
+  RPK_CUDA(cudaMemcpyAsync(dst, st24, 24 * sizeof(double), cudaMemcpyHostToDevice, L->stream));
   k_ghost<Real><<<1, 32, 0, L->stream>>>(K, hdt, dst, static_cast<Real*>(L->ghost));
   rpk_status st = check_launch("k_ghost");
+  if (st != RPK_OK) return st;
+  k_ghost<Real><<<1, 32, 0, L->stream>>>(K, hdt, dst + 12, static_cast<Real*>(L->ghost) + 2 * kGhostStride);
+  st = check_launch("k_ghost");
   if (st != RPK_OK) return st;
   RPK_CUDA(cudaStreamSynchronize(L->stream));
   return RPK_OK;
@@ -224,12 +260,19 @@ rpk_status Ops<Store, Real>::moments(rpk_lattice* L, double* rho, double* u, dou
   const Real* wcol = static_cast<const Real*>(L->wrho);
   const dim3 grid = point_grid(L, 128);
   const bool res = L->grid.bc_x == RPK_BC_RESERVOIR;
+  const int wm = wall_mask(L);
   if (L->streamed) {
     k_moments<Store, Real, false, 0><<<grid, 128, 0, L->stream>>>(K, pin, e, gh, rho, u, T, R, E, wcol);
-  } else if (L->walls) {
+  } else if (wm) {
     rpk_status st = wall_launch<Store, Real>(L, K);
     if (st != RPK_OK) return st;
-    k_moments<Store, Real, true, 2><<<grid, 128, 0, L->stream>>>(K, pin, e, gh, rho, u, T, R, E, wcol);
+    if (wm == kWallY)
+      k_moments<Store, Real, true, kWallY><<<grid, 128, 0, L->stream>>>(K, pin, e, gh, rho, u, T, R, E, wcol);
+    else if (wm == kWallX)
+      k_moments<Store, Real, true, kWallX><<<grid, 128, 0, L->stream>>>(K, pin, e, gh, rho, u, T, R, E, wcol);
+    else
+      k_moments<Store, Real, true, kWallY | kWallX><<<grid, 128, 0, L->stream>>>(K, pin, e, gh, rho, u, T, R,
+                                                                                E, wcol);
   } else if (res) {
     k_moments<Store, Real, true, 1><<<grid, 128, 0, L->stream>>>(K, pin, e, gh, rho, u, T, R, E, wcol);
   } else {
@@ -248,12 +291,21 @@ rpk_status Ops<Store, Real>::diag(rpk_lattice* L, double out[8]) {
   const int nblk = (int)std::max<int64_t>(1, std::min<int64_t>(kDiagBlocks, need));
   const Real* wcol = static_cast<const Real*>(L->wrho);
   const bool res = L->grid.bc_x == RPK_BC_RESERVOIR;
+  const int wm = wall_mask(L);
   if (L->streamed) {
     k_diag<Store, Real, false, 0><<<nblk, kDiagThreads, 0, L->stream>>>(K, pin, e, gh, L->diag_partial, wcol);
-  } else if (L->walls) {
+  } else if (wm) {
     rpk_status sw = wall_launch<Store, Real>(L, K);
     if (sw != RPK_OK) return sw;
-    k_diag<Store, Real, true, 2><<<nblk, kDiagThreads, 0, L->stream>>>(K, pin, e, gh, L->diag_partial, wcol);
+    if (wm == kWallY)
+      k_diag<Store, Real, true, kWallY><<<nblk, kDiagThreads, 0, L->stream>>>(K, pin, e, gh, L->diag_partial,
+                                                                               wcol);
+    else if (wm == kWallX)
+      k_diag<Store, Real, true, kWallX><<<nblk, kDiagThreads, 0, L->stream>>>(K, pin, e, gh, L->diag_partial,
+                                                                               wcol);
+    else
+      k_diag<Store, Real, true, kWallY | kWallX><<<nblk, kDiagThreads, 0, L->stream>>>(
+          K, pin, e, gh, L->diag_partial, wcol);
   } else if (res) {
     k_diag<Store, Real, true, 1><<<nblk, kDiagThreads, 0, L->stream>>>(K, pin, e, gh, L->diag_partial, wcol);
   } else {

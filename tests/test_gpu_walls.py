@@ -1,5 +1,5 @@
-"""Diffuse walls on the GPU (rpk_set_walls) against the FP64 oracle, and the
-paper's two wall experiments run on the GPU path (Sec. 6).
+"""Diffuse walls on the GPU (rpk_set_walls, rpk_set_x_walls) against the FP64
+oracle, and the paper's three wall experiments run on the GPU path (Sec. 6).
 
 Parity bars as for the periodic lattice: FP64 relative L-inf <= 1e-12 per
 field (rounding order differs), FP32 <= 1e-5 (u on the c_s scale). Sizes span
@@ -11,6 +11,10 @@ box, so the exact answer is the oracle's small run tiled back.
 E4 (startup Couette flow, Sec. 6): the paper's 128 x 64 x 8 grid, top wall
 started impulsively; u(y, t) against the printed series solution at diffusion
 times t* = nu t / L^2 = 0.02 ... 0.5.
+E5 (conduction in a square cavity, Sec. 6): 128 x 128 cells, walls on all four
+sides, the top one hotter by 0.1 theta0;
+the steady theta along the paper's lines x = 0.1L, 0.2L, 0.5L and
+y = 0.25L, 0.5L, 0.75L against the printed series.
 E6 (thermal Couette flow, Sec. 6): 128 points between the walls, walls at
 theta0 -+ dT/2, top wall at Mach 0.1, Ec = U0^2/(c_p dT) = 1,
 Pr = 0.75, 2.5, 5, 7.5, 10; the steady theta(y) against the printed profile
@@ -43,13 +47,21 @@ def rel(a, b, floor=1e-300):
     return float(np.abs(np.asarray(a) - np.asarray(b)).max() / max(np.abs(b).max(), floor))
 
 
-def run_pair(nx, ny, nz, f, relax, nsteps, precision="f64", walls=WALLS):
+XWALLS = ([0.0, 0.02, -0.01, T0 * 1.02], [0.0, -0.03, 0.02, T0 * 0.98])
+
+
+def run_pair(nx, ny, nz, f, relax, nsteps, precision="f64", walls=WALLS, xwalls=None):
     lat = rpk.Lattice(nx, ny, nz, precision=precision).set_relax(**relax)
-    lat.set_walls(*walls)
+    if walls is not None:
+        lat.set_walls(*walls)
+    if xwalls is not None:
+        lat.set_x_walls(*xwalls)
     lat.init_fields(f["rho"], f["u"], f["T"], f["R"])
     nsub = lat.info()["nsub"]
     P = O.make_params(relax["delta"], relax["tau"], relax["tau1"], relax.get("b", 0.0),
-                      relax.get("k_r", 0.0), 1.0, nsub, walls=list(walls[0]) + list(walls[1]))
+                      relax.get("k_r", 0.0), 1.0, nsub,
+                      walls=None if walls is None else list(walls[0]) + list(walls[1]),
+                      xwalls=None if xwalls is None else list(xwalls[0]) + list(xwalls[1]))
     S = O.State(P, nx, ny, nz).init_fields(f["rho"], f["u"], f["T"], f["R"])
     lat.step(nsteps)
     S.step(nsteps)
@@ -72,6 +84,64 @@ def test_f64_parity_with_walls(dims):
     assert abs(d["M"] - dr["M"]) <= 1e-12 * dr["M"]
     assert abs(d["E"] - dr["E"]) <= 1e-12 * dr["E"]
     assert d["status"] == 0
+
+
+@pytest.mark.parametrize("dims", [(12, 7, 3), (2, 5, 2), (137, 3, 2)])
+def test_f64_parity_with_x_walls(dims):
+    nx, ny, nz = dims
+    f = I.random_smooth(nx, ny, nz, T0, seed=31)
+    got, ref, lat, S = run_pair(nx, ny, nz, f, RELAX, 40, walls=None, xwalls=XWALLS)
+    check(got, ref, 1e-12)
+    assert abs(lat.diagnostics()["M"] - S.diag()["M"]) <= 1e-12 * S.diag()["M"]
+
+
+@pytest.mark.parametrize("dims", [(9, 10, 2), (130, 6, 1), (2, 2, 2)])
+def test_f64_parity_with_walls_on_x_and_y(dims):
+    nx, ny, nz = dims
+    f = I.random_smooth(nx, ny, nz, T0, seed=32)
+    got, ref, lat, S = run_pair(nx, ny, nz, f, RELAX, 40, xwalls=XWALLS)
+    check(got, ref, 1e-12)
+    d, dr = lat.diagnostics(), S.diag()
+    assert abs(d["M"] - dr["M"]) <= 1e-12 * dr["M"]
+    assert abs(d["E"] - dr["E"]) <= 1e-12 * dr["E"]
+    assert d["status"] == 0
+
+
+def test_f32_parity_with_walls_on_x_and_y():
+    nx, ny, nz = 24, 20, 3
+    f = I.random_smooth(nx, ny, nz, T0, seed=33, amp=2e-3, aniso_R=2e-3)
+    got, ref, _, _ = run_pair(nx, ny, nz, f, RELAX, 300, precision="f32", xwalls=XWALLS)
+    check(got, ref, 1e-5, keys=("rho", "u", "T", "Erot"))
+
+
+def test_four_walls_fixed_point_mass_and_checkpoint(tmp_path):
+    u = [0.0, 0.0, 0.03]
+    w = u + [0.31]
+    lat = rpk.Lattice(5, 4, 3, precision="f64").set_relax(**RELAX).set_walls(w, w).set_x_walls(w, w)
+    f = I.uniform(5, 4, 3, 0.31, rho=1.1, u=u)
+    lat.init_fields(f["rho"], f["u"], f["T"], f["R"])
+    a = lat.read_moments()
+    lat.step(7)
+    b = lat.read_moments()
+    for k in ("rho", "u", "T", "R"):
+        assert np.abs(b[k] - a[k]).max() < 1e-13, k
+    nx, ny, nz = 12, 10, 4
+    f = I.random_smooth(nx, ny, nz, T0, seed=34)
+    lat = rpk.Lattice(nx, ny, nz, precision="f64").set_relax(**RELAX)
+    lat.set_walls(*WALLS).set_x_walls(*XWALLS)
+    lat.init_fields(f["rho"], f["u"], f["T"], f["R"])
+    m0 = lat.diagnostics()["M"]
+    lat.step(1000)
+    assert abs(lat.diagnostics()["M"] - m0) <= 1e-12 * m0
+    path = str(tmp_path / "four.ckpt")
+    lat.save(path)
+    lat.step(9)
+    other = rpk.Lattice(nx, ny, nz, precision="f64")
+    other.load(path)
+    other.step(9)
+    ma, mb = lat.read_moments(), other.read_moments()
+    for k in ("rho", "u", "T", "R"):
+        assert np.array_equal(ma[k], mb[k]), k
 
 
 def test_f64_parity_with_walls_auto_nsub_and_strong_rotational_conduction():
@@ -170,6 +240,14 @@ def test_wall_argument_errors():
     lat.set_rot_mode("paper")
     with pytest.raises(rpk.RpkError):
         lat.set_walls(*WALLS)
+    with pytest.raises(rpk.RpkError):
+        lat.set_x_walls(*XWALLS)
+    with pytest.raises(rpk.RpkError):
+        rpk.Lattice(1, 4, 2).set_relax(**RELAX).set_x_walls(*XWALLS)     # nx < 2
+    with pytest.raises(rpk.RpkError):
+        rpk.Lattice(4, 4, 2, bc_x="reservoir").set_relax(**RELAX).set_x_walls(*XWALLS)
+    with pytest.raises(rpk.RpkError):
+        rpk.Lattice(4, 4, 2).set_relax(**RELAX).set_x_walls([0.01, 0, 0, T0], [0, 0, 0, T0])
 
 
 # ---------------------------------------------------------------------------
@@ -236,4 +314,62 @@ def test_e6_thermal_couette_profile(Pr):
     err = float(np.abs(got - exact).max() / exact.max())
     print("E6 Pr %g: max |theta - exact| / max exact = %.4f" % (Pr, err))
     assert err < 0.03, (Pr, err)
+    assert lat.diagnostics()["status"] == 0
+
+
+# ---------------------------------------------------------------------------
+# E5: conduction in a square cavity heated from the top (Sec. 6)
+
+
+def _cavity_series(xi, eta, nmax=399):
+    """(T - T0)/(T1 - T0) = (2/pi) sum_n ((-1)^(n+1) + 1)/n sin(n pi xi)
+    sinh(n pi eta)/sinh(n pi) (Sec. 6), the sinh ratio written with
+    exponentials."""
+    n = np.arange(1, nmax + 1, 2)[:, None]  # only odd n contribute (factor 2)
+    ratio = np.exp(n * np.pi * (eta - 1)) * (1 - np.exp(-2 * n * np.pi * eta)) / (1 - np.exp(-2 * n * np.pi))
+    return (2 / np.pi) * np.sum(2.0 / n * np.sin(n * np.pi * xi) * ratio, axis=0)
+
+
+def test_e5_heated_cavity_conduction_follows_the_series_solution():
+    n, nu, Pr = 128, 0.2, 0.71
+    dT = 0.1 * T0
+    eta_, etaB, kap = rpk.gas_from_nondim(1.4, nu, 0.6, Pr)
+    lat = rpk.Lattice(n, n, 1, precision="f32").set_gas(1.4, eta_, etaB, kap)
+    cold = [0.0, 0.0, 0.0, T0]
+    lat.set_walls(cold, [0.0, 0.0, 0.0, T0 + dT]).set_x_walls(cold, cold)
+    f = I.uniform(n, n, 1, T0)
+    lat.init_fields(f["rho"], f["u"], f["T"], f["R"])
+    lat.step(int(0.8 * n * n / (nu / Pr)))
+    m = lat.read_moments()
+    th = (3 * m["T"] + 2 * m["R"]) / 5
+    X = I.positions(n, n, 1)
+    xi, eta = (X[0] + 0.25) / n, (X[1] + 0.25) / n
+    got = (th - T0) / dT
+    ref = _cavity_series(xi, eta)
+    lines = (("x=0.1L", np.abs(xi - 0.1) < 0.5 / n), ("x=0.2L", np.abs(xi - 0.2) < 0.5 / n),
+             ("x=0.5L", np.abs(xi - 0.5) < 0.5 / n), ("y=0.25L", np.abs(eta - 0.25) < 0.5 / n),
+             ("y=0.5L", np.abs(eta - 0.5) < 0.5 / n), ("y=0.75L", np.abs(eta - 0.75) < 0.5 / n))
+    full, away = {}, {}
+    for name, sel in lines:
+        assert sel.sum() >= n // 2, name
+        full[name] = float(np.abs(got[sel] - ref[sel]).max())
+        sel = sel & (eta <= 0.9)
+        away[name] = float(np.abs(got[sel] - ref[sel]).max())
+    umax = float(np.abs(m["u"]).max())
+    print("E5 max |(T - T0)/dT - series| along the paper's lines:", full,
+          "; below 0.9 L:", away, "; max |u| / c_s = %.2e" % (umax / CS))
+    # Measured: 1.4% of dT below 0.9 L and 1.75% on the full lines (x = 0.1L,
+    # next to the hot corner). The series is the linear, continuum answer. Two
+    # effects separate the lattice gas from it: (i) the lattice conductivity
+    # depends on theta at O(theta - theta0) (the third-order equilibrium's
+    # energy flux is exact only to first order in theta - theta0), so with
+    # dT = 0.1 theta0 the profile bends away from the harmonic one -- with dT =
+    # 0.01 theta0 the FP64 oracle's interior error at 32 x 32 falls from 1-2% to
+    # below 0.5%; (ii) next to the heated wall and its singular corners the gas
+    # stays colder than the wall (the oracle at 32 x 32: -1.5% at 0.9 L and
+    # -4.4% at 0.96 L on x = 0.1L), shrinking with L. The thermal creep along
+    # the walls near the corners stays below 1% of c_s.
+    assert max(away.values()) < 0.02, away
+    assert max(full.values()) < 0.025, full
+    assert umax < 1e-2 * CS
     assert lat.diagnostics()["status"] == 0
