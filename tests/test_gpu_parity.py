@@ -135,6 +135,51 @@ def test_f64_sod_400_steps():
     assert_fields(got, ref, 1e-12)
 
 
+@pytest.mark.parametrize("kind", ["periodic", "reservoir", "walls"])
+def test_f64_parity_single_ftcs_sub_step_with_reads_and_checkpoint(kind, tmp_path):
+    """nsub = 1 (the benchmark's setting) for each boundary kind, with moment
+    reads, diagnostics and a checkpoint between the steps: the run equals the
+    oracle's uninterrupted run, and a restart from the checkpoint is bitwise
+    the continued run."""
+    relax = dict(RELAX, nsub=1)
+    nx, ny, nz = (40, 6, 3) if kind != "reservoir" else (300, 1, 1)
+    f = I.random_smooth(nx, ny, nz, T0, seed=41)
+    res = None
+    lat = rpk.Lattice(nx, ny, nz, precision="f64", bc_x="reservoir" if kind == "reservoir" else "periodic")
+    lat.set_relax(**relax)
+    walls, xwalls = None, None
+    if kind == "reservoir":
+        res = np.array([1.02, 0.01, 0, 0, T0, T0 * 1.01, 0.98, -0.01, 0, 0, T0 * 0.99, T0], float)
+        lat.set_reservoirs(res)
+    if kind == "walls":
+        walls = [0.02, 0, 0, T0 * 1.02, -0.01, 0, 0.01, T0 * 0.98]
+        xwalls = [0, 0.01, 0, T0, 0, 0, -0.02, T0 * 1.01]
+        lat.set_walls(walls[:4], walls[4:]).set_x_walls(xwalls[:4], xwalls[4:])
+    lat.init_fields(f["rho"], f["u"], f["T"], f["R"])
+    assert lat.info()["nsub"] == 1
+    P = O.make_params(relax["delta"], relax["tau"], relax["tau1"], relax["b"], relax["k_r"], 1.0, 1,
+                      1 if kind == "reservoir" else 0, walls=walls, xwalls=xwalls)
+    S = O.State(P, nx, ny, nz, reservoirs=res).init_fields(f["rho"], f["u"], f["T"], f["R"])
+    lat.step(7)
+    S.step(7)
+    assert_fields(lat.read_moments(), S.fields(), 1e-12)
+    lat.step(6)
+    d = lat.diagnostics()
+    path = str(tmp_path / "folded.ckpt")
+    lat.save(path)
+    lat.step(5)
+    S.step(11)
+    assert_fields(lat.read_moments(), S.fields(), 1e-12)
+    assert abs(d["M"] - O.State(P, nx, ny, nz, reservoirs=res).init_fields(
+        f["rho"], f["u"], f["T"], f["R"]).step(13).diag()["M"]) <= 1e-12 * d["M"]
+    other = rpk.Lattice(nx, ny, nz, precision="f64", bc_x="reservoir" if kind == "reservoir" else "periodic")
+    other.load(path)
+    other.step(5)
+    a, b = lat.read_moments(), other.read_moments()
+    for k in ("rho", "u", "T", "R"):
+        assert np.array_equal(a[k], b[k]), k
+
+
 def test_f64_conservation_1000_steps():
     nx, ny, nz = 16, 8, 6
     f = I.random_smooth(nx, ny, nz, T0, seed=3)
