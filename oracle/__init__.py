@@ -256,9 +256,9 @@ class State:
                               _ptr(self.g), _ptr(self.Er), _ptr(self.uprev), int(n))
         if rc == 2:
             raise ValueError("unsupported setting: the backward-Euler diffusion variant needs "
-                             "ny = nz = 1 and bcx = 1; walls need at least 2 cells across, "
-                             "zero normal wall velocity, no x reservoirs and the conservative "
-                             "rotational form")
+                             "ny = nz = 1, bcx = 1 and the conservative rotational form; walls "
+                             "need at least 2 cells across, zero normal wall velocity, no x "
+                             "reservoirs and no backward-Euler variant")
         if rc != 0:
             raise MemoryError("oracle step could not allocate its work arrays")
         self.t += int(n)

@@ -511,7 +511,8 @@ static void make_ghost(const ora_params *P, const double *st, ghost *gh)
  * diffusive flux through the wall face of point p is
  * kappa_R(p) (theta_w - theta_R(p)) / d, d the distance from p to the wall
  * (1/4 or 3/4), and the advective flux through a wall is zero (the walls slide
- * tangentially: uy = 0).
+ * tangentially: uy = 0). In the paper's theta_R mode the same Dirichlet value
+ * enters through wall_ghost in the advection differences and the Laplacian.
  */
 
 /* Index along axis a (not wrapped) of the destination of population i leaving
@@ -539,6 +540,18 @@ static long wall_slot(const grid *G, int w, int x, int y, int z)
     const long ny_cols = (long)G->nx * G->nz, nx_cols = (long)G->ny * G->nz;
     if (w < 2) return w * ny_cols + (long)z * G->nx + x;
     return 2 * ny_cols + (w - 2) * nx_cols + (long)z * G->ny + y;
+}
+
+/* Paper mode: theta_R on the axis neighbour beyond the wall of code q (<= -3)
+ * of point p, given theta_R(p) = thp: the straight line through theta_w at the
+ * wall (distance d from p), so that differences across the wall face see the
+ * Dirichlet value theta_R = theta_w as the conservative form's flux does. */
+static double wall_ghost(const ora_params *P, const grid *G, long p, long q, double thp)
+{
+    const int w = (int)(-3 - q), side = w & 1, s = (int)(p / G->n3);
+    const double *wl = (w < 2) ? P->wall : P->xwall;
+    const double d = wall_distance(s, side), thw = wl[4 * side + 3];
+    return thw + (thw - thp) * (1.0 - d) / d;
 }
 
 /* rw[wall_slot(w, ...)]: rho_w of wall w for each of its columns, from the
@@ -683,10 +696,9 @@ int ora_step(const ora_params *P, int nx, int ny, int nz, const double *res, dou
     }
     need_lattice();
     if ((P->diff == 1 && (ny != 1 || nz != 1 || P->bcx != 1)) || (P->diff == 1 && P->rot_mode == 1) ||
-        (P->bcy == 1 && (ny < 2 || P->bcx == 1 || P->rot_mode == 1 || P->diff == 1 ||
+        (P->bcy == 1 && (ny < 2 || P->bcx == 1 || P->diff == 1 ||
                          P->wall[1] != 0.0 || P->wall[5] != 0.0)) ||
-        (P->bcx == 2 && (nx < 2 || P->rot_mode == 1 || P->diff == 1 ||
-                         P->xwall[0] != 0.0 || P->xwall[4] != 0.0))) {
+        (P->bcx == 2 && (nx < 2 || P->diff == 1 || P->xwall[0] != 0.0 || P->xwall[4] != 0.0))) {
         free(gs); free(rho); free(u); free(kap); free(Ep); free(Ec); free(th); free(v); free(Tt);
         free(rw);
         return 2;
@@ -750,7 +762,8 @@ int ora_step(const ora_params *P, int nx, int ny, int nz, const double *res, dou
                 double adv = 0.0;
                 for (a = 0; a < 3; a++) {
                     long qf = axis_nb(P, &G, p, a, +1);
-                    double Rq = (qf >= 0) ? Er[qf] : gh[-1 - qf].Er;
+                    double Rq = (qf >= 0) ? Er[qf]
+                                : (qf >= -2) ? gh[-1 - qf].Er : wall_ghost(P, &G, p, qf, Er[p]);
                     adv += u[a * N + p] * (Rq - Er[p]);
                 }
                 Ep[p] = Er[p] - P->dt * adv;
@@ -759,7 +772,8 @@ int ora_step(const ora_params *P, int nx, int ny, int nz, const double *res, dou
                 double adv = 0.0;
                 for (a = 0; a < 3; a++) {
                     long qb = axis_nb(P, &G, p, a, -1);
-                    double Rq = (qb >= 0) ? Ep[qb] : gh[-1 - qb].Er;
+                    double Rq = (qb >= 0) ? Ep[qb]
+                                : (qb >= -2) ? gh[-1 - qb].Er : wall_ghost(P, &G, p, qb, Ep[p]);
                     adv += u[a * N + p] * (Ep[p] - Rq);
                 }
                 Ec[p] = 0.5 * (Er[p] + Ep[p] - P->dt * adv);
@@ -772,8 +786,10 @@ int ora_step(const ora_params *P, int nx, int ny, int nz, const double *res, dou
                     double lap = 0.0;
                     for (a = 0; a < 3; a++) {
                         long qp = axis_nb(P, &G, p, a, +1), qm = axis_nb(P, &G, p, a, -1);
-                        double Rp = (qp >= 0) ? Er[qp] : gh[-1 - qp].Er;
-                        double Rm = (qm >= 0) ? Er[qm] : gh[-1 - qm].Er;
+                        double Rp = (qp >= 0) ? Er[qp]
+                                    : (qp >= -2) ? gh[-1 - qp].Er : wall_ghost(P, &G, p, qp, Er[p]);
+                        double Rm = (qm >= 0) ? Er[qm]
+                                    : (qm >= -2) ? gh[-1 - qm].Er : wall_ghost(P, &G, p, qm, Er[p]);
                         lap += Rp - 2.0 * Er[p] + Rm;
                     }
                     Ec[p] = Er[p] + h * 2.0 * kap[p] / (rho[p] * P->delta) * lap;

@@ -14,6 +14,7 @@ condition the paper cites for its Sec. 6 Couette and cavity flows):
   * thermal Couette flow (Sec. 6) shows the viscous heating of the printed
     profile;
   * conduction in the square cavity (Sec. 6) follows the printed series;
+  * the paper's theta_R solver keeps these properties between the walls;
   * with walls on x and y the corner entries follow a brute-force count
     (the y walls own what crosses both), the state equal to all four walls is
     fixed and mass is conserved;
@@ -28,11 +29,11 @@ from oracle import params as PM
 T0 = O.THETA0
 
 
-def _params(nu=0.1, lam=0.6, Pr=0.71, walls=None, kr=None, xwalls=None):
+def _params(nu=0.1, lam=0.6, Pr=0.71, walls=None, kr=None, xwalls=None, rot_mode=0):
     d, tau, tau1, b, k_r = PM.relax_from_gas(1.4, *PM.gas_from_nondim(1.4, nu, lam, Pr), 0.0)
     if kr is not None:
         k_r = kr
-    return O.make_params(d, tau, tau1, b, k_r, 1.0, 1, walls=walls, xwalls=xwalls)
+    return O.make_params(d, tau, tau1, b, k_r, 1.0, 1, rot_mode=rot_mode, walls=walls, xwalls=xwalls)
 
 
 def _state(P, nx, ny, nz, f):
@@ -150,7 +151,7 @@ def pin_couette(times=(0.1, 0.2, 0.5)):
     return errs
 
 
-def pin_conduction(kr=None):
+def pin_conduction(kr=None, rot_mode=0):
     """steady conduction between walls at theta0 -+ eps (linear regime), from
     straight-line fits of theta on each sublattice in the interior: the mean
     slope against 2 eps theta0 / L, the mean value at mid-channel, the
@@ -158,7 +159,7 @@ def pin_conduction(kr=None):
     theta_R| in the interior, all in units of eps theta0."""
     ny, nu, Pr, eps = 16, 0.1, 0.71, 2e-4
     dT = eps * T0
-    P = _params(nu=nu, Pr=Pr, walls=[0, 0, 0, T0 - dT, 0, 0, 0, T0 + dT], kr=kr)
+    P = _params(nu=nu, Pr=Pr, walls=[0, 0, 0, T0 - dT, 0, 0, 0, T0 + dT], kr=kr, rot_mode=rot_mode)
     S = _state(P, 1, ny, 1, I.uniform(1, ny, 1, T0))
     L = ny
     S.step(int(3 * L * L / (nu / Pr)))
@@ -175,7 +176,7 @@ def pin_conduction(kr=None):
     return slope * L / 2, 0.5 * (at[0] + at[1]), at[0] - at[1], TR
 
 
-def pin_transpose():
+def pin_transpose(rot_mode=0):
     """A run with walls normal to x equals the transposed run with walls normal
     to y (x <-> y is a symmetry of the lattice and of every step), 10 steps of
     a random 3-D state. Returns the largest field difference."""
@@ -194,8 +195,8 @@ def pin_transpose():
     perm = idx.transpose(0, 1, 3, 2).reshape(-1)      # B point order -> A point index
     fb = {k: (v[..., perm].copy()) for k, v in fa.items()}
     fb["u"] = fb["u"][[1, 0, 2]]
-    A = _state(_params(xwalls=xw), nxa, nya, nz, fa).step(10).fields()
-    B = _state(_params(walls=yw), nya, nxa, nz, fb).step(10).fields()
+    A = _state(_params(xwalls=xw, rot_mode=rot_mode), nxa, nya, nz, fa).step(10).fields()
+    B = _state(_params(walls=yw, rot_mode=rot_mode), nya, nxa, nz, fb).step(10).fields()
     err = max(float(np.abs(B[k] - A[k][perm]).max()) for k in ("rho", "T", "R", "Erot"))
     return max(err, float(np.abs(B["u"] - A["u"][[1, 0, 2]][:, perm]).max()))
 
@@ -255,13 +256,13 @@ def pin_corners():
     return err
 
 
-def pin_all_walls_fixed_and_mass():
+def pin_all_walls_fixed_and_mass(rot_mode=0):
     """All four walls sliding along z at the fluid's velocity and temperature:
     the uniform state is fixed; then mass is conserved with four different
     walls on a random 3-D state."""
     u = [0, 0, 0.03]
     w = u + [0.31]
-    P = _params(walls=w + w, xwalls=w + w)
+    P = _params(walls=w + w, xwalls=w + w, rot_mode=rot_mode)
     f = I.uniform(4, 5, 2, 0.31, rho=1.1, u=u)
     S = _state(P, 4, 5, 2, f)
     F0 = S.fields()
@@ -272,7 +273,7 @@ def pin_all_walls_fixed_and_mass():
     nx, ny, nz = 5, 4, 2
     n = 2 * nx * ny * nz
     P = _params(walls=[0.02, 0, 0, 0.28, -0.03, 0, 0.01, 0.31],
-                xwalls=[0, 0.01, 0.02, 0.30, 0, -0.02, 0, 0.29])
+                xwalls=[0, 0.01, 0.02, 0.30, 0, -0.02, 0, 0.29], rot_mode=rot_mode)
     f = I.uniform(nx, ny, nz, T0)
     f["rho"] = 1 + 0.05 * rng.uniform(-1, 1, n)
     f["u"] = 0.03 * rng.uniform(-1, 1, (3, n))
@@ -402,6 +403,18 @@ def test_square_cavity_conduction_follows_the_series():
     assert v < 0.025 and h < 0.025, (v, h)
 
 
+def test_paper_mode_between_walls():
+    """The paper's theta_R solver (rot_mode = 1) between the same walls: the
+    state equal to all four walls is fixed, mass is conserved, x walls equal
+    the transposed y-wall run, and steady conduction is linear with theta_T =
+    theta_R in the interior."""
+    fixed, dm = pin_all_walls_fixed_and_mass(rot_mode=1)
+    assert fixed < 1e-13 and dm < 1e-13, (fixed, dm)
+    assert pin_transpose(rot_mode=1) < 1e-12
+    r = pin_conduction(rot_mode=1)
+    assert _conduction_ok(*r), r
+
+
 # planted mistakes in the wall code: (name, original, mistake, pin that must fail)
 WALL_MUTANTS = [
     ("no mass balance", "rw[k] = (in[k] > 0.0) ? out[k] / in[k] : 0.0;",
@@ -419,10 +432,13 @@ WALL_MUTANTS = [
      "for (a = 0; a < 9; a++) Lam[a] = (a % 4 == 0) ? THETA0 : 0.0;", "fixed"),
     ("corner leaving owned by the x wall", "if (P->bcy == 1 && yd < 0) wo = 0;",
      "if (P->bcy == 1 && yd < 0 && !(P->bcx == 2 && xd < 0)) wo = 0;", "corners"),
-    ("x wall ghost on the y-wall temperatures", "const double *wl = (w < 2) ? P->wall : P->xwall;",
-     "const double *wl = P->wall;", "transpose"),
+    ("x wall ghost on the y-wall temperatures",
+     "                        const double *wl = (w < 2) ? P->wall : P->xwall;",
+     "                        const double *wl = P->wall;", "transpose"),
     ("x walls emit from the y walls' columns", "return 2 * ny_cols + (w - 2) * nx_cols + (long)z * G->ny + y;",
      "return 2 * ny_cols + (w - 2) * nx_cols + (long)z * G->ny + x % G->ny;", "corners"),
+    ("paper-mode wall ghost at the wall's own temperature", "    return thw + (thw - thp) * (1.0 - d) / d;\n}",
+     "    return thw + 0.0 * (thw - thp) * (1.0 - d) / d;\n}", "paper conduction"),
 ]
 
 
@@ -438,6 +454,8 @@ def _fails(pin):
         return not pin_corners() < 1e-15
     if pin == "transpose":
         return not pin_transpose() < 1e-12
+    if pin == "paper conduction":
+        return not _conduction_ok(*pin_conduction(rot_mode=1))
     return not _conduction_ok(*pin_conduction())
 
 
