@@ -170,10 +170,11 @@ rpk_status rpk_set_rot_mode(rpk_lattice* lat, int mode);
  *   column through it in the same step: mass is conserved to round-off.
  *   Rotational energy: Dirichlet theta_R = theta_w; the diffusive flux through
  *   the wall face of a point at distance d (1/4 or 3/4) from the wall is
- *   kappa_R(p)(theta_w - theta_R(p))/d; no advective flux through a wall.
- * Requires ny >= 2, bc_x = RPK_BC_PERIODIC and rotational mode 0
- * (RPK_ERR_STATE otherwise; rpk_set_rot_mode(1) is refused while walls are
- * on). Takes effect at the next step or moment read; the automatic nsub of
+ *   kappa_R(p)(theta_w - theta_R(p))/d; no advective flux through a wall. In
+ *   rotational mode 1 the same Dirichlet value enters the advection
+ *   differences and the Laplacian as the straight line through theta_w.
+ * Requires ny >= 2 and bc_x = RPK_BC_PERIODIC (RPK_ERR_STATE otherwise).
+ * Takes effect at the next step or moment read; the automatic nsub of
  * rpk_init_fields accounts for the stiffer near-wall diffusion (one face with
  * coefficient 4 kappa_R) and for the wall temperatures. Checkpoints record the
  * walls. Synchronises the lattice's stream. */
@@ -184,9 +185,9 @@ rpk_status rpk_set_walls(rpk_lattice* lat, const double* walls8);
  * high-x wall (ux must be 0; theta > 0); NULL makes x periodic again. With
  * walls on both axes, a population whose pull source lies beyond a y wall and
  * an x wall (a corner) is emitted by the y wall, and each x wall balances the
- * mass of the entries the y walls leave to it. Requires nx >= 2,
- * bc_x = RPK_BC_PERIODIC (the x walls take the reservoirs' place) and
- * rotational mode 0; otherwise as rpk_set_walls. */
+ * mass of the entries the y walls leave to it. Requires nx >= 2 and
+ * bc_x = RPK_BC_PERIODIC (the x walls take the reservoirs' place); otherwise
+ * as rpk_set_walls. */
 rpk_status rpk_set_x_walls(rpk_lattice* lat, const double* walls8);
 
 /* Initial state from hydrodynamic fields (layout above): rho > 0, u (3

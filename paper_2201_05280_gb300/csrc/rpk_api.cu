@@ -288,7 +288,6 @@ rpk_status rpk_set_walls(rpk_lattice* L, const double* w) {
   }
   if (L->grid.ny < 2) return fail(RPK_ERR_STATE, "walls need ny >= 2");
   if (L->grid.bc_x != RPK_BC_PERIODIC) return fail(RPK_ERR_STATE, "walls need a periodic x boundary");
-  if (L->rot_mode != 0) return fail(RPK_ERR_STATE, "walls need the conservative rotational form (mode 0)");
   if (!L->relax_ok) return fail(RPK_ERR_STATE, "set the relaxation parameters first");
   for (int k = 0; k < 8; ++k)
     if (!std::isfinite(w[k])) return fail(RPK_ERR_PARAM, "wall state not finite");
@@ -308,7 +307,6 @@ rpk_status rpk_set_x_walls(rpk_lattice* L, const double* w) {
   }
   if (L->grid.nx < 2) return fail(RPK_ERR_STATE, "x walls need nx >= 2");
   if (L->grid.bc_x != RPK_BC_PERIODIC) return fail(RPK_ERR_STATE, "x walls replace the x reservoirs: use bc_x = periodic");
-  if (L->rot_mode != 0) return fail(RPK_ERR_STATE, "walls need the conservative rotational form (mode 0)");
   if (!L->relax_ok) return fail(RPK_ERR_STATE, "set the relaxation parameters first");
   for (int k = 0; k < 8; ++k)
     if (!std::isfinite(w[k])) return fail(RPK_ERR_PARAM, "wall state not finite");
@@ -324,11 +322,9 @@ rpk_status rpk_set_rot_mode(rpk_lattice* L, int mode) {
   if (!L) return fail(RPK_ERR_ARG, "lattice is NULL");
   if (mode != 0 && mode != 1) return fail(RPK_ERR_ARG, "mode must be 0 (conservative) or 1 (paper)");
   if (mode == L->rot_mode) return RPK_OK;
-  if (mode == 1 && (L->walls || L->xwalls))
-    return fail(RPK_ERR_STATE, "the paper-mode solver has no wall boundary");
   L->rot_mode = mode;
   L->init_ok = false;  // the stored rotational state changes meaning: initialise again
-  if (L->res_ok) {
+  if (L->res_ok || L->walls || L->xwalls) {
     cudaError_t err = cudaSetDevice(L->device);
     if (err != cudaSuccess) return cuda_fail(err, "cudaSetDevice");
     return with_ops(L->grid.precision, [&](auto ops) { return decltype(ops)::ghosts(L); });
@@ -564,8 +560,8 @@ rpk_status rpk_load(rpk_lattice* L, const char* path) {
   rpk_status st = RPK_OK;
   if (fread(&h, sizeof(h), 1, f) != 1 || std::memcmp(h.magic, "RPKCKPT4", 8) != 0)
     st = fail(RPK_ERR_IO, "not a checkpoint");
-  else if ((h.walls && (h.rot_mode != 0 || h.bc_x != RPK_BC_PERIODIC || h.ny < 2)) ||
-           (h.xwalls && (h.rot_mode != 0 || h.bc_x != RPK_BC_PERIODIC || h.nx < 2)))
+  else if ((h.walls && (h.bc_x != RPK_BC_PERIODIC || h.ny < 2)) ||
+           (h.xwalls && (h.bc_x != RPK_BC_PERIODIC || h.nx < 2)))
     st = fail(RPK_ERR_IO, "inconsistent checkpoint");
   else if (h.rot_mode != L->rot_mode)
     st = fail(RPK_ERR_ARG, "checkpoint rotational mode differs from the lattice (rpk_set_rot_mode)");

@@ -102,13 +102,18 @@ __device__ __forceinline__ const Real* ghost_block(const Real* __restrict__ ghos
 // 3/4 otherwise), written as the value theta_w + (theta_w - theta_p)(1 - d)/d
 // on the axis neighbour (whose face coefficient is then kappa_R(p)).
 template <typename Real>
+__device__ __forceinline__ Real wall_line(Real thw, int64_t q, int s, Real thp) {
+  const bool low = (q == -3 || q == -5);
+  const Real r = (low == (s == 0)) ? Real(3) : Real(1.0 / 3.0);
+  return thw + (thw - thp) * r;
+}
+
+template <typename Real>
 __device__ __forceinline__ Real wall_theta(const StepConst<Real>& K, const Real* __restrict__ g,
                                            int64_t q, int s, Real thp) {
   const Real thw = (Real(2) * g[kGhE] - K.delta * K.theta0 * g[kGhDrho]) /
                    (K.delta * (Real(1) + g[kGhDrho]));
-  const bool low = (q == -3 || q == -5);
-  const Real r = (low == (s == 0)) ? Real(3) : Real(1.0 / 3.0);
-  return thw + (thw - thp) * r;
+  return wall_line(thw, q, s, thp);
 }
 
 // advecting velocity: second-order extrapolation to t + dt/2
@@ -281,12 +286,17 @@ __global__ void __launch_bounds__(kTBX * kTBY)
 //   k_pm_ftcs  FTCS sub-step of (2/(rho delta)) kappa_R lap theta_R; the last
 //              sub-step also applies step 4, the second half step with the
 //              stored time-t theta_T
+// theta_R - theta0 of the axis neighbour (a, d) in the array r; beyond a
+// reservoir its table value, beyond a wall the straight line through the
+// wall's theta_R (its table entry holds theta_R - theta0 in this mode) at the
+// wall's distance, extrapolated from r at the point itself.
 template <typename Real, int kBC>
 __device__ __forceinline__ Real pm_nb(const StepConst<Real>& K, const PointIdx& P, const Real* __restrict__ r,
                                       const Real* __restrict__ ghost, int a, int d) {
-  static_assert(kBC <= 1, "the paper-mode solver has no wall boundary");
   const int64_t q = axis_nb<kBC>(K, P, a, d);
   if (kBC == 1 && q < 0) return ghost[(q == -1 ? 0 : kGhostStride) + kGhE];
+  if ((kBC & (kWallX | kWallY)) && q < 0)
+    return wall_line(ghost_block(ghost, q)[kGhE], q, P.s, r[(int64_t)P.s * K.n3 + P.cell]);
   return r[q];
 }
 

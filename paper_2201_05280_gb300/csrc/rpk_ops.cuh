@@ -96,14 +96,12 @@ static rpk_status collide_launch(rpk_lattice* L, const StepConst<Real>& K) {
   Store* pout = static_cast<Store*>(L->pop[L->cur ^ 1]);
   Real* ucur = static_cast<Real*>(L->u[L->steps & 1]);
   const Real* wcol = static_cast<const Real*>(L->wrho);
-  if constexpr (kBC <= 1) {
-    if (L->rot_mode) {
-      k_collide<Store, Real, kPull, kBC, true><<<point_grid(L, 128), 128, 0, L->stream>>>(
-          K, pin, pout, static_cast<const Real*>(L->e), static_cast<Real*>(L->e_star),
-          static_cast<Real*>(L->drho), ucur, static_cast<Real*>(L->kap),
-          static_cast<const Real*>(L->ghost), L->status, static_cast<Real*>(L->thbuf), wcol);
-      return check_launch("k_collide");
-    }
+  if (L->rot_mode) {
+    k_collide<Store, Real, kPull, kBC, true><<<point_grid(L, 128), 128, 0, L->stream>>>(
+        K, pin, pout, static_cast<const Real*>(L->e), static_cast<Real*>(L->e_star),
+        static_cast<Real*>(L->drho), ucur, static_cast<Real*>(L->kap),
+        static_cast<const Real*>(L->ghost), L->status, static_cast<Real*>(L->thbuf), wcol);
+    return check_launch("k_collide");
   }
   k_collide<Store, Real, kPull, kBC, false><<<point_grid(L, 128), 128, 0, L->stream>>>(
       K, pin, pout, static_cast<const Real*>(L->e), static_cast<Real*>(L->e_star),
@@ -130,22 +128,20 @@ static rpk_status transport_launch(rpk_lattice* L, const StepConst<Real>& K) {
   const dim3 tgrid((unsigned)((L->grid.nx + kTBX - 1) / kTBX),
                    (unsigned)((L->grid.ny + kTBY - 1) / kTBY), (unsigned)(2 * L->grid.nz));
   RPK_CUDA(timing_begin(L));
-  if constexpr (kBC <= 1) {
-    if (L->rot_mode) {
-      // paper mode: MacCormack on theta_R, FTCS sub-steps, the last with the
-      // second relaxation half step (th holds the time-t theta_T)
-      k_pm_pred<Real, kBC><<<tgrid, tb, 0, L->stream>>>(K, es, ucur, ea, gh);
-      k_pm_corr<Real, kBC><<<tgrid, tb, 0, L->stream>>>(K, es, ea, ucur, eb, gh);
-      const Real* src = eb;
-      for (int k = 0; k < L->nsub; ++k) {
-        Real* dst = (k == L->nsub - 1) ? e : (src == eb ? ea : eb);
-        k_pm_ftcs<Real, kBC><<<tgrid, tb, 0, L->stream>>>(K, src, drho, kap, th, dst, gh,
-                                                           k == L->nsub - 1);
-        src = dst;
-      }
-      RPK_CUDA(timing_end(L, RPK_KC_TRANSPORT, 2 + L->nsub));
-      return check_launch("rotational transport (paper mode)");
+  if (L->rot_mode) {
+    // paper mode: MacCormack on theta_R, FTCS sub-steps, the last with the
+    // second relaxation half step (th holds the time-t theta_T)
+    k_pm_pred<Real, kBC><<<tgrid, tb, 0, L->stream>>>(K, es, ucur, ea, gh);
+    k_pm_corr<Real, kBC><<<tgrid, tb, 0, L->stream>>>(K, es, ea, ucur, eb, gh);
+    const Real* src = eb;
+    for (int k = 0; k < L->nsub; ++k) {
+      Real* dst = (k == L->nsub - 1) ? e : (src == eb ? ea : eb);
+      k_pm_ftcs<Real, kBC><<<tgrid, tb, 0, L->stream>>>(K, src, drho, kap, th, dst, gh,
+                                                         k == L->nsub - 1);
+      src = dst;
     }
+    RPK_CUDA(timing_end(L, RPK_KC_TRANSPORT, 2 + L->nsub));
+    return check_launch("rotational transport (paper mode)");
   }
   k_mac_pred<Real, kBC><<<tgrid, tb, 0, L->stream>>>(K, es, ucur, uprev, ea, v, gh);
   k_mac_corr<Real, kBC><<<tgrid, tb, 0, L->stream>>>(K, es, ea, v, drho, eb, th, gh);
