@@ -173,7 +173,9 @@ rpk_status rpk_set_rot_mode(rpk_lattice* lat, int mode);
  *   kappa_R(p)(theta_w - theta_R(p))/d; no advective flux through a wall. In
  *   rotational mode 1 the same Dirichlet value enters the advection
  *   differences and the Laplacian as the straight line through theta_w.
- * Requires ny >= 2 and bc_x = RPK_BC_PERIODIC (RPK_ERR_STATE otherwise).
+ * Requires ny >= 2, bc_x = RPK_BC_PERIODIC and the relaxation parameters set
+ * (RPK_ERR_STATE otherwise); a non-finite state, uy != 0 or theta <= 0 gives
+ * RPK_ERR_PARAM and leaves the walls as they were.
  * Takes effect at the next step or moment read; the automatic nsub of
  * rpk_init_fields accounts for the stiffer near-wall diffusion (one face with
  * coefficient 4 kappa_R) and for the wall temperatures. Checkpoints record the
