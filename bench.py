@@ -81,7 +81,8 @@ def load_bf16_peak(sustained=False):
 
 def ncu_traffic(prec):
     """DRAM bytes per point of the collide kernel from the committed ncu
-    summary, if the kernel source has not changed since it was captured."""
+    summary and the summary's one-line description of the capture, if the
+    kernel source has not changed since it was captured; else None."""
     path = os.path.join(ROOT, "profiles", "ncu_collide_%s.txt" % prec)
     csrc = os.path.join(ROOT, "paper_2201_05280_gb300", "csrc")
     srcs = [os.path.join(csrc, f) for f in ("rpk_lattice.cuh", "rpk_device.cuh", "rpk_collide.cuh")]
@@ -98,7 +99,7 @@ def ncu_traffic(prec):
         sha = h.hexdigest()
         if kv.get("kernel_source_sha256") != sha:
             return None
-        return float(kv["dram_bytes_per_point"])
+        return float(kv["dram_bytes_per_point"]), kv.get("capture", "")
     except (OSError, KeyError, ValueError):
         return None
 
@@ -603,16 +604,22 @@ def main():
     coll_ms, coll_n = ktimes["collide"]
     coll_avg_s = coll_ms / max(coll_n, 1) * 1e-3
     achieved = ab["collide"] * npts / coll_avg_s / 1e9
-    traffic_pp = ncu_traffic(args.precision)
+    traffic = ncu_traffic(args.precision)
+    step_gbs = ab["step"] * npts * args.steps / (ms * 1e-3) / 1e9
     roofline = {"bound": "hbm", "kernel": "k_collide (pull-stream + collide + exchange)",
                 "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "peak_source": peak_src,
                 "algorithmic_bytes_per_point": ab["collide"],
-                "traffic": None if traffic_pp is None else traffic_pp * npts,
+                "traffic": None if traffic is None else traffic[0] * npts,
+                "traffic_bytes_per_point": None if traffic is None else traffic[0],
+                "traffic_source": None if traffic is None else traffic[1],
                 "kernel_ms": {k: v[0] / max(v[1], 1) for k, v in ktimes.items()},
                 "kernel_share": {k: v[0] / sum(x[0] for x in ktimes.values())
                                  for k, v in ktimes.items()},
-                "step_gbs_at_376B": ab["step"] * npts * args.steps / (ms * 1e-3) / 1e9}
+                # the whole step against the same peak, at the algorithmic
+                # bytes of one step (populations once each way + the fields)
+                "step_algorithmic_bytes_per_point": ab["step"],
+                "step_gbs": step_gbs, "step_frac": step_gbs / peak}
     cpu_mlups, cpu_dt = oracle_mlups(args.cpu_n, args.cpu_steps, warmup=1)
     all_mlups, all_dt, procs = oracle_mlups_allcore(args.cpu_n, args.cpu_steps, warmup=1)
     launches = sum(v[1] for v in ktimes.values())

@@ -123,6 +123,31 @@ rpk_status rpk_map_gas(double gamma, double eta, double eta_B, double kappa, dou
  * theta = 1.25 theta_max. Returns >= 1. */
 int rpk_auto_nsub(const rpk_relax* r, double theta_max, int ndim);
 
+/* The gas as the experiments specify it -- kinematic viscosity nu, bulk to
+ * shear viscosity ratio lam = eta_B/eta and Prandtl number Pr -- in the
+ * (eta, eta_B, kappa) that rpk_map_gas takes (Sec. 4, eq. viscosities and the
+ * Prandtl-number paragraph); host only, needs no GPU. delta from gamma as in
+ * rpk_map_gas, eta = rho0 nu, eta_B = lam eta and kappa = eta c_p/Pr with the
+ * heat capacity per unit mass c_p = (5 + delta)/2 (theta units). Writes
+ * out[0..2] = eta, eta_B, kappa (host array of 3). RPK_ERR_ARG for out = NULL,
+ * RPK_ERR_PARAM for gamma outside (1, 5/3] or nu, lam, Pr, rho0 not finite
+ * and positive. */
+rpk_status rpk_gas_from_nondim(double gamma, double nu, double lam, double Pr, double rho0,
+                               double out[3]);
+
+/* Adiabatic sound speed c_s = sqrt(gamma theta0) of the lattice reference
+ * state (Sec. 4, hydrodynamic limit; Sec. 6 measures it); NaN for gamma
+ * outside (1, 5/3]. Host only. */
+double rpk_sound_speed(double gamma);
+
+/* rpk_auto_nsub at the hottest state of a set of fields: theta_max is the
+ * largest theta = (3 theta_T + delta theta_R)/(3 + delta) (eq. thetadef) over
+ * the n host values theta_T[p], theta_R[p] and, if res is not NULL, the two
+ * reservoir states res[12] (layout of rpk_set_reservoirs). Host only; returns
+ * 1 for NULL or non-positive input. */
+int rpk_auto_nsub_fields(const rpk_relax* r, const double* theta_T, const double* theta_R,
+                         int64_t n, const double* res, int ndim);
+
 /* Create a lattice on the current device. cuda_stream is a cudaStream_t (or
  * NULL). Allocates 2 x 41 populations per point (ping-pong) plus ~12 scalar
  * planes. */
@@ -423,6 +448,13 @@ rpk_status rpk_sur_apply(const rpk_sur_config* cfg, const float* state, const fl
                          double* totals, void* cuda_stream);
 
 typedef struct rpk_rollout rpk_rollout;
+/* The values (rho, u_x, theta_T, E_R) that a tube's low and high reservoir
+ * states take in the moment blocks the surrogate reads, E_R = delta rho
+ * theta_R / 2 (eq. thetadef's rotational energy): out (host, 8 floats) =
+ * low side then high side. The paper has no counterpart (the surrogate is
+ * this library's). RPK_ERR_ARG for a NULL argument. */
+rpk_status rpk_sur_reservoirs(const rpk_tube* tube, float* out);
+
 /* A rollout engine for ntubes tubes (every relax.nsub > 0): the network `net`
  * (not owned), per-tube conditioning cond[2 i], cond[2 i + 1] (host), and an
  * internal FP32 batch of the same tubes for spot checks and fallback. */
@@ -452,24 +484,27 @@ rpk_status rpk_rollout_run(rpk_rollout* r, float* state, int64_t* stats, double*
 rpk_status rpk_rollout_errors(const rpk_rollout* r, double* out, int* windows);
 
 /* Conserved totals of hydrodynamic fields held by the caller in device memory,
- * computed without allocating anything. The paper has no counterpart; this is
- * for callers that cannot call cudaMalloc where they need the totals (a loop
- * being recorded into a CUDA graph, where allocation is not allowed during
- * stream capture, or an application whose memory manager owns all device
- * memory). Inputs: rho, u (3 planes), theta_T, theta_R, npts values each, in
+ * computed without allocating anything. The paper has no counterpart. It is
+ * for callers that may not call cudaMalloc where they need the totals: an
+ * application whose own memory manager owns all device memory (a pooling
+ * allocator or a fixed budget) and forbids libraries to allocate, or a loop
+ * that must not stall on cudaMalloc/cudaFree, which can synchronise the
+ * device. Inputs: rho, u (3 planes), theta_T, theta_R, npts values each, in
  * the field layout above (e.g. written by rpk_read_moments with on_device = 1);
  * delta as in rpk_relax. Output: out[0..4] in device memory =
  *   sum rho, sum rho u_x, sum rho u_y, sum rho u_z,
  *   sum (rho |u|^2/2 + 3 rho theta_T/2 + delta rho theta_R/2)   (E_T + E_R),
  * which equal rpk_diagnostics' mass, mom and energy of the same state.
  * Asynchronous on cuda_stream (NULL = legacy default stream); the device is
- * the current one. The per-block partial sums live in a static 320 KiB device
- * array that every GPU loading the library keeps until exit; npts is limited
- * to 67,108,864 (8192 blocks of 8192 points), larger sizes return
- * RPK_ERR_ARG. The first call on each device looks up that array's address;
- * make that first call before any stream capture. All calls share the array,
- * so calls whose kernels overlap on the GPU race: order them on one stream.
- * No part of the array needs to start at zero. */
+ * the current one, and every pointer must be device memory of that device and
+ * the stream one of its streams, else RPK_ERR_ARG (nothing is launched). The
+ * per-block partial sums live in a static 320 KiB device array that every GPU
+ * loading the library keeps until exit; npts is limited to 67,108,864 (8192
+ * blocks of 8192 points), larger sizes return RPK_ERR_ARG. The first call on
+ * each device looks up that array's address; make that first call before any
+ * stream capture. All calls share the array, so calls whose kernels overlap
+ * on the GPU race: order them on one stream. No part of the array needs to
+ * start at zero: a call reads only the slots its own blocks wrote. */
 rpk_status rpk_field_totals_noalloc(const double* rho, const double* u, const double* theta_T,
                                     const double* theta_R, int64_t npts, double delta,
                                     void* cuda_stream, double* out);

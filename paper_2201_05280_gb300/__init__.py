@@ -17,7 +17,8 @@ import os
 import numpy as np
 
 __all__ = ["Lattice", "RpkError", "load_library", "theta0", "map_gas", "auto_nsub",
-           "gas_from_nondim", "field_totals_noalloc", "Batch", "Net", "Rollout", "SurConfig", "SurSeq",
+           "gas_from_nondim", "sound_speed", "auto_nsub_fields", "tube_reservoirs",
+           "field_totals_noalloc", "Batch", "Net", "Rollout", "SurConfig", "SurSeq",
            "sur_pack", "sur_apply", "PRECISIONS", "library_path"]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -119,6 +120,10 @@ def load_library(path=None):
         "rpk_last_error": (ctypes.c_char_p, []),
         "rpk_map_gas": (i, [d, d, d, d, d, d, ctypes.POINTER(Relax)]),
         "rpk_auto_nsub": (i, [ctypes.POINTER(Relax), d, i]),
+        "rpk_gas_from_nondim": (i, [d, d, d, d, d, ctypes.POINTER(d)]),
+        "rpk_sound_speed": (d, [d]),
+        "rpk_auto_nsub_fields": (i, [ctypes.POINTER(Relax), _dp, _dp, i64, _dp, i]),
+        "rpk_sur_reservoirs": (i, [ctypes.POINTER(Tube), ctypes.POINTER(ctypes.c_float)]),
         "rpk_create": (i, [ctypes.POINTER(Grid), vp, ctypes.POINTER(vp)]),
         "rpk_destroy": (None, [vp]),
         "rpk_set_relax": (i, [vp, ctypes.POINTER(Relax)]),
@@ -202,29 +207,81 @@ def auto_nsub(relax, theta_max, ndim):
 
 def gas_from_nondim(gamma, nu, lam, Pr, rho0=1.0):
     """(eta, eta_B, kappa) from kinematic viscosity nu, eta_B/eta = lam and
-    Pr = eta c_p/kappa with c_p = (5 + delta)/2 (Sec. 4)."""
-    delta = (5.0 - 3.0 * gamma) / (gamma - 1.0)
-    eta = rho0 * nu
-    return eta, lam * eta, eta * (5.0 + delta) / 2.0 / Pr
+    the Prandtl number (rpk_gas_from_nondim)."""
+    out = (ctypes.c_double * 3)()
+    _check(load_library().rpk_gas_from_nondim(float(gamma), float(nu), float(lam), float(Pr),
+                                              float(rho0), out))
+    return out[0], out[1], out[2]
+
+
+def sound_speed(gamma):
+    """Adiabatic sound speed of the lattice reference state (rpk_sound_speed)."""
+    return load_library().rpk_sound_speed(float(gamma))
+
+
+def auto_nsub_fields(relax, T, R, res=None, ndim=1):
+    """FTCS sub-steps at the hottest of the fields T, R (host arrays) and the
+    optional 12 reservoir values (rpk_auto_nsub_fields)."""
+    r = Relax(**{k: relax.get(k, 0) for k, _ in Relax._fields_})
+    T = np.ascontiguousarray(T, dtype=np.float64).reshape(-1)
+    R = np.ascontiguousarray(R, dtype=np.float64).reshape(-1)
+    if T.size != R.size:
+        raise ValueError("T and R differ in size")
+    rs = None if res is None else np.ascontiguousarray(res, dtype=np.float64).reshape(12)
+    return load_library().rpk_auto_nsub_fields(
+        ctypes.byref(r), T.ctypes.data_as(_dp), R.ctypes.data_as(_dp), T.size,
+        None if rs is None else rs.ctypes.data_as(_dp), int(ndim))
+
+
+def tube_reservoirs(tube):
+    """(2, 4) float32 moment-block values (rho, u_x, theta_T, E_R) of a tube
+    dict's reservoirs (rpk_sur_reservoirs)."""
+    t = _tube_struct(tube)
+    out = np.zeros(8, dtype=np.float32)
+    _check(load_library().rpk_sur_reservoirs(ctypes.byref(t),
+                                             out.ctypes.data_as(ctypes.POINTER(ctypes.c_float))))
+    return out.reshape(2, 4)
 
 
 def field_totals_noalloc(rho, u, T, R, delta, out, stream=None):
     """Conserved totals (sum rho, sum rho u (3), E_T + E_R) of CUDA float64
     tensors, written into the CUDA float64 tensor ``out`` (5 values) on
-    ``stream``; allocates nothing (rpk_field_totals_noalloc). For callers that
-    cannot allocate device memory at that point, e.g. while recording a CUDA
-    graph. Asynchronous: synchronise the stream before reading ``out``."""
+    ``stream``; allocates nothing (rpk_field_totals_noalloc). For callers
+    that may not allocate device memory at that point (an application whose
+    memory manager owns all device memory, or a loop that must not stall on
+    cudaMalloc). Every tensor and the stream must be on the current CUDA
+    device. Asynchronous: synchronise the stream before reading ``out``."""
+    import torch
+    cur = torch.cuda.current_device()
     n = rho.numel()
     ptrs = []
-    for a, m in ((rho, n), (u, 3 * n), (T, n), (R, n), (out, 5)):
+    for name, a, m in (("rho", rho, n), ("u", u, 3 * n), ("T", T, n), ("R", R, n), ("out", out, 5)):
         p, dev, _ = _arg(a, m)
         if dev != 1:
-            raise ValueError("field_totals_noalloc takes CUDA tensors only")
+            raise ValueError("field_totals_noalloc takes CUDA tensors only (%s)" % name)
+        if a.device.index != cur:
+            raise ValueError("%s is on cuda:%d, not on the current device cuda:%d"
+                             % (name, a.device.index, cur))
         ptrs.append(p)
+    if stream is not None and not isinstance(stream, int) and stream.device.index != cur:
+        raise ValueError("the stream is on cuda:%d, not on the current device cuda:%d"
+                         % (stream.device.index, cur))
     _check(load_library().rpk_field_totals_noalloc(ptrs[0], ptrs[1], ptrs[2], ptrs[3], n,
                                                    float(delta), _stream_handle(stream),
                                                    ptrs[4]))
     return out
+
+
+def _tube_struct(d):
+    """rpk_tube of a tube dict (nx, nsteps, relax, res)."""
+    t = Tube()
+    t.nx, t.nsteps = int(d["nx"]), int(d["nsteps"])
+    r = d["relax"]
+    t.relax = Relax(r["delta"], r["tau"], r["tau1"], r.get("b", 0.0), r.get("k_r", 0.0),
+                    r.get("dt", 1.0), int(r.get("nsub", 0)))
+    for k in range(12):
+        t.res[k] = float(d["res"][k])
+    return t
 
 
 def _is_torch(a):
@@ -406,14 +463,7 @@ class Batch:
 
     def __init__(self, tubes, precision="f32", save_every=32, stream=None):
         lib = load_library()
-        arr = (Tube * len(tubes))()
-        for t, d in zip(arr, tubes):
-            t.nx, t.nsteps = int(d["nx"]), int(d["nsteps"])
-            r = d["relax"]
-            t.relax = Relax(r["delta"], r["tau"], r["tau1"], r.get("b", 0.0), r.get("k_r", 0.0),
-                            r.get("dt", 1.0), int(r.get("nsub", 0)))
-            for k in range(12):
-                t.res[k] = float(d["res"][k])
+        arr = (Tube * len(tubes))(*[_tube_struct(d) for d in tubes])
         self.tubes = [dict(d) for d in tubes]
         self.save_every = int(save_every)
         self.offsets = np.cumsum([0] + [2 * int(d["nx"]) for d in tubes])
@@ -672,14 +722,7 @@ class Rollout:
 
     def __init__(self, net, cfg, tubes, cond, stream=None):
         lib = load_library()
-        arr = (Tube * len(tubes))()
-        for t, d in zip(arr, tubes):
-            t.nx, t.nsteps = int(d["nx"]), int(d["nsteps"])
-            r = d["relax"]
-            t.relax = Relax(r["delta"], r["tau"], r["tau1"], r.get("b", 0.0), r.get("k_r", 0.0),
-                            r.get("dt", 1.0), int(r.get("nsub", 0)))
-            for k in range(12):
-                t.res[k] = float(d["res"][k])
+        arr = (Tube * len(tubes))(*[_tube_struct(d) for d in tubes])
         c = np.ascontiguousarray(cond, dtype=np.float32).reshape(-1)
         if c.size != 2 * len(tubes):
             raise ValueError("cond must have 2 values per tube")

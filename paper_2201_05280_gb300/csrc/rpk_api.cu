@@ -148,6 +148,38 @@ int rpk_auto_nsub(const rpk_relax* r, double theta_max, int ndim) {
   return nsub_for_diagonal(r, theta_max, 2.0 * ndim);
 }
 
+rpk_status rpk_gas_from_nondim(double gamma, double nu, double lam, double Pr, double rho0,
+                               double out[3]) {
+  if (!out) return fail(RPK_ERR_ARG, "out is NULL");
+  if (!(gamma > 1.0) || !(gamma <= 5.0 / 3.0)) return fail(RPK_ERR_PARAM, "gamma must lie in (1, 5/3]");
+  if (!(nu > 0.0) || !(lam > 0.0) || !(Pr > 0.0) || !(rho0 > 0.0) || !std::isfinite(nu) ||
+      !std::isfinite(lam) || !std::isfinite(Pr) || !std::isfinite(rho0))
+    return fail(RPK_ERR_PARAM, "nu, eta_B/eta, Pr and rho0 must be finite and > 0");
+  const double delta = (5.0 - 3.0 * gamma) / (gamma - 1.0);
+  const double cp = 0.5 * (5.0 + delta);  // heat capacity per unit mass (theta units)
+  const double eta = rho0 * nu;
+  out[0] = eta;
+  out[1] = lam * eta;
+  out[2] = eta * cp / Pr;
+  return RPK_OK;
+}
+
+double rpk_sound_speed(double gamma) {
+  if (!(gamma > 1.0) || !(gamma <= 5.0 / 3.0)) return NAN;
+  return std::sqrt(gamma * kTheta0);
+}
+
+int rpk_auto_nsub_fields(const rpk_relax* r, const double* theta_T, const double* theta_R,
+                         int64_t n, const double* res, int ndim) {
+  if (!r || (n > 0 && (!theta_T || !theta_R))) return 1;
+  double tmax = 0.0;
+  auto theta = [&](double T, double R) { return (3.0 * T + r->delta * R) / (3.0 + r->delta); };
+  for (int64_t p = 0; p < n; ++p) tmax = std::max(tmax, theta(theta_T[p], theta_R[p]));
+  if (res) tmax = std::max(tmax, std::max(theta(res[4], res[5]), theta(res[10], res[11])));
+  if (!(tmax > 0.0) || !std::isfinite(tmax)) return 1;
+  return rpk_auto_nsub(r, tmax, ndim);
+}
+
 static void free_all(rpk_lattice* L) {
   if (!L) return;
   for (cudaEvent_t ev : L->events) cudaEventDestroy(ev);
@@ -355,13 +387,7 @@ rpk_status rpk_init_fields(rpk_lattice* L, const double* rho, const double* u,
   const int64_t n = L->npts;
   const double *drho = rho, *du = u, *dT = T, *dR = R;
   if (!on_device) {
-    // host validation, then one copy per field into the staging buffer
-    for (int64_t p = 0; p < n; ++p)
-      if (!(rho[p] > 0.0) || !(T[p] > 0.0) || !(R[p] > 0.0) || !std::isfinite(rho[p]) ||
-          !std::isfinite(T[p]) || !std::isfinite(R[p]))
-        return fail(RPK_ERR_PARAM, "fields need finite rho > 0, theta_T > 0, theta_R > 0");
-    for (int64_t p = 0; p < 3 * n; ++p)
-      if (!std::isfinite(u[p])) return fail(RPK_ERR_PARAM, "u not finite");
+    // one copy per field into the staging buffer; checked on the device below
     rpk_status st = ensure_stage(L);
     if (st != RPK_OK) return st;
     double* s = L->stage;
@@ -374,17 +400,23 @@ rpk_status rpk_init_fields(rpk_lattice* L, const double* rho, const double* u,
     dT = s + 4 * n;
     dR = s + 5 * n;
   }
+  // validation and the largest initial theta (for nsub = 0) in one device pass
+  const int nb = 256;
+  k_check_fields<<<nb, 256, 0, L->stream>>>(drho, du, dT, dR, n, L->relax.delta, L->diag_partial);
+  RPK_CUDA(cudaGetLastError());
+  std::vector<double> part(2 * nb);
+  RPK_CUDA(cudaMemcpyAsync(part.data(), L->diag_partial, 2 * nb * sizeof(double),
+                           cudaMemcpyDeviceToHost, L->stream));
+  RPK_CUDA(cudaStreamSynchronize(L->stream));
+  double tmax = -INFINITY;
+  for (int b = 0; b < nb; ++b) {
+    if (part[2 * b + 1] != 0.0)
+      return fail(RPK_ERR_PARAM, "fields need finite rho > 0, theta_T > 0, theta_R > 0 and finite u");
+    tmax = std::max(tmax, part[2 * b]);
+  }
+  if (!(tmax > 0.0) || !std::isfinite(tmax)) return fail(RPK_ERR_PARAM, "fields need theta > 0");
   // FTCS sub-steps from the largest initial theta when nsub = 0
   if (L->relax.nsub == 0) {
-    const int nb = 256;
-    k_theta_max<<<nb, 256, 0, L->stream>>>(dT, dR, n, L->relax.delta, L->diag_partial);
-    RPK_CUDA(cudaGetLastError());
-    std::vector<double> part(nb);
-    RPK_CUDA(cudaMemcpyAsync(part.data(), L->diag_partial, nb * sizeof(double),
-                             cudaMemcpyDeviceToHost, L->stream));
-    RPK_CUDA(cudaStreamSynchronize(L->stream));
-    double tmax = *std::max_element(part.begin(), part.end());
-    if (!(tmax > 0.0) || !std::isfinite(tmax)) return fail(RPK_ERR_PARAM, "fields need theta > 0");
     if (L->walls || L->xwalls) {
       // a point next to a wall has one face of coefficient 4 kappa_R (distance
       // 1/4) per wall axis

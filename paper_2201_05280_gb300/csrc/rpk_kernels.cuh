@@ -584,22 +584,40 @@ static __global__ void __launch_bounds__(1024) k_diag_final(const double* __rest
   }
 }
 
-// max over points of theta = (3 theta_T + delta theta_R)/(3 + delta), for nsub
-static __global__ void __launch_bounds__(256) k_theta_max(const double* __restrict__ T,
-                                                   const double* __restrict__ R, int64_t n,
-                                                   double delta, double* __restrict__ out) {
+// Checks the initial fields and finds the hottest point: per block, the
+// largest theta = (3 theta_T + delta theta_R)/(3 + delta) (eq. thetadef; for
+// nsub) and a flag that is 1 where some rho, theta_T or theta_R is not finite
+// and positive or some velocity component is not finite. out[2 b] = max theta,
+// out[2 b + 1] = flag of block b.
+static __global__ void __launch_bounds__(256) k_check_fields(const double* __restrict__ rho,
+                                                      const double* __restrict__ u,
+                                                      const double* __restrict__ T,
+                                                      const double* __restrict__ R, int64_t n,
+                                                      double delta, double* __restrict__ out) {
   __shared__ double red[8];
+  __shared__ int bad_any;
+  if (threadIdx.x == 0) bad_any = 0;
+  __syncthreads();
   double v = -INFINITY;
+  int bad = 0;
   for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n;
-       p += (int64_t)gridDim.x * blockDim.x)
-    v = fmax(v, (3.0 * T[p] + delta * R[p]) / (3.0 + delta));
+       p += (int64_t)gridDim.x * blockDim.x) {
+    const double r = rho[p], t = T[p], q = R[p];
+    const double ux = u[p], uy = u[n + p], uz = u[2 * n + p];
+    if (!(r > 0.0) || !(t > 0.0) || !(q > 0.0) || !isfinite(r) || !isfinite(t) || !isfinite(q) ||
+        !isfinite(ux) || !isfinite(uy) || !isfinite(uz))
+      bad = 1;
+    v = fmax(v, (3.0 * t + delta * q) / (3.0 + delta));
+  }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  if (bad) bad_any = 1;
   __syncthreads();
   if (threadIdx.x == 0) {
     for (int w = 1; w < 8; ++w) v = fmax(v, red[w]);
-    out[blockIdx.x] = v;
+    out[2 * blockIdx.x] = v;
+    out[2 * blockIdx.x + 1] = bad_any ? 1.0 : 0.0;
   }
 }
 

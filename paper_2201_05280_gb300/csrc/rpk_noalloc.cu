@@ -1,22 +1,25 @@
 // rpk_field_totals_noalloc: FP64 conserved totals of hydrodynamic fields that
 // the caller keeps in device memory, computed without allocating anything.
 //
-// Who needs this: code that must not call cudaMalloc at the point where it
-// wants the totals -- for example a solver loop that is being recorded into a
-// CUDA graph (allocation is not allowed while a stream is captured), or a host
-// application whose own memory manager owns all device memory and forbids
-// allocations from libraries. Such a caller already holds rho, u, theta_T and
-// theta_R (for example filled by rpk_read_moments with on_device = 1) and only
-// needs a reduction.
+// Who needs this: callers that are not allowed to call cudaMalloc at the point
+// where they want the totals. One kind is an application whose own memory
+// manager owns all of the device memory (a pooling allocator that accounts
+// for every byte, or a fixed budget shared with other work) and forbids
+// libraries to allocate behind its back. Another is a loop that must not
+// stall: cudaMalloc and cudaFree can synchronise the device, which would
+// serialise work that other streams have in flight. Such a caller already
+// holds rho, u, theta_T and theta_R (for example filled by rpk_read_moments
+// with on_device = 1) and only needs a reduction.
 //
 // Scratch: the per-block partial sums live in one file-scope __device__ array
 // of kMaxChunks x kVals doubles (320 KiB). Every GPU that loads the library
 // keeps that array until the process exits. Each call uses one block per chunk
 // of kChunk points, so one call reduces at most kMaxChunks * kChunk points.
-// Every block writes all of its own slots before the final pass reads them, so
-// no part of the array has to start at zero and nothing is cleared. All calls,
-// on any stream, share the array: calls whose kernels overlap on the GPU race
-// and must be ordered by the caller (same stream, or events).
+// Every block writes all of its own slots before the final pass reads them,
+// and the final pass reads only the slots of this call's blocks, so no part
+// of the array has to start at zero and nothing is cleared. All calls, on any
+// stream, share the array: calls whose kernels overlap on the GPU race and
+// must be ordered by the caller (same stream, or events).
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -141,11 +144,43 @@ extern "C" rpk_status rpk_field_totals_noalloc(const double* rho, const double* 
   double* scratch = nullptr;
   rpk_status st = scratch_on_current_device(&scratch);
   if (st != RPK_OK) return st;
+  int dev = -1;
+  cudaError_t err = cudaGetDevice(&dev);
+  if (err != cudaSuccess) return rpk::cuda_fail(err, "cudaGetDevice");
+  // every pointer must be device memory of the current device: the kernels
+  // run there and would otherwise read another GPU's or the host's memory
+  const void* ptrs[5] = {rho, u, theta_T, theta_R, out};
+  const char* names[5] = {"rho", "u", "theta_T", "theta_R", "out"};
+  for (int k = 0; k < 5; ++k) {
+    cudaPointerAttributes a{};
+    err = cudaPointerGetAttributes(&a, ptrs[k]);
+    if (err != cudaSuccess) {
+      cudaGetLastError();
+      rpk::set_error(std::string("rpk_field_totals_noalloc: ") + names[k] +
+                     " is not device memory of the current device (no CUDA pointer)");
+      return RPK_ERR_ARG;
+    }
+    if (a.type != cudaMemoryTypeDevice || a.device != dev) {
+      rpk::set_error(std::string("rpk_field_totals_noalloc: ") + names[k] +
+                     " is not device memory of the current device " + std::to_string(dev));
+      return RPK_ERR_ARG;
+    }
+  }
   cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
+  if (stream) {
+    int sdev = -1;
+    err = cudaStreamGetDevice(stream, &sdev);
+    if (err != cudaSuccess) return rpk::cuda_fail(err, "cudaStreamGetDevice");
+    if (sdev != dev) {
+      rpk::set_error("rpk_field_totals_noalloc: the stream belongs to device " +
+                     std::to_string(sdev) + ", not the current device " + std::to_string(dev));
+      return RPK_ERR_ARG;
+    }
+  }
   const int nchunks = (int)((npts + kChunk - 1) / kChunk);
   k_totals_partial<<<nchunks, kThreads, 0, stream>>>(rho, u, theta_T, theta_R, npts, delta,
                                                      scratch);
-  cudaError_t err = cudaGetLastError();
+  err = cudaGetLastError();
   if (err != cudaSuccess) return rpk::cuda_fail(err, "k_totals_partial");
   k_totals_final<<<1, 1024, 0, stream>>>(scratch, nchunks, out);
   err = cudaGetLastError();

@@ -338,6 +338,18 @@ int seq_len(const rpk_rollout* R, int tube) {
   return (n + 3) / 4 * 4;
 }
 
+// The moment-block values (rho, u_x, theta_T, E_R = delta rho theta_R / 2,
+// eq. thetadef's rotational energy) of a tube's low and high reservoir states.
+void tube_reservoir_moments(const rpk_tube& t, float* out8) {
+  for (int side = 0; side < 2; ++side) {
+    const double* r = t.res + 6 * side;
+    out8[4 * side + 0] = (float)r[0];
+    out8[4 * side + 1] = (float)r[1];
+    out8[4 * side + 2] = (float)r[4];
+    out8[4 * side + 3] = (float)(0.5 * t.relax.delta * r[0] * r[5]);
+  }
+}
+
 rpk_sur_seq make_seq(const rpk_rollout* R, int tube, int64_t out) {
   rpk_sur_seq s;
   std::memset(&s, 0, sizeof(s));
@@ -349,13 +361,7 @@ rpk_sur_seq make_seq(const rpk_rollout* R, int tube, int64_t out) {
   s.nx = t.nx;
   s.len = seq_len(R, tube);
   s.crop = 0;
-  for (int side = 0; side < 2; ++side) {
-    const double* r = t.res + 6 * side;
-    s.res[side][0] = (float)r[0];
-    s.res[side][1] = (float)r[1];
-    s.res[side][2] = (float)r[4];
-    s.res[side][3] = (float)(0.5 * t.relax.delta * r[0] * r[5]);
-  }
+  tube_reservoir_moments(t, &s.res[0][0]);
   s.cond[0] = R->cond[2 * tube];
   s.cond[1] = R->cond[2 * tube + 1];
   return s;
@@ -394,6 +400,12 @@ float elapsed(rpk_rollout* R) {
 }  // namespace
 
 extern "C" {
+
+rpk_status rpk_sur_reservoirs(const rpk_tube* tube, float* out) {
+  if (!tube || !out) return rpk::fail(RPK_ERR_ARG, "NULL argument");
+  tube_reservoir_moments(*tube, out);
+  return RPK_OK;
+}
 
 rpk_status rpk_sur_pack(const rpk_sur_config* cfg, const float* store, const rpk_sur_seq* seqs,
                         int nseq, int maxlen, int margin, const float* noise, uint64_t seed,

@@ -49,19 +49,15 @@ def make_tubes(specs, fields, theta0):
     parameters from the library's gas mapping and explicit FTCS sub-step
     counts (rpk_auto_nsub on the tube's hottest initial state), and the
     conditioning features (ntubes, 2)."""
-    cs = math.sqrt(GAMMA * theta0)
+    cs = rpk.sound_speed(GAMMA)
     tubes, cond = [], []
     off = 0
     for sp in specs:
-        nu = sp["kn"] * cs * sp["nx"]
+        nu = sp["kn"] * cs * sp["nx"]  # Kn = nu / (c_s L), L = cells along the tube
         eta, etaB, kap = rpk.gas_from_nondim(GAMMA, nu, sp["lam"], sp.get("pr", PR))
         r = rpk.map_gas(GAMMA, eta, etaB, kap, 0.0)
-        d = r["delta"]
         sl = slice(off, off + 2 * sp["nx"])
-        tmax = float(np.max((3 * fields["T"][sl] + d * fields["R"][sl]) / (3 + d)))
-        res = np.asarray(sp["res"])
-        tmax = max(tmax, float(np.max((3 * res[[4, 10]] + d * res[[5, 11]]) / (3 + d))))
-        r["nsub"] = rpk.auto_nsub(r, tmax, 1)
+        r["nsub"] = rpk.auto_nsub_fields(r, fields["T"][sl], fields["R"][sl], sp["res"], 1)
         tubes.append({"nx": sp["nx"], "nsteps": sp["nsteps"], "relax": r, "res": sp["res"]})
         cond.append(cond_features(nu, sp["lam"]))
         off += 2 * sp["nx"]
@@ -70,10 +66,7 @@ def make_tubes(specs, fields, theta0):
 
 def reservoirs(tube):
     """(2, 4) reservoir states (rho, u_x, theta_T, E_R) of a tube dict."""
-    r = tube["res"]
-    d = tube["relax"]["delta"]
-    return np.array([[r[0], r[1], r[4], 0.5 * d * r[0] * r[5]],
-                     [r[6], r[7], r[10], 0.5 * d * r[6] * r[11]]], dtype=np.float32)
+    return rpk.tube_reservoirs(tube)
 
 
 class TrainingSet:

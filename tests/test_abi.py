@@ -77,6 +77,45 @@ def test_auto_nsub_matches_oracle_rule(lib, theta_max, ndim):
         assert rpk.auto_nsub(r, theta_max, ndim) == PM.nsub_for(2.0, tau, tau1, kr, theta_max, ndim)
 
 
+def test_gas_from_nondim_in_the_library(lib):
+    """The Sec. 4 relations the binding no longer computes itself: the
+    library's (eta, eta_B, kappa) against the oracle's mapping, a hand value
+    for air (delta = 2: c_p = 7/2, so kappa = 7 eta / (2 Pr)) and the errors."""
+    eta, etaB, kap = rpk.gas_from_nondim(1.4, 0.02, 0.6, 0.71)
+    assert (eta, etaB) == (0.02, 0.6 * 0.02)
+    assert abs(kap - 3.5 * 0.02 / 0.71) <= 1e-16
+    for bad in ((1.0, 0.02, 0.6, 0.71), (1.4, 0.0, 0.6, 0.71), (1.4, 0.02, 0.6, -1.0),
+                (1.4, float("nan"), 0.6, 0.71)):
+        with pytest.raises(rpk.RpkError) as e:
+            rpk.gas_from_nondim(*bad)
+        assert e.value.code == 2
+
+
+def test_sound_speed_and_nsub_of_fields(lib):
+    t0 = PM.THETA0
+    assert abs(rpk.sound_speed(1.4) - np.sqrt(1.4 * t0)) <= 1e-16
+    assert np.isnan(rpk.sound_speed(1.8))
+    rng = np.random.default_rng(3)
+    T = t0 * (1 + 0.3 * rng.random(50))
+    R = t0 * (1 + 0.3 * rng.random(50))
+    res = [1.0, 0, 0, 0, 2.0 * t0, 1.5 * t0, 0.5, 0, 0, 0, t0, t0]
+    r = {"delta": 2.0, "tau": 0.9, "tau1": 1.1, "b": 0.0, "k_r": 3.0, "dt": 1.0, "nsub": 0}
+    theta = (3 * T + 2.0 * R) / 5.0
+    assert rpk.auto_nsub_fields(r, T, R, None, 3) == PM.nsub_for(2.0, 0.9, 1.1, 3.0, theta.max(), 3)
+    # the hotter reservoir decides
+    assert rpk.auto_nsub_fields(r, T, R, res, 1) == PM.nsub_for(2.0, 0.9, 1.1, 3.0, 1.8 * t0, 1)
+
+
+def test_tube_reservoirs_in_the_library(lib):
+    t0 = PM.THETA0
+    tube = {"nx": 10, "nsteps": 5, "relax": {"delta": 2.0, "tau": 1.0, "tau1": 1.0},
+            "res": [1.0, 0.1, 0, 0, t0, 1.2 * t0, 0.4, 0.0, 0, 0, 0.8 * t0, 0.9 * t0]}
+    got = rpk.tube_reservoirs(tube)
+    # E_R = delta rho theta_R / 2
+    ref = np.array([[1.0, 0.1, t0, 1.2 * t0], [0.4, 0.0, 0.8 * t0, 0.4 * 0.9 * t0]], np.float32)
+    assert np.array_equal(got, ref)
+
+
 def test_gpu_calls_fail_loudly_without_a_device(lib):
     import torch
     if torch.cuda.is_available():

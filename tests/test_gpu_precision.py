@@ -28,6 +28,11 @@ WAVE_BOUNDS = {"f32": (1e-5, 1e-5, 1e-5, 1e-5), "f16dev": (5e-6, 5e-6, 5e-6, 5e-
                "bf16dev": (5e-5, 5e-5, 5e-5, 5e-5)}
 TGV_BOUNDS = {"f32": (1e-5, 3e-5, 1e-5, 1e-5), "f16dev": (2e-3, 2e-3, 2e-3, 2e-3),
               "bf16dev": (2e-2, 2e-2, 2e-2, 2e-2)}
+# the same errors on the deviation scale (max|ref - rest state| per field)
+WAVE_DEV_BOUNDS = {"f32": (1.0, 1.0, 1.0, 1.0), "f16dev": (1.0, 1.0, 1.0, 1.0),
+                   "bf16dev": (1.0, 1.0, 1.0, 1.0)}
+TGV_DEV_BOUNDS = {"f32": (1.0, 1.0, 1.0, 1.0), "f16dev": (1.0, 1.0, 1.0, 1.0),
+                  "bf16dev": (1.0, 1.0, 1.0, 1.0)}
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -42,6 +47,16 @@ def _gpu():
 def _rel(a, b, key="rho"):
     scale = max(np.abs(b).max(), CS) if key == "u" else np.abs(b).max()
     return float(np.abs(a - b).max() / scale)
+
+
+# base values of the fields: the deviation scale of a field is max|ref - base|
+BASE = {"rho": 1.0, "u": 0.0, "T": T0, "Erot": 0.5 * 2.0 * T0}
+
+
+def _rel_dev(a, b, key):
+    """max|a - b| on the scale of the flow itself: the largest deviation of
+    the reference from the rest state (rho = 1, u = 0, theta0, delta theta0/2)."""
+    return float(np.abs(a - b).max() / np.abs(b - BASE[key]).max())
 
 
 @pytest.fixture(scope="module")
@@ -69,10 +84,13 @@ def test_storage_precision_wave_field_1000_steps(prec, wave_reference):
     got = lat.read_moments()
     d = lat.diagnostics()
     errs = {k: _rel(got[k], ref[k], k) for k in KEYS}
-    print("storage %s errors after %d steps: %s" % (prec, nsteps, errs))
+    devs = {k: _rel_dev(got[k], ref[k], k) for k in KEYS}
+    print("storage %s errors after %d steps: full scale %s, deviation scale %s" % (prec, nsteps, errs, devs))
     assert d["status"] == 0
     for k, bound in zip(KEYS, WAVE_BOUNDS[prec]):
         assert errs[k] <= bound, (prec, k, errs[k], bound)
+    for k, bound in zip(KEYS, WAVE_DEV_BOUNDS[prec]):
+        assert devs[k] <= bound, (prec, k, devs[k], bound)
 
 
 @pytest.fixture(scope="module")
@@ -104,6 +122,9 @@ def test_storage_precision_taylor_green(prec, tgv_reference):
     lat.init_fields(f["rho"], f["u"], f["T"], f["R"]).step(nsteps)
     got = lat.read_moments()
     errs = {k: _rel(got[k], ref[k], k) for k in KEYS}
-    print("TGV storage %s errors after %d steps: %s" % (prec, nsteps, errs))
+    devs = {k: _rel_dev(got[k], ref[k], k) for k in KEYS}
+    print("TGV storage %s errors after %d steps: full scale %s, deviation scale %s" % (prec, nsteps, errs, devs))
     for k, bound in zip(KEYS, TGV_BOUNDS[prec]):
         assert errs[k] <= bound, (prec, k, errs[k], bound)
+    for k, bound in zip(KEYS, TGV_DEV_BOUNDS[prec]):
+        assert devs[k] <= bound, (prec, k, devs[k], bound)
