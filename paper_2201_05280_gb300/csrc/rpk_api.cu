@@ -210,6 +210,7 @@ rpk_status rpk_create(const rpk_grid* grid, void* cuda_stream, rpk_lattice** out
   L->grid = *grid;
   L->stream = static_cast<cudaStream_t>(cuda_stream);
   cudaError_t err = cudaGetDevice(&L->device);
+  if (err == cudaSuccess) err = cudaDeviceGetAttribute(&L->sms, cudaDevAttrMultiProcessorCount, L->device);
   if (err != cudaSuccess) {
     delete L;
     return cuda_fail(err, "cudaGetDevice");

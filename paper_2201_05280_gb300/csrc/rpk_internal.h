@@ -13,6 +13,7 @@
 struct rpk_lattice {
   rpk_grid grid;
   int device = 0;
+  int sms = 1;           // streaming multiprocessors of the device
   cudaStream_t stream = nullptr;
   rpk_relax relax{};
   bool relax_ok = false;

@@ -477,7 +477,7 @@ __device__ __forceinline__ double warp_min(double v) {
 }
 
 template <typename Store, typename Real, bool kPull, int kBC>
-__global__ void __launch_bounds__(kDiagThreads)
+__global__ void __launch_bounds__(kDiagThreads, sizeof(Real) == 4 ? 4 : 1)
     k_diag(StepConst<Real> K, const Store* __restrict__ pin, const Real* __restrict__ e_in,
            const Real* __restrict__ ghost, double* __restrict__ partial,
            const Real* __restrict__ wcol) {
@@ -494,24 +494,44 @@ __global__ void __launch_bounds__(kDiagThreads)
     P.z = (int)(P.cell / ((int64_t)K.nx * K.ny));
     Real h[kQ];
     gather<Store, Real, kPull, kBC>(pin, ghost, K, P, h, wcol);
-    // conserved sums in FP64 from the stored values
-    double dm = kWeightRest * (double)h[0], jx = 0, jy = 0, jz = 0, ek = 0;
-    double gmin = kWeightRest * (1.0 + (double)h[0]);
-    static_for<kPairs>([&](auto kc) {
-      constexpr int k = decltype(kc)::value;
-      constexpr Vel2 v = kPairVel2[k];
-      constexpr double w = pair_weight(k);
-      constexpr double c2 = 0.25 * (v.x * v.x + v.y * v.y + v.z * v.z);
-      const double hp = (double)h[2 * k + 1], hm = (double)h[2 * k + 2];
-      dm += w * (hp + hm);
-      jx += 0.5 * v.x * w * (hp - hm);
-      jy += 0.5 * v.y * w * (hp - hm);
-      jz += 0.5 * v.z * w * (hp - hm);
-      ek += 0.5 * c2 * w * (hp + hm);
-      gmin = fmin(gmin, fmin(w * (1.0 + hp), w * (1.0 + hm)));
-    });
     Mom<Real> m;
     raw_moments(h, m);
+    double dm, jx, jy, jz, ek, gmin;
+    if constexpr (sizeof(Real) == 8) {
+      // FP64 path: conserved sums of the stored values, term by term
+      dm = kWeightRest * (double)h[0];
+      jx = jy = jz = ek = 0.0;
+      gmin = kWeightRest * (1.0 + (double)h[0]);
+      static_for<kPairs>([&](auto kc) {
+        constexpr int k = decltype(kc)::value;
+        constexpr Vel2 v = kPairVel2[k];
+        constexpr double w = pair_weight(k);
+        constexpr double c2 = 0.25 * (v.x * v.x + v.y * v.y + v.z * v.z);
+        const double hp = (double)h[2 * k + 1], hm = (double)h[2 * k + 2];
+        dm += w * (hp + hm);
+        jx += 0.5 * v.x * w * (hp - hm);
+        jy += 0.5 * v.y * w * (hp - hm);
+        jz += 0.5 * v.z * w * (hp - hm);
+        ek += 0.5 * c2 * w * (hp + hm);
+        gmin = fmin(gmin, fmin(w * (1.0 + hp), w * (1.0 + hm)));
+      });
+    } else {
+      // FP32 arithmetic (FP32 or 16-bit storage): the point's sums come from
+      // its FP32 moments (deviation form, so they carry the 2^-24 rounding of
+      // the deviations, not of rho = 1); FP64 accumulates them across points
+      dm = (double)m.drho;
+      jx = (double)m.j[0];
+      jy = (double)m.j[1];
+      jz = (double)m.j[2];
+      ek = 0.5 * ((double)m.dP[0] + (double)m.dP[1] + (double)m.dP[2]);
+      Real gm = Real(kWeightRest) * (Real(1) + h[0]);
+      static_for<kPairs>([&](auto kc) {
+        constexpr int k = decltype(kc)::value;
+        const Real w = Real(pair_weight(k));
+        gm = fminf(gm, fminf(w * (Real(1) + h[2 * k + 1]), w * (Real(1) + h[2 * k + 2])));
+      });
+      gmin = (double)gm;
+    }
     if (K.paper)
       recover<Real, true>(m, e_in[p], K);
     else
@@ -533,7 +553,10 @@ __global__ void __launch_bounds__(kDiagThreads)
     mix_coeffs(m, K, H);
     const Real beta = K.beta, keep = Real(1) - K.beta;
     auto hterm = [](Real w, Real fw) {  // w (fw ln fw - fw), fw = f/w
-      return fw > Real(0) ? w * (fw * log(fw) - fw) : Real(NAN);
+      if constexpr (sizeof(Real) == 8)
+        return fw > Real(0) ? w * (fw * log(fw) - fw) : Real(NAN);
+      else
+        return fw > Real(0) ? w * (fw * __logf(fw) - fw) : Real(NAN);
     };
     Real Hp = hterm(Real(kWeightRest), Real(1) + keep * h[0] + beta * H.e0);
     static_for<kPairs>([&](auto kc) {

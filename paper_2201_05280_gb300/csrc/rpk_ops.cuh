@@ -7,6 +7,7 @@
 
 #include "rpk_internal.h"
 #include "rpk_kernels.cuh"
+#include "rpk_transport.cuh"
 
 namespace rpk {
 
@@ -143,18 +144,32 @@ static rpk_status transport_launch(rpk_lattice* L, const StepConst<Real>& K) {
     RPK_CUDA(timing_end(L, RPK_KC_TRANSPORT, 2 + L->nsub));
     return check_launch("rotational transport (paper mode)");
   }
-  k_mac_pred<Real, kBC><<<tgrid, tb, 0, L->stream>>>(K, es, ucur, uprev, ea, v, gh);
-  k_mac_corr<Real, kBC><<<tgrid, tb, 0, L->stream>>>(K, es, ea, v, drho, eb, th, gh);
-  // first FTCS sub-step from the stored theta_R; further sub-steps end in e
+  // predictor, corrector and the first FTCS sub-step; further sub-steps end in e
   Real* dst = L->nsub == 1 ? e : ea;
-  k_ftcs_first<Real, kBC><<<tgrid, tb, 0, L->stream>>>(K, eb, th, kap, dst, gh);
+  int launches = 3;
+  if constexpr (kBC == 0) {
+    // periodic grid: one fused pass (intermediates in shared memory)
+    constexpr int bps = sizeof(Real) == 4 ? 4 : 2;
+    const int zc = fused_zchunk(L->grid.nx, L->grid.ny, L->grid.nz, L->sms, bps);
+    const dim3 fgrid((unsigned)(((L->grid.nx + kFTX - 1) / kFTX) * ((L->grid.ny + kFTY - 1) / kFTY) * 2),
+                     (unsigned)((L->grid.nz + zc - 1) / zc));
+    const size_t smem = sizeof(FusedSmem<Real>);
+    RPK_CUDA(cudaFuncSetAttribute(k_transport_fused<Real>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem));
+    k_transport_fused<Real><<<fgrid, kFThreads, smem, L->stream>>>(K, es, ucur, uprev, drho, kap, dst, zc);
+    launches = 1;
+  } else {
+    k_mac_pred<Real, kBC><<<tgrid, tb, 0, L->stream>>>(K, es, ucur, uprev, ea, v, gh);
+    k_mac_corr<Real, kBC><<<tgrid, tb, 0, L->stream>>>(K, es, ea, v, drho, eb, th, gh);
+    k_ftcs_first<Real, kBC><<<tgrid, tb, 0, L->stream>>>(K, eb, th, kap, dst, gh);
+  }
   Real* src = dst;
   for (int k = 1; k < L->nsub; ++k) {
     dst = (k == L->nsub - 1) ? e : (src == ea ? eb : ea);
     k_ftcs<Real, kBC><<<grid, 128, 0, L->stream>>>(K, src, drho, kap, dst, gh);
     src = dst;
   }
-  RPK_CUDA(timing_end(L, RPK_KC_TRANSPORT, 2 + L->nsub));
+  RPK_CUDA(timing_end(L, RPK_KC_TRANSPORT, launches - 1 + L->nsub));
   return check_launch("rotational transport");
 }
 
@@ -283,8 +298,10 @@ rpk_status Ops<Store, Real>::diag(rpk_lattice* L, double out[8]) {
   const Store* pin = static_cast<const Store*>(L->pop[L->cur]);
   const Real* e = static_cast<const Real*>(L->e);
   const Real* gh = static_cast<const Real*>(L->ghost);
+  // one wave of resident blocks (4 per SM in FP32 arithmetic), grid-stride
   const int64_t need = (L->npts + kDiagThreads - 1) / kDiagThreads;
-  const int nblk = (int)std::max<int64_t>(1, std::min<int64_t>(kDiagBlocks, need));
+  const int64_t wave = (int64_t)L->sms * (sizeof(Real) == 4 ? 4 : 1);
+  const int nblk = (int)std::max<int64_t>(1, std::min<int64_t>(std::min<int64_t>(kDiagBlocks, wave), need));
   const Real* wcol = static_cast<const Real*>(L->wrho);
   const bool res = L->grid.bc_x == RPK_BC_RESERVOIR;
   const int wm = wall_mask(L);

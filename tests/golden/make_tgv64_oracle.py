@@ -1,20 +1,31 @@
-"""Writes tgv64_oracle.npz: the FP64 oracle's moment fields of the 3-D
-Taylor-Green vortex at Ma 0.3, Re 1600 (diatomic gas, eta_B/eta = 0.6,
-Pr = 0.71, b = 0) on a 64^3 box of each BCC sublattice after 1000 steps.
+"""Writes tgv64_re<Re>_oracle.npz: the FP64 oracle's moment fields of the
+3-D Taylor-Green vortex at Ma 0.3 (diatomic gas, eta_B/eta = 0.6, Pr = 0.71,
+b = 0) on a 64^3 box of each BCC sublattice.
+
+Two cases of the 512^3 Taylor-Green vortex at Ma 0.3, Re 1600, copied to 64^3:
+  --re 200 --steps 1000   the same lattice viscosity as the 512^3 run
+                          (nu = u0 L / Re with L eight times smaller), i.e.
+                          the same relaxation times and the same per-step
+                          rounding regime of the stored populations;
+  --re 1600 --steps 200   the same Reynolds number; on 64^3 the method itself
+                          breaks down between steps 250 and 300 (the oracle's
+                          state turns non-finite), so it is compared earlier.
 
 The reduced-storage test (tests/test_gpu_tgv64.py) compares the GPU path's
-FP32, FP16-deviation and BF16-deviation storage runs of the same setup with
-these fields point by point. The single-threaded oracle needs about twenty
-minutes for it, so its result is stored once. This script calls only
+FP32, FP16-deviation and BF16-deviation storage runs of the same setups with
+these fields point by point. The single-threaded oracle needs about half an
+hour for 1000 steps, so its results are stored once. This script calls only
 ``oracle/`` and the input generator ``rpk_inputs``; nothing here comes from
 the CUDA library.
 
-Stored (float32 deviations, so that rounding the FP64 values costs at most
-2^-24 of each deviation's own scale): rho - 1, u (3 x npts),
-theta_T - theta0, E_R - delta theta0 / 2, at step 0 and at each step of
-STEPS; the oracle's FP64 totals M, J, E at the same steps; the parameters.
+Stored, on every fourth z plane (z = 0, 4, ..., 60) of both sublattices, as
+float32 deviations (rounding the FP64 values costs at most 2^-24 of each
+deviation's own scale): rho - 1, u (3 components), theta_T - theta0,
+E_R - delta theta0 / 2 at each step of STEPS; the oracle's FP64 totals M, J, E
+at step 0 and at those steps; the parameters.
 
-    python tests/golden/make_tgv64_oracle.py [--n 64] [--steps 1000]
+    python tests/golden/make_tgv64_oracle.py --re 200 --steps 1000
+    python tests/golden/make_tgv64_oracle.py --re 1600 --steps 200
 """
 import argparse
 import os
@@ -31,15 +42,16 @@ import oracle as O  # noqa: E402
 from oracle import params as PM  # noqa: E402
 import rpk_inputs as I  # noqa: E402
 
-MA, RE, LAM, PR, GAMMA = 0.3, 1600.0, 0.6, 0.71, 1.4
+MA, LAM, PR, GAMMA = 0.3, 0.6, 0.71, 1.4
+ZSTRIDE = 4  # stored z planes: 0, 4, 8, ...
 
 
-def setup(n):
-    """Fields and oracle parameters of the n^3 Taylor-Green vortex at Ma 0.3,
-    Re 1600: u0 = Ma c_s, L = n/(2 pi), nu = u0 L / Re."""
+def setup(n, re):
+    """Fields and oracle parameters of the n^3 Taylor-Green vortex at Ma 0.3
+    and Reynolds number re: u0 = Ma c_s, L = n/(2 pi), nu = u0 L / re."""
     t0 = PM.THETA0
     u0 = MA * np.sqrt(GAMMA * t0)
-    nu = u0 * (n / (2.0 * np.pi)) / RE
+    nu = u0 * (n / (2.0 * np.pi)) / re
     eta, etaB, kap = PM.gas_from_nondim(GAMMA, nu, LAM, PR)
     d, tau, tau1, b, kr = PM.relax_from_gas(GAMMA, eta, etaB, kap, 0.0)
     f = I.taylor_green(n, t0, u0)
@@ -49,25 +61,34 @@ def setup(n):
     return f, P, dict(delta=d, tau=tau, tau1=tau1, b=b, k_r=kr, nsub=nsub, nu=nu, u0=u0)
 
 
-def deviations(fl, delta):
+def sample(a, n):
+    """Every ZSTRIDE-th z plane of a field (..., 2, n, n, n) in [s][z][y][x]."""
+    a = np.asarray(a).reshape(a.shape[:-1] + (2, n, n, n))
+    return np.ascontiguousarray(a[..., ::ZSTRIDE, :, :])
+
+
+def deviations(fl, delta, n):
     t0 = PM.THETA0
-    return {"drho": (fl["rho"] - 1.0).astype(np.float32),
-            "u": fl["u"].astype(np.float32),
-            "dT": (fl["T"] - t0).astype(np.float32),
-            "dE": (fl["Erot"] - 0.5 * delta * t0).astype(np.float32)}
+    return {"drho": sample(fl["rho"] - 1.0, n).astype(np.float32),
+            "u": sample(fl["u"], n).astype(np.float32),
+            "dT": sample(fl["T"] - t0, n).astype(np.float32),
+            "dE": sample(fl["Erot"] - 0.5 * delta * t0, n).astype(np.float32)}
 
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--n", type=int, default=64)
+    ap.add_argument("--re", type=float, default=200.0)
     ap.add_argument("--steps", default="1000", help="comma-separated steps to store")
-    ap.add_argument("--out", default=os.path.join(HERE, "tgv64_oracle.npz"))
+    ap.add_argument("--out", default=None)
     a = ap.parse_args()
+    out_path = a.out or os.path.join(HERE, "tgv%d_re%d_oracle.npz" % (a.n, int(a.re)))
     steps = sorted(int(s) for s in a.steps.split(","))
     O.build()
-    f, P, prm = setup(a.n)
+    f, P, prm = setup(a.n, a.re)
     S = O.State(P, a.n, a.n, a.n).init_fields(f["rho"], f["u"], f["T"], f["R"])
-    out = {"n": np.int64(a.n), "steps": np.array(steps, dtype=np.int64)}
+    out = {"n": np.int64(a.n), "re": np.float64(a.re), "zstride": np.int64(ZSTRIDE),
+           "steps": np.array(steps, dtype=np.int64)}
     for k, v in prm.items():
         out["param_" + k] = np.float64(v)
     d0 = S.diag()
@@ -85,13 +106,13 @@ def main():
                      time.time() - t_start), flush=True)
             if not np.all(np.isfinite(fl["rho"])):
                 raise SystemExit("oracle state not finite at step %d" % t)
-        dv = deviations(S.fields(), prm["delta"])
+        dv = deviations(S.fields(), prm["delta"], a.n)
         for k, v in dv.items():
             out["%s_%d" % (k, target)] = v
         dg = S.diag()
         out["diag_%d" % target] = np.array([dg["M"], *dg["J"], dg["E"]])
-    np.savez_compressed(a.out, **out)
-    print("wrote", a.out, os.path.getsize(a.out), "bytes")
+    np.savez_compressed(out_path, **out)
+    print("wrote", out_path, os.path.getsize(out_path), "bytes")
 
 
 if __name__ == "__main__":

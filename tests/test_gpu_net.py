@@ -22,8 +22,14 @@ import paper_2201_05280_gb300 as rpk
 
 pytestmark = pytest.mark.gpu
 
-ELEM_FWD = 2e-2
-ELEM_GRAD = 5e-2
+# Element-wise bars against the BF16-rounded oracle, on the scale of each
+# tensor's largest element: a BF16 rounding flip moves one operand by one
+# BF16 step (2^-8 relative), and an output element sums a few such flips
+# through up to 6 (forward) or 11 (gradients) contractions in series.
+# Measured on GB300: forward <= 7.4e-4, gradients <= 5.1e-3 (the first
+# block convolution's weights); the bars are about 3x that.
+ELEM_FWD = 3e-3
+ELEM_GRAD = 1.5e-2
 
 
 @pytest.fixture(scope="module", autouse=True)

@@ -2,7 +2,9 @@
 as h = g/w - 1 in FP16 or BF16, arithmetic in FP32).
 
 Stated bounds: relative L-inf against the oracle for rho, theta_T, E_rot; for
-u the scale is max(max|u|, c_s) (see test_gpu_parity). Each step rounds every
+u the scale is max(max|u|, c_s) (see test_gpu_parity). A second set bounds
+the same errors on the deviation scale, the largest departure of each field
+from the rest state. Each step rounds every
 stored h once (unit roundoff 2^-24 for FP32, 2^-11 for FP16, 2^-8 for BF16),
 with errors of order u_r |h| per step that add up nearly linearly in smooth
 flows. The bounds below are about 3x the errors measured on GB300:
@@ -28,11 +30,16 @@ WAVE_BOUNDS = {"f32": (1e-5, 1e-5, 1e-5, 1e-5), "f16dev": (5e-6, 5e-6, 5e-6, 5e-
                "bf16dev": (5e-5, 5e-5, 5e-5, 5e-5)}
 TGV_BOUNDS = {"f32": (1e-5, 3e-5, 1e-5, 1e-5), "f16dev": (2e-3, 2e-3, 2e-3, 2e-3),
               "bf16dev": (2e-2, 2e-2, 2e-2, 2e-2)}
-# the same errors on the deviation scale (max|ref - rest state| per field)
-WAVE_DEV_BOUNDS = {"f32": (1.0, 1.0, 1.0, 1.0), "f16dev": (1.0, 1.0, 1.0, 1.0),
-                   "bf16dev": (1.0, 1.0, 1.0, 1.0)}
-TGV_DEV_BOUNDS = {"f32": (1.0, 1.0, 1.0, 1.0), "f16dev": (1.0, 1.0, 1.0, 1.0),
-                  "bf16dev": (1.0, 1.0, 1.0, 1.0)}
+# The same errors on the scale of the flow itself (max|ref - rest state| per
+# field: rho - 1, u, theta_T - theta0, E_R - delta theta0 / 2), about 3x the
+# errors measured on GB300 (wave field / Taylor-Green):
+#   FP32  1.2e-4 / 8.3e-5     FP16  1.1e-3 / 3.2e-2     BF16  9.7e-3 / 2.7e-1
+# BF16 deviation storage keeps about one significant digit of the Taylor-Green
+# flow after 200 steps: 8 bits of h ~ 1 cannot resolve a deviation of 0.05.
+WAVE_DEV_BOUNDS = {"f32": (3e-4, 4e-4, 3e-4, 4e-4), "f16dev": (1.5e-3, 1.5e-3, 3e-3, 1.5e-3),
+                   "bf16dev": (2e-2, 1.5e-2, 3e-2, 1.5e-2)}
+TGV_DEV_BOUNDS = {"f32": (2.5e-4, 2e-4, 2.5e-4, 2.5e-4), "f16dev": (6e-2, 1e-2, 7e-2, 1e-1),
+                  "bf16dev": (0.6, 0.1, 0.65, 0.8)}
 
 
 @pytest.fixture(scope="module", autouse=True)

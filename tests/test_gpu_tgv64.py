@@ -1,0 +1,118 @@
+"""Reduced-storage precision on the Taylor-Green vortex at Ma 0.3 (the 512^3,
+Re 1600 workload copied to 64^3), against the FP64 oracle point by point.
+
+The oracle's fields are stored in tests/golden/tgv64_re*_oracle.npz by
+tests/golden/make_tgv64_oracle.py (which calls only the oracle): every fourth
+z plane of both sublattices, as float32 deviations from the rest state.
+Two copies of the 512^3 run:
+  Re 200, 1000 steps   the 512^3 run's lattice viscosity (nu = 9.9e-3), so the
+                       same relaxation times and per-step rounding of the
+                       stored populations; laminar, about 19 convective times
+  Re 1600, 200 steps   the 512^3 run's Reynolds number; on 64^3 the method
+                       itself breaks down between steps 250 and 300 (the FP64
+                       oracle's state turns non-finite), so it is compared at
+                       step 200
+Each storage (FP64, FP32, FP16 and BF16 deviations h = g/w - 1) is run with
+the oracle's parameters and FTCS sub-step count. Errors are max|gpu - oracle|
+on two scales: the full field (max|oracle|; c_s for u) and the deviation
+(max|oracle - rest state|: rho = 1, u = 0, theta0, delta theta0 / 2). The
+FP64 drift of the totals M, E (rpk_diagnostics) over the run is bounded per
+storage. Bounds are about 3x the errors measured on GB300 (the design doc lists
+the measured values).
+"""
+import os
+
+import numpy as np
+import pytest
+
+import paper_2201_05280_gb300 as rpk
+
+pytestmark = pytest.mark.gpu
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+T0 = 0.2948964908710633
+CS = float(np.sqrt(1.4 * T0))
+KEYS = ("rho", "u", "T", "Erot")
+STORED = {"rho": "drho", "u": "u", "T": "dT", "Erot": "dE"}
+CASES = {"re200": "tgv64_re200_oracle.npz", "re1600": "tgv64_re1600_oracle.npz"}
+
+# bounds per case and storage: (full scale, deviation scale) for rho, u, theta_T, E_R,
+# and (|dM|/M, |dE|/E) over the run
+BOUNDS = {
+    "re200": {
+        "f64": ((1e-6,) * 4, (1e-6,) * 4, (1e-12, 1e-12)),
+        "f32": ((1.0,) * 4, (1.0,) * 4, (1.0, 1.0)),
+        "f16dev": ((1.0,) * 4, (1.0,) * 4, (1.0, 1.0)),
+        "bf16dev": ((1.0,) * 4, (1.0,) * 4, (1.0, 1.0)),
+    },
+    "re1600": {
+        "f64": ((1e-6,) * 4, (1e-6,) * 4, (1e-12, 1e-12)),
+        "f32": ((1.0,) * 4, (1.0,) * 4, (1.0, 1.0)),
+        "f16dev": ((1.0,) * 4, (1.0,) * 4, (1.0, 1.0)),
+        "bf16dev": ((1.0,) * 4, (1.0,) * 4, (1.0, 1.0)),
+    },
+}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    from paper_2201_05280_gb300 import build as B
+    B.build()
+    import torch
+    assert torch.cuda.is_available()
+    torch.cuda.set_device(0)
+
+
+def _load(case):
+    z = np.load(os.path.join(HERE, "golden", CASES[case]))
+    n, zs = int(z["n"]), int(z["zstride"])
+    step = int(z["steps"][-1])
+    ref = {k: z["%s_%d" % (STORED[k], step)].astype(np.float64) for k in KEYS}
+    relax = {k: float(z["param_" + k]) for k in ("delta", "tau", "tau1", "b", "k_r")}
+    relax["nsub"] = int(z["param_nsub"])
+    return n, zs, step, ref, relax, float(z["param_u0"]), z["diag0"], z["diag_%d" % step]
+
+
+def _sample(a, n, zs):
+    a = np.asarray(a).reshape(a.shape[:-1] + (2, n, n, n))
+    return a[..., ::zs, :, :]
+
+
+@pytest.mark.parametrize("case", ["re200", "re1600"])
+@pytest.mark.parametrize("prec", ["f64", "f32", "f16dev", "bf16dev"])
+def test_taylor_green_64_storage_against_oracle(case, prec):
+    import rpk_inputs as I
+    n, zs, step, ref, relax, u0, dg0, dg1 = _load(case)
+    f = I.taylor_green(n, T0, u0)
+    lat = rpk.Lattice(n, n, n, precision=prec).set_relax(**relax)
+    lat.init_fields(f["rho"], f["u"], f["T"], f["R"])
+    d0 = lat.diagnostics()
+    lat.step(step)
+    d1 = lat.diagnostics()
+    got = lat.read_moments()
+    lat.close()
+    base = {"rho": 1.0, "u": 0.0, "T": T0, "Erot": 0.5 * relax["delta"] * T0}
+    full, dev = {}, {}
+    for k in KEYS:
+        g = _sample(got[k], n, zs) - base[k]   # deviations, as stored
+        r = ref[k]
+        assert g.shape == r.shape, (k, g.shape, r.shape)
+        err = np.abs(g - r).max()
+        scale = max(np.abs(r).max(), CS) if k == "u" else np.abs(r + base[k]).max()
+        full[k] = float(err / scale)
+        dev[k] = float(err / np.abs(r).max())
+    drift = (abs(d1["M"] - d0["M"]) / d0["M"], abs(d1["E"] - d0["E"]) / d0["E"])
+    print("TGV64 %s %s step %d: full %s dev %s drift M %.2e E %.2e"
+          % (case, prec, step, {k: "%.2e" % v for k, v in full.items()},
+             {k: "%.2e" % v for k, v in dev.items()}, drift[0], drift[1]))
+    if prec == "f64":
+        # the oracle's own totals agree with the GPU's FP64 sums
+        assert abs(d0["M"] - dg0[0]) <= 1e-12 * dg0[0]
+        assert abs(d1["E"] - dg1[4]) <= 1e-12 * dg1[4]
+    fb, db, cb = BOUNDS[case][prec]
+    for k, b in zip(KEYS, fb):
+        assert full[k] <= b, ("full", k, full[k], b)
+    for k, b in zip(KEYS, db):
+        assert dev[k] <= b, ("deviation", k, dev[k], b)
+    assert drift[0] <= cb[0] and drift[1] <= cb[1], drift
+    assert d1["status"] == 0
