@@ -3,39 +3,48 @@
 #pragma once
 
 #include "rpk_device.cuh"
+#include "rpk_pair.cuh"
 
 namespace rpk {
 
-// One collision per point after the pull (Sec. 5):
+// Collision of one gathered point (or pair of points, V = F2), in place of
+// the paper's explicit update (Sec. 5):
 //   g' = (1 - 2 beta*) g + 2 beta* f^mix,   in h form: h' = c_keep h + c_relax (f^mix/w - 1)
 //   Er' = Er + dt (delta rho/2)(theta - theta_R)/tau1   (rotational exchange)
-// Writes h', e', rho - 1, u (ring slot of this step) and kappa_R.
-// Collision of one gathered point, in place of the paper's explicit update:
-// writes the 41 relaxed populations through `out` (element q at out[q * n3]),
-// returns the moments in m and the exchanged auxiliary rotational energy.
-template <typename Store, typename Real, bool kPaper = false>
-__device__ __forceinline__ Real collide_point(const StepConst<Real>& K, const Real (&h)[kQ], Real e,
-                                              Store* __restrict__ out, Mom<Real>& m) {
+// hands the 41 relaxed populations to emit(q, value) in the order q = 0, 1, 2,
+// ..., returns the moments in m and the exchanged auxiliary rotational energy
+// (paper mode: theta_R after the first backward-Euler half step).
+template <typename Real, bool kPaper = false, typename V, typename Emit>
+__device__ __forceinline__ V collide_emit(const StepConst<Real>& K, const V (&h)[kQ], V e, Emit&& emit,
+                                          Mom<V>& m) {
   raw_moments(h, m);
   recover<Real, kPaper>(m, e, K);
-  Herm<Real> H;
+  Herm<V> H;
   mix_coeffs(m, K, H);
-  const int64_t n3 = K.n3;
-  out[0] = from_real<Store, Real>(K.c_keep * h[0] + K.c_relax * H.e0);
+  emit(0, fmad(K.c_keep, h[0], K.c_relax * H.e0));
   static_for<kPairs>([&](auto kc) {
     constexpr int k = decltype(kc)::value;
     constexpr Vel2 v = kPairVel2[k];
-    const Real ev = herm_even<v.x, v.y, v.z>(H);
-    const Real od = herm_odd<v.x, v.y, v.z>(H);
-    out[(int64_t)(2 * k + 1) * n3] = from_real<Store, Real>(K.c_keep * h[2 * k + 1] + K.c_relax * (ev + od));
-    out[(int64_t)(2 * k + 2) * n3] = from_real<Store, Real>(K.c_keep * h[2 * k + 2] + K.c_relax * (ev - od));
+    const V ev = herm_even<v.x, v.y, v.z>(H);
+    const V od = herm_odd<v.x, v.y, v.z>(H);
+    emit(2 * k + 1, fmad(K.c_keep, h[2 * k + 1], K.c_relax * (ev + od)));
+    emit(2 * k + 2, fmad(K.c_keep, h[2 * k + 2], K.c_relax * (ev - od)));
   });
   // conservative form: the exchanged auxiliary energy; paper mode: theta_R after
   // the first backward-Euler half step with the time-t theta_T (Sec. 5, step 1)
   if constexpr (kPaper)
-    return K.ra_keep * m.dR + K.ra_t * m.dT;
+    return fmad(K.ra_keep, m.dR, K.ra_t * m.dT);
   else
-    return e + K.exc * m.rho * (m.dth - m.dR);
+    return fmad(K.exc * m.rho, m.dth - m.dR, e);
+}
+
+// One point: the populations go to out[q * n3].
+template <typename Store, typename Real, bool kPaper = false>
+__device__ __forceinline__ Real collide_point(const StepConst<Real>& K, const Real (&h)[kQ], Real e,
+                                              Store* __restrict__ out, Mom<Real>& m) {
+  const int64_t n3 = K.n3;
+  return collide_emit<Real, kPaper>(
+      K, h, e, [&](int q, Real v) { out[(int64_t)q * n3] = from_real<Store, Real>(v); }, m);
 }
 
 // Device status flags: 1 non-finite moment, 2 rho <= 0, 4 theta_T or theta_R <= 0.
@@ -82,6 +91,63 @@ __global__ void __launch_bounds__(128, sizeof(Real) == 4 ? 5 : 1)
   kap_out[p] = K.kapc * m.rho * (K.theta0 + m.dth);
   if constexpr (kPaper) tt_out[p] = m.dT;  // paper mode: theta_T(f) - theta0 of time t
   flag_moments(m, K.theta0, status);
+}
+
+}  // namespace rpk
+
+namespace rpk {
+
+// Status flags of two points (as flag_moments).
+__device__ __forceinline__ void flag_moments2(const Mom<F2>& m, float theta0, unsigned* __restrict__ status) {
+  const float rho[2] = {m.rho.v.x, m.rho.v.y}, dT[2] = {m.dT.v.x, m.dT.v.y}, dR[2] = {m.dR.v.x, m.dR.v.y};
+#pragma unroll
+  for (int l = 0; l < 2; ++l) {
+    const bool ok = (rho[l] > 0.0f) && (theta0 + dT[l] > 0.0f) && (theta0 + dR[l] > 0.0f);
+    if (!ok) {
+      unsigned f = 0;
+      if (!(rho[l] == rho[l]) || !(dT[l] == dT[l]) || !(dR[l] == dR[l])) f |= 1u;
+      if (!(rho[l] > 0.0f)) f |= 2u;
+      if (!(theta0 + dT[l] > 0.0f) || !(theta0 + dR[l] > 0.0f)) f |= 4u;
+      atomicOr(status, f);
+    }
+  }
+}
+
+// The pull-stream + collide + exchange step of k_collide for two x-adjacent
+// points per thread on a periodic grid with nx even, FP32 arithmetic in
+// packed FP32x2 form (same numbers as the one-point kernel's FP32 path, half
+// the arithmetic instructions; pair words halve the loads and stores).
+// Thread (blockIdx.x * blockDim.x + threadIdx.x) owns x0 = 2 * that index.
+template <typename Store>
+__global__ void __launch_bounds__(128, 3)
+    k_collide_pair(StepConst<float> K, const Store* __restrict__ pin, Store* __restrict__ pout,
+                   const float* __restrict__ e_in, float* __restrict__ e_out, float* __restrict__ drho_out,
+                   float* __restrict__ u_out, float* __restrict__ kap_out, unsigned* __restrict__ status) {
+  using IO = PairIO<Store>;
+  using Word = typename IO::Word;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (K.nx >> 1)) return;
+  const int y = blockIdx.y;
+  const int s = blockIdx.z / K.nz;
+  const int z = blockIdx.z - s * K.nz;
+  const int64_t n3p = K.n3 >> 1;                                     // pairs per sublattice
+  const int64_t cellp = ((((int64_t)z * K.ny + y) * K.nx) >> 1) + i;  // pair of the cell
+  const int64_t pp = (int64_t)s * n3p + cellp;                        // pair in a field plane
+  F2 h[kQ];
+  gather_pair<Store>(reinterpret_cast<const Word*>(pin), K, s, i, y, z, h);
+  Mom<F2> m;
+  Word* out = reinterpret_cast<Word*>(pout) + (int64_t)(s * kQ) * n3p + cellp;
+  const F2 es = collide_emit<float, false>(
+      K, h, F2(reinterpret_cast<const float2*>(e_in)[pp]),
+      [&](int q, F2 v) { out[(int64_t)q * n3p] = IO::from_f2(v); }, m);
+  reinterpret_cast<float2*>(e_out)[pp] = es.v;
+  reinterpret_cast<float2*>(drho_out)[pp] = m.drho.v;
+  float2* u2 = reinterpret_cast<float2*>(u_out);
+  u2[pp] = (m.j[0] * m.inv_rho).v;
+  u2[K.n3 + pp] = (m.j[1] * m.inv_rho).v;
+  u2[2 * K.n3 + pp] = (m.j[2] * m.inv_rho).v;
+  reinterpret_cast<float2*>(kap_out)[pp] = (K.kapc * m.rho * (K.theta0 + m.dth)).v;
+  flag_moments2(m, K.theta0, status);
 }
 
 }  // namespace rpk

@@ -24,6 +24,7 @@
 #include <utility>
 
 #include "rpk_lattice.cuh"
+#include "rpk_vec2.cuh"
 
 namespace rpk {
 
@@ -113,31 +114,33 @@ struct Mom {
   Real sig[6];   // sigma(f), a density
 };
 
-// rho, j, P of g = w (1 + h), pair by pair.
-template <typename Real>
-__device__ __forceinline__ void raw_moments(const Real (&h)[kQ], Mom<Real>& m) {
-  Real d = Real(kWeightRest) * h[0];
-  Real jx = 0, jy = 0, jz = 0, pxx = 0, pyy = 0, pzz = 0, pxy = 0, pxz = 0, pyz = 0;
+// rho, j, P of g = w (1 + h), pair by pair. Generic over the value type V
+// (float, double, or F2 = the same quantity at two points).
+template <typename V>
+__device__ __forceinline__ void raw_moments(const V (&h)[kQ], Mom<V>& m) {
+  using S = scalar_t<V>;
+  V d = S(kWeightRest) * h[0];
+  V jx = splat<V>(0), jy = jx, jz = jx, pxx = jx, pyy = jx, pzz = jx, pxy = jx, pxz = jx, pyz = jx;
   static_for<kPairs>([&](auto kc) {
     constexpr int k = decltype(kc)::value;
     constexpr Vel2 v = kPairVel2[k];
     constexpr double w = pair_weight(k);
-    const Real ev = Real(w) * (h[2 * k + 1] + h[2 * k + 2]);
-    const Real od = Real(w) * (h[2 * k + 1] - h[2 * k + 2]);
+    const V ev = S(w) * (h[2 * k + 1] + h[2 * k + 2]);
+    const V od = S(w) * (h[2 * k + 1] - h[2 * k + 2]);
     d += ev;
-    if constexpr (v.x != 0) jx += Real(0.5 * v.x) * od;
-    if constexpr (v.y != 0) jy += Real(0.5 * v.y) * od;
-    if constexpr (v.z != 0) jz += Real(0.5 * v.z) * od;
-    if constexpr (v.x != 0) pxx += Real(0.25 * v.x * v.x) * ev;
-    if constexpr (v.y != 0) pyy += Real(0.25 * v.y * v.y) * ev;
-    if constexpr (v.z != 0) pzz += Real(0.25 * v.z * v.z) * ev;
-    if constexpr (v.x * v.y != 0) pxy += Real(0.25 * v.x * v.y) * ev;
-    if constexpr (v.x * v.z != 0) pxz += Real(0.25 * v.x * v.z) * ev;
-    if constexpr (v.y * v.z != 0) pyz += Real(0.25 * v.y * v.z) * ev;
+    if constexpr (v.x != 0) jx = fmad(S(0.5 * v.x), od, jx);
+    if constexpr (v.y != 0) jy = fmad(S(0.5 * v.y), od, jy);
+    if constexpr (v.z != 0) jz = fmad(S(0.5 * v.z), od, jz);
+    if constexpr (v.x != 0) pxx = fmad(S(0.25 * v.x * v.x), ev, pxx);
+    if constexpr (v.y != 0) pyy = fmad(S(0.25 * v.y * v.y), ev, pyy);
+    if constexpr (v.z != 0) pzz = fmad(S(0.25 * v.z * v.z), ev, pzz);
+    if constexpr (v.x * v.y != 0) pxy = fmad(S(0.25 * v.x * v.y), ev, pxy);
+    if constexpr (v.x * v.z != 0) pxz = fmad(S(0.25 * v.x * v.z), ev, pxz);
+    if constexpr (v.y * v.z != 0) pyz = fmad(S(0.25 * v.y * v.z), ev, pyz);
   });
   m.drho = d;
-  m.rho = Real(1) + d;
-  m.inv_rho = Real(1) / m.rho;
+  m.rho = S(1) + d;
+  m.inv_rho = S(1) / m.rho;
   m.j[0] = jx; m.j[1] = jy; m.j[2] = jz;
   m.dP[0] = pxx; m.dP[1] = pyy; m.dP[2] = pzz;
   m.dP[3] = pxy; m.dP[4] = pxz; m.dP[5] = pyz;
@@ -153,26 +156,27 @@ __device__ __forceinline__ void raw_moments(const Real (&h)[kQ], Mom<Real>& m) {
 //   D = (theta_T(g) - Rt)/(1 + dt/(2 tau1)) = theta_T(f) - theta_R
 //   theta_T(f) = theta + delta D/(3 + delta),  theta_R = theta - 3 D/(3 + delta)
 //   sigma(f) = (P - jj/rho - rho theta_T(g) I)/(1 + dt/(2 tau*) - b dt/(2 tau))
-template <typename Real, bool kPaper = false>
-__device__ __forceinline__ void recover(Mom<Real>& m, Real e, const StepConst<Real>& K) {
-  const Real t0 = K.theta0;
-  const Real jj = m.j[0] * m.j[0] + m.j[1] * m.j[1] + m.j[2] * m.j[2];
-  const Real trdP = m.dP[0] + m.dP[1] + m.dP[2];
-  m.dTg = (trdP - jj * m.inv_rho - Real(3) * t0 * m.drho) * m.inv_rho * Real(1.0 / 3.0);
+template <typename Real, bool kPaper = false, typename V>
+__device__ __forceinline__ void recover(Mom<V>& m, V e, const StepConst<Real>& K) {
+  using S = scalar_t<V>;
+  const S t0 = K.theta0;
+  const V jj = fmad(m.j[2], m.j[2], fmad(m.j[1], m.j[1], m.j[0] * m.j[0]));
+  const V trdP = m.dP[0] + m.dP[1] + m.dP[2];
+  m.dTg = (trdP - jj * m.inv_rho - S(3) * t0 * m.drho) * m.inv_rho * S(1.0 / 3.0);
   if constexpr (kPaper) {
     // paper mode: e is theta_R - theta0 itself
     m.dR = e;
-    m.dT = (m.dTg + K.pa * m.dR) * K.inv_1pa;
-    m.dth = (Real(3) * m.dT + K.delta * m.dR) * K.inv_3pd;
+    m.dT = fmad(K.pa, m.dR, m.dTg) * K.inv_1pa;
+    m.dth = fmad(K.delta, m.dR, S(3) * m.dT) * K.inv_3pd;
   } else {
-    const Real dRt = (Real(2) * e - K.delta * t0 * m.drho) * m.inv_rho / K.delta;
-    m.dth = (Real(3) * m.dTg + K.delta * dRt) * K.inv_3pd;
-    const Real D = (m.dTg - dRt) * K.inv_d;
-    m.dT = m.dth + K.delta * D * K.inv_3pd;
-    m.dR = m.dth - Real(3) * D * K.inv_3pd;
+    const V dRt = (S(2) * e - K.delta * t0 * m.drho) * m.inv_rho / K.delta;
+    m.dth = fmad(K.delta, dRt, S(3) * m.dTg) * K.inv_3pd;
+    const V D = (m.dTg - dRt) * K.inv_d;
+    m.dT = fmad(K.delta * K.inv_3pd, D, m.dth);
+    m.dR = m.dth - (S(3) * K.inv_3pd) * D;
   }
-  const Real iso = m.rho * m.dTg + t0 * m.drho;
-  const Real ir = m.inv_rho;
+  const V iso = fmad(t0, m.drho, m.rho * m.dTg);
+  const V ir = m.inv_rho;
   m.sig[0] = (m.dP[0] - m.j[0] * m.j[0] * ir - iso) * K.inv_sig;
   m.sig[1] = (m.dP[1] - m.j[1] * m.j[1] * ir - iso) * K.inv_sig;
   m.sig[2] = (m.dP[2] - m.j[2] * m.j[2] * ir - iso) * K.inv_sig;
@@ -193,47 +197,50 @@ struct Herm {
   Real oxxx, oyyy, ozzz, oxxy, oxxz, oyyx, oyyz, ozzx, ozzy, oxyz;
 };
 
-template <typename Real>
-__device__ __forceinline__ void hermite(Real drho, Real rho, Real inv_rho, const Real (&j)[3],
-                                        const Real (&Dl)[6], Real t0, Herm<Real>& H) {
-  const Real jx = j[0], jy = j[1], jz = j[2];
-  const Real a2xx = jx * jx * inv_rho + rho * Dl[0];
-  const Real a2yy = jy * jy * inv_rho + rho * Dl[1];
-  const Real a2zz = jz * jz * inv_rho + rho * Dl[2];
-  const Real a2xy = jx * jy * inv_rho + rho * Dl[3];
-  const Real a2xz = jx * jz * inv_rho + rho * Dl[4];
-  const Real a2yz = jy * jz * inv_rho + rho * Dl[5];
-  const Real ir2 = inv_rho * inv_rho;
-  const Real dxx = Dl[0], dyy = Dl[1], dzz = Dl[2], dxy = Dl[3], dxz = Dl[4], dyz = Dl[5];
-  const Real a3xxx = jx * jx * jx * ir2 + Real(3) * dxx * jx;
-  const Real a3yyy = jy * jy * jy * ir2 + Real(3) * dyy * jy;
-  const Real a3zzz = jz * jz * jz * ir2 + Real(3) * dzz * jz;
-  const Real a3xxy = jx * jx * jy * ir2 + dxx * jy + Real(2) * dxy * jx;
-  const Real a3xxz = jx * jx * jz * ir2 + dxx * jz + Real(2) * dxz * jx;
-  const Real a3yyx = jy * jy * jx * ir2 + dyy * jx + Real(2) * dxy * jy;
-  const Real a3yyz = jy * jy * jz * ir2 + dyy * jz + Real(2) * dyz * jy;
-  const Real a3zzx = jz * jz * jx * ir2 + dzz * jx + Real(2) * dxz * jz;
-  const Real a3zzy = jz * jz * jy * ir2 + dzz * jy + Real(2) * dyz * jz;
-  const Real a3xyz = jx * jy * jz * ir2 + dxy * jz + dyz * jx + dxz * jy;
-  const Real i1 = Real(1) / t0;
-  const Real i2 = i1 * i1;
-  const Real i3 = i2 * i1;
+template <typename V>
+__device__ __forceinline__ void hermite(V drho, V rho, V inv_rho, const V (&j)[3], const V (&Dl)[6],
+                                        scalar_t<V> t0, Herm<V>& H) {
+  using S = scalar_t<V>;
+  const V jx = j[0], jy = j[1], jz = j[2];
+  const V jxr = jx * inv_rho, jyr = jy * inv_rho, jzr = jz * inv_rho;
+  const V a2xx = fmad(jx, jxr, rho * Dl[0]);
+  const V a2yy = fmad(jy, jyr, rho * Dl[1]);
+  const V a2zz = fmad(jz, jzr, rho * Dl[2]);
+  const V a2xy = fmad(jx, jyr, rho * Dl[3]);
+  const V a2xz = fmad(jx, jzr, rho * Dl[4]);
+  const V a2yz = fmad(jy, jzr, rho * Dl[5]);
+  // j_a j_b j_c / rho^2 = (j_a j_b / rho)(j_c / rho)
+  const V xx = jx * jxr, yy = jy * jyr, zz = jz * jzr;
+  const V dxx = Dl[0], dyy = Dl[1], dzz = Dl[2], dxy = Dl[3], dxz = Dl[4], dyz = Dl[5];
+  const V a3xxx = fmad(S(3) * dxx, jx, xx * jxr);
+  const V a3yyy = fmad(S(3) * dyy, jy, yy * jyr);
+  const V a3zzz = fmad(S(3) * dzz, jz, zz * jzr);
+  const V a3xxy = fmad(dxx, jy, fmad(S(2) * dxy, jx, xx * jyr));
+  const V a3xxz = fmad(dxx, jz, fmad(S(2) * dxz, jx, xx * jzr));
+  const V a3yyx = fmad(dyy, jx, fmad(S(2) * dxy, jy, yy * jxr));
+  const V a3yyz = fmad(dyy, jz, fmad(S(2) * dyz, jy, yy * jzr));
+  const V a3zzx = fmad(dzz, jx, fmad(S(2) * dxz, jz, zz * jxr));
+  const V a3zzy = fmad(dzz, jy, fmad(S(2) * dyz, jz, zz * jyr));
+  const V a3xyz = fmad(dxy, jz, fmad(dyz, jx, fmad(dxz, jy, (jx * jyr) * jzr)));
+  const S i1 = S(1) / t0;
+  const S i2 = i1 * i1;
+  const S i3 = i2 * i1;
   // even part
-  H.e0 = drho - Real(0.5) * i1 * (a2xx + a2yy + a2zz);
-  H.exx = Real(0.5) * i2 * a2xx;
-  H.eyy = Real(0.5) * i2 * a2yy;
-  H.ezz = Real(0.5) * i2 * a2zz;
+  H.e0 = drho - (S(0.5) * i1) * (a2xx + a2yy + a2zz);
+  H.exx = (S(0.5) * i2) * a2xx;
+  H.eyy = (S(0.5) * i2) * a2yy;
+  H.ezz = (S(0.5) * i2) * a2zz;
   H.exy = i2 * a2xy;
   H.exz = i2 * a2xz;
   H.eyz = i2 * a2yz;
   // odd part: j.c/t0 - t0 * 3 V.c/(6 t0^3), V_a = sum_b A3_abb
-  const Real vx = a3xxx + a3yyx + a3zzx;
-  const Real vy = a3xxy + a3yyy + a3zzy;
-  const Real vz = a3xxz + a3yyz + a3zzz;
-  H.ox = jx * i1 - Real(0.5) * i2 * vx;
-  H.oy = jy * i1 - Real(0.5) * i2 * vy;
-  H.oz = jz * i1 - Real(0.5) * i2 * vz;
-  const Real s6 = i3 * Real(1.0 / 6.0), s2 = i3 * Real(0.5);
+  const V vx = a3xxx + a3yyx + a3zzx;
+  const V vy = a3xxy + a3yyy + a3zzy;
+  const V vz = a3xxz + a3yyz + a3zzz;
+  H.ox = fmad(-S(0.5) * i2, vx, jx * i1);
+  H.oy = fmad(-S(0.5) * i2, vy, jy * i1);
+  H.oz = fmad(-S(0.5) * i2, vz, jz * i1);
+  const S s6 = i3 * S(1.0 / 6.0), s2 = i3 * S(0.5);
   H.oxxx = s6 * a3xxx;
   H.oyyy = s6 * a3yyy;
   H.ozzz = s6 * a3zzz;
@@ -246,43 +253,44 @@ __device__ __forceinline__ void hermite(Real drho, Real rho, Real inv_rho, const
   H.oxyz = i3 * a3xyz;
 }
 
-template <int VX, int VY, int VZ, typename Real>
-__device__ __forceinline__ Real herm_even(const Herm<Real>& H) {
+template <int VX, int VY, int VZ, typename V>
+__device__ __forceinline__ V herm_even(const Herm<V>& H) {
+  using S = scalar_t<V>;
   constexpr double cx = 0.5 * VX, cy = 0.5 * VY, cz = 0.5 * VZ;
-  Real r = H.e0;
-  if constexpr (VX != 0) r += Real(cx * cx) * H.exx;
-  if constexpr (VY != 0) r += Real(cy * cy) * H.eyy;
-  if constexpr (VZ != 0) r += Real(cz * cz) * H.ezz;
-  if constexpr (VX * VY != 0) r += Real(cx * cy) * H.exy;
-  if constexpr (VX * VZ != 0) r += Real(cx * cz) * H.exz;
-  if constexpr (VY * VZ != 0) r += Real(cy * cz) * H.eyz;
+  V r = H.e0;
+  if constexpr (VX != 0) r = fmad(S(cx * cx), H.exx, r);
+  if constexpr (VY != 0) r = fmad(S(cy * cy), H.eyy, r);
+  if constexpr (VZ != 0) r = fmad(S(cz * cz), H.ezz, r);
+  if constexpr (VX * VY != 0) r = fmad(S(cx * cy), H.exy, r);
+  if constexpr (VX * VZ != 0) r = fmad(S(cx * cz), H.exz, r);
+  if constexpr (VY * VZ != 0) r = fmad(S(cy * cz), H.eyz, r);
   return r;
 }
 
-template <int VX, int VY, int VZ, typename Real>
-__device__ __forceinline__ Real herm_odd(const Herm<Real>& H) {
+template <int VX, int VY, int VZ, typename V>
+__device__ __forceinline__ V herm_odd(const Herm<V>& H) {
+  using S = scalar_t<V>;
   constexpr double cx = 0.5 * VX, cy = 0.5 * VY, cz = 0.5 * VZ;
-  Real r = Real(0);
-  if constexpr (VX != 0) r += Real(cx) * H.ox + Real(cx * cx * cx) * H.oxxx;
-  if constexpr (VY != 0) r += Real(cy) * H.oy + Real(cy * cy * cy) * H.oyyy;
-  if constexpr (VZ != 0) r += Real(cz) * H.oz + Real(cz * cz * cz) * H.ozzz;
-  if constexpr (VX * VY != 0) r += Real(cx * cx * cy) * H.oxxy + Real(cy * cy * cx) * H.oyyx;
-  if constexpr (VX * VZ != 0) r += Real(cx * cx * cz) * H.oxxz + Real(cz * cz * cx) * H.ozzx;
-  if constexpr (VY * VZ != 0) r += Real(cy * cy * cz) * H.oyyz + Real(cz * cz * cy) * H.ozzy;
-  if constexpr (VX * VY * VZ != 0) r += Real(cx * cy * cz) * H.oxyz;
+  V r = splat<V>(0);
+  if constexpr (VX != 0) r = fmad(S(cx * cx * cx), H.oxxx, fmad(S(cx), H.ox, r));
+  if constexpr (VY != 0) r = fmad(S(cy * cy * cy), H.oyyy, fmad(S(cy), H.oy, r));
+  if constexpr (VZ != 0) r = fmad(S(cz * cz * cz), H.ozzz, fmad(S(cz), H.oz, r));
+  if constexpr (VX * VY != 0) r = fmad(S(cy * cy * cx), H.oyyx, fmad(S(cx * cx * cy), H.oxxy, r));
+  if constexpr (VX * VZ != 0) r = fmad(S(cz * cz * cx), H.ozzx, fmad(S(cx * cx * cz), H.oxxz, r));
+  if constexpr (VY * VZ != 0) r = fmad(S(cz * cz * cy), H.ozzy, fmad(S(cy * cy * cz), H.oyyz, r));
+  if constexpr (VX * VY * VZ != 0) r = fmad(S(cx * cy * cz), H.oxyz, r);
   return r;
 }
 
 // Hermite coefficients of f^mix = tau*(f^ES/tau + f^Eq/tau1) (Sec. 5): both
 // targets share rho and u and are linear in Lambda, so
 //   Lambda_mix = (tau*/tau)(theta_T I + b sigma/rho) + (tau*/tau1) theta I.
-template <typename Real>
-__device__ __forceinline__ void mix_coeffs(const Mom<Real>& m, const StepConst<Real>& K,
-                                           Herm<Real>& H) {
-  const Real iso = K.w_es * m.dT + K.w_eq * m.dth;
-  const Real bs = K.w_es * K.b * m.inv_rho;
-  Real Dl[6] = {iso + bs * m.sig[0], iso + bs * m.sig[1], iso + bs * m.sig[2],
-                bs * m.sig[3], bs * m.sig[4], bs * m.sig[5]};
+template <typename Real, typename V>
+__device__ __forceinline__ void mix_coeffs(const Mom<V>& m, const StepConst<Real>& K, Herm<V>& H) {
+  const V iso = fmad(K.w_eq, m.dth, K.w_es * m.dT);
+  const V bs = (K.w_es * K.b) * m.inv_rho;
+  V Dl[6] = {fmad(bs, m.sig[0], iso), fmad(bs, m.sig[1], iso), fmad(bs, m.sig[2], iso),
+             bs * m.sig[3], bs * m.sig[4], bs * m.sig[5]};
   hermite(m.drho, m.rho, m.inv_rho, m.j, Dl, K.theta0, H);
 }
 

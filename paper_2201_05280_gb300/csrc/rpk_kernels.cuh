@@ -278,6 +278,179 @@ __global__ void __launch_bounds__(kTBX * kTBY)
 }
 
 // ---------------------------------------------------------------------------
+// The same three transport passes on a periodic FP32 grid with nx a multiple
+// of 4, four x-adjacent points per thread: every field is read and written as
+// aligned 16-byte quads, the y and z neighbours of a quad are quads too, and
+// only the x neighbours beyond the quad's ends (x0 - 1, x0 + 4) are single
+// values. Same expressions in the same order as k_mac_pred, k_mac_corr and
+// k_ftcs_first (identical results), four times the bytes in flight per
+// thread. Block (32, 8): threadIdx.x runs over quads along x.
+struct Quad {
+  int x0, y, z, s;
+  int64_t p;             // element index of the quad's first point
+  int64_t xm, xp;        // offsets of x0 - 1 and x0 + 4 from p (periodic)
+  int64_t ym, yp, zm, zp;  // offsets of the neighbour rows / planes
+};
+
+inline __device__ bool quad_from_block(const StepConst<float>& K, Quad& Q) {
+  Q.x0 = 4 * (blockIdx.x * kTBX + threadIdx.x);
+  Q.y = blockIdx.y * kTBY + threadIdx.y;
+  Q.s = blockIdx.z / K.nz;
+  Q.z = blockIdx.z - Q.s * K.nz;
+  if (Q.x0 >= K.nx || Q.y >= K.ny) return false;
+  const int64_t pl = (int64_t)K.nx * K.ny;
+  Q.p = (int64_t)Q.s * K.n3 + ((int64_t)Q.z * K.ny + Q.y) * K.nx + Q.x0;
+  Q.xm = Q.x0 > 0 ? -1 : K.nx - 1;
+  Q.xp = Q.x0 + 4 < K.nx ? 4 : 4 - K.nx;
+  Q.ym = Q.y > 0 ? -(int64_t)K.nx : (int64_t)(K.ny - 1) * K.nx;
+  Q.yp = Q.y < K.ny - 1 ? (int64_t)K.nx : -(int64_t)(K.ny - 1) * K.nx;
+  Q.zm = Q.z > 0 ? -pl : (int64_t)(K.nz - 1) * pl;
+  Q.zp = Q.z < K.nz - 1 ? pl : -(int64_t)(K.nz - 1) * pl;
+  return true;
+}
+
+__device__ __forceinline__ float4 ld4(const float* __restrict__ a, int64_t i) {
+  return *reinterpret_cast<const float4*>(a + i);
+}
+__device__ __forceinline__ void st4(float* __restrict__ a, int64_t i, const float (&v)[4]) {
+  *reinterpret_cast<float4*>(a + i) = make_float4(v[0], v[1], v[2], v[3]);
+}
+__device__ __forceinline__ void un4(float4 q, float (&v)[4]) {
+  v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+}
+
+static __global__ void __launch_bounds__(kTBX * kTBY)
+    k_mac_pred4(StepConst<float> K, const float* __restrict__ e, const float* __restrict__ ucur,
+                const float* __restrict__ uprev, float* __restrict__ ep, float* __restrict__ v) {
+  Quad Q;
+  if (!quad_from_block(K, Q)) return;
+  const int64_t npts = 2 * K.n3, p = Q.p;
+  float e0[4], div[4] = {0.f, 0.f, 0.f, 0.f}, vp[3][4];
+  un4(ld4(e, p), e0);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    float uc[4], up[4];
+    un4(ld4(ucur, a * npts + p), uc);
+    un4(ld4(uprev, a * npts + p), up);
+#pragma unroll
+    for (int l = 0; l < 4; ++l) vp[a][l] = 1.5f * uc[l] - 0.5f * up[l];
+    // forward neighbours of the four points along axis a
+    float eq[4], vq[4];
+    if (a == 0) {
+#pragma unroll
+      for (int l = 0; l < 3; ++l) eq[l] = e0[l + 1];
+      eq[3] = e[p + Q.xp];
+      for (int l = 0; l < 3; ++l) vq[l] = vp[0][l + 1];
+      vq[3] = vadv(ucur, uprev, p + Q.xp);
+    } else {
+      const int64_t o = a == 1 ? Q.yp : Q.zp;
+      float uq[4], upq[4];
+      un4(ld4(e, p + o), eq);
+      un4(ld4(ucur, a * npts + p + o), uq);
+      un4(ld4(uprev, a * npts + p + o), upq);
+#pragma unroll
+      for (int l = 0; l < 4; ++l) vq[l] = 1.5f * uq[l] - 0.5f * upq[l];
+    }
+#pragma unroll
+    for (int l = 0; l < 4; ++l) div[l] += K.E0 * (vq[l] - vp[a][l]) + (eq[l] * vq[l] - e0[l] * vp[a][l]);
+    st4(v, a * npts + p, vp[a]);
+  }
+  float r[4];
+#pragma unroll
+  for (int l = 0; l < 4; ++l) r[l] = e0[l] - K.dt * div[l];
+  st4(ep, p, r);
+}
+
+static __global__ void __launch_bounds__(kTBX * kTBY)
+    k_mac_corr4(StepConst<float> K, const float* __restrict__ e, const float* __restrict__ ep,
+                const float* __restrict__ v, const float* __restrict__ drho, float* __restrict__ ec,
+                float* __restrict__ th) {
+  Quad Q;
+  if (!quad_from_block(K, Q)) return;
+  const int64_t npts = 2 * K.n3, p = Q.p;
+  float epp[4], div[4] = {0.f, 0.f, 0.f, 0.f};
+  un4(ld4(ep, p), epp);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    float vp[4], eq[4], vq[4];
+    un4(ld4(v, a * npts + p), vp);
+    if (a == 0) {
+      eq[0] = ep[p + Q.xm];
+      vq[0] = v[p + Q.xm];
+#pragma unroll
+      for (int l = 1; l < 4; ++l) {
+        eq[l] = epp[l - 1];
+        vq[l] = vp[l - 1];
+      }
+    } else {
+      const int64_t o = a == 1 ? Q.ym : Q.zm;
+      un4(ld4(ep, p + o), eq);
+      un4(ld4(v, a * npts + p + o), vq);
+    }
+#pragma unroll
+    for (int l = 0; l < 4; ++l) div[l] += K.E0 * (vp[l] - vq[l]) + (epp[l] * vp[l] - eq[l] * vq[l]);
+  }
+  float e0[4], dr[4], val[4], t[4];
+  un4(ld4(e, p), e0);
+  un4(ld4(drho, p), dr);
+#pragma unroll
+  for (int l = 0; l < 4; ++l) {
+    val[l] = 0.5f * (e0[l] + epp[l] - K.dt * div[l]);
+    t[l] = (2.f * val[l] - K.delta * K.theta0 * dr[l]) / (K.delta * (1.f + dr[l]));
+  }
+  st4(ec, p, val);
+  st4(th, p, t);
+}
+
+static __global__ void __launch_bounds__(kTBX * kTBY)
+    k_ftcs_first4(StepConst<float> K, const float* __restrict__ ec, const float* __restrict__ th,
+                  const float* __restrict__ kap, float* __restrict__ e_next) {
+  Quad Q;
+  if (!quad_from_block(K, Q)) return;
+  const int64_t p = Q.p;
+  float thp[4], kp[4], acc[4] = {0.f, 0.f, 0.f, 0.f};
+  un4(ld4(th, p), thp);
+  un4(ld4(kap, p), kp);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+#pragma unroll
+    for (int d = -1; d <= 1; d += 2) {
+      float thq[4], kq[4];
+      if (a == 0) {
+        if (d < 0) {
+          thq[0] = th[p + Q.xm];
+          kq[0] = kap[p + Q.xm];
+#pragma unroll
+          for (int l = 1; l < 4; ++l) {
+            thq[l] = thp[l - 1];
+            kq[l] = kp[l - 1];
+          }
+        } else {
+#pragma unroll
+          for (int l = 0; l < 3; ++l) {
+            thq[l] = thp[l + 1];
+            kq[l] = kp[l + 1];
+          }
+          thq[3] = th[p + Q.xp];
+          kq[3] = kap[p + Q.xp];
+        }
+      } else {
+        const int64_t o = a == 1 ? (d < 0 ? Q.ym : Q.yp) : (d < 0 ? Q.zm : Q.zp);
+        un4(ld4(th, p + o), thq);
+        un4(ld4(kap, p + o), kq);
+      }
+#pragma unroll
+      for (int l = 0; l < 4; ++l) acc[l] += 0.5f * (kp[l] + kq[l]) * (thq[l] - thp[l]);
+    }
+  }
+  float c[4], r[4];
+  un4(ld4(ec, p), c);
+#pragma unroll
+  for (int l = 0; l < 4; ++l) r[l] = c[l] + K.hsub * acc[l];
+  st4(e_next, p, r);
+}
+
+// ---------------------------------------------------------------------------
 // Paper mode of the rotational solver (Sec. 5): after the collision has done
 // step 1 (first backward-Euler half step, stored in es), three passes on
 // theta_R - theta0 with u of time t:

@@ -7,7 +7,6 @@
 
 #include "rpk_internal.h"
 #include "rpk_kernels.cuh"
-#include "rpk_transport.cuh"
 
 namespace rpk {
 
@@ -104,6 +103,17 @@ static rpk_status collide_launch(rpk_lattice* L, const StepConst<Real>& K) {
         static_cast<const Real*>(L->ghost), L->status, static_cast<Real*>(L->thbuf), wcol);
     return check_launch("k_collide");
   }
+  if constexpr (kPull && kBC == 0 && sizeof(Real) == 4) {
+    if (L->grid.nx % 2 == 0) {
+      // two x-adjacent points per thread, packed FP32x2 arithmetic
+      const dim3 grid((unsigned)((L->grid.nx / 2 + 127) / 128), (unsigned)L->grid.ny,
+                      (unsigned)(2 * L->grid.nz));
+      k_collide_pair<Store><<<grid, 128, 0, L->stream>>>(
+          K, pin, pout, static_cast<const Real*>(L->e), static_cast<Real*>(L->e_star),
+          static_cast<Real*>(L->drho), ucur, static_cast<Real*>(L->kap), L->status);
+      return check_launch("k_collide_pair");
+    }
+  }
   k_collide<Store, Real, kPull, kBC, false><<<point_grid(L, 128), 128, 0, L->stream>>>(
       K, pin, pout, static_cast<const Real*>(L->e), static_cast<Real*>(L->e_star),
       static_cast<Real*>(L->drho), ucur, static_cast<Real*>(L->kap),
@@ -146,18 +156,17 @@ static rpk_status transport_launch(rpk_lattice* L, const StepConst<Real>& K) {
   }
   // predictor, corrector and the first FTCS sub-step; further sub-steps end in e
   Real* dst = L->nsub == 1 ? e : ea;
-  int launches = 3;
-  if constexpr (kBC == 0) {
-    // periodic grid: one fused pass (intermediates in shared memory)
-    constexpr int bps = sizeof(Real) == 4 ? 4 : 2;
-    const int zc = fused_zchunk(L->grid.nx, L->grid.ny, L->grid.nz, L->sms, bps);
-    const dim3 fgrid((unsigned)(((L->grid.nx + kFTX - 1) / kFTX) * ((L->grid.ny + kFTY - 1) / kFTY) * 2),
-                     (unsigned)((L->grid.nz + zc - 1) / zc));
-    const size_t smem = sizeof(FusedSmem<Real>);
-    RPK_CUDA(cudaFuncSetAttribute(k_transport_fused<Real>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)smem));
-    k_transport_fused<Real><<<fgrid, kFThreads, smem, L->stream>>>(K, es, ucur, uprev, drho, kap, dst, zc);
-    launches = 1;
+  bool quads = false;
+  if constexpr (kBC == 0 && sizeof(Real) == 4) quads = L->grid.nx % 4 == 0;
+  if (quads) {
+    if constexpr (kBC == 0 && sizeof(Real) == 4) {
+      // periodic FP32 grid, nx a multiple of 4: four x-adjacent points per thread
+      const dim3 qgrid((unsigned)((L->grid.nx / 4 + kTBX - 1) / kTBX),
+                       (unsigned)((L->grid.ny + kTBY - 1) / kTBY), (unsigned)(2 * L->grid.nz));
+      k_mac_pred4<<<qgrid, tb, 0, L->stream>>>(K, es, ucur, uprev, ea, v);
+      k_mac_corr4<<<qgrid, tb, 0, L->stream>>>(K, es, ea, v, drho, eb, th);
+      k_ftcs_first4<<<qgrid, tb, 0, L->stream>>>(K, eb, th, kap, dst);
+    }
   } else {
     k_mac_pred<Real, kBC><<<tgrid, tb, 0, L->stream>>>(K, es, ucur, uprev, ea, v, gh);
     k_mac_corr<Real, kBC><<<tgrid, tb, 0, L->stream>>>(K, es, ea, v, drho, eb, th, gh);
@@ -169,7 +178,7 @@ static rpk_status transport_launch(rpk_lattice* L, const StepConst<Real>& K) {
     k_ftcs<Real, kBC><<<grid, 128, 0, L->stream>>>(K, src, drho, kap, dst, gh);
     src = dst;
   }
-  RPK_CUDA(timing_end(L, RPK_KC_TRANSPORT, launches - 1 + L->nsub));
+  RPK_CUDA(timing_end(L, RPK_KC_TRANSPORT, 2 + L->nsub));
   return check_launch("rotational transport");
 }
 
