@@ -85,7 +85,8 @@ def ncu_traffic(prec):
     kernel source has not changed since it was captured; else None."""
     path = os.path.join(ROOT, "profiles", "ncu_collide_%s.txt" % prec)
     csrc = os.path.join(ROOT, "paper_2201_05280_gb300", "csrc")
-    srcs = [os.path.join(csrc, f) for f in ("rpk_lattice.cuh", "rpk_device.cuh", "rpk_collide.cuh")]
+    srcs = [os.path.join(csrc, f) for f in ("rpk_lattice.cuh", "rpk_vec2.cuh", "rpk_device.cuh",
+                                            "rpk_pair.cuh", "rpk_collide.cuh")]
     try:
         kv = {}
         for line in open(path):
@@ -606,7 +607,8 @@ def main():
     achieved = ab["collide"] * npts / coll_avg_s / 1e9
     traffic = ncu_traffic(args.precision)
     step_gbs = ab["step"] * npts * args.steps / (ms * 1e-3) / 1e9
-    roofline = {"bound": "hbm", "kernel": "k_collide (pull-stream + collide + exchange)",
+    roofline = {"bound": "hbm", "kernel": "k_collide_pair (pull-stream + collide + exchange, two points per thread)"
+                if args.n % 2 == 0 else "k_collide (pull-stream + collide + exchange)",
                 "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "peak_source": peak_src,
                 "algorithmic_bytes_per_point": ab["collide"],
