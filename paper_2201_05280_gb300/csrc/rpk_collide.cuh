@@ -119,7 +119,7 @@ __device__ __forceinline__ void flag_moments2(const Mom<F2>& m, float theta0, un
 // the arithmetic instructions; pair words halve the loads and stores).
 // Thread (blockIdx.x * blockDim.x + threadIdx.x) owns x0 = 2 * that index.
 template <typename Store>
-__global__ void __launch_bounds__(128, 3)
+__global__ void __launch_bounds__(128, sizeof(Store) == 4 ? 3 : 4)
     k_collide_pair(StepConst<float> K, const Store* __restrict__ pin, Store* __restrict__ pout,
                    const float* __restrict__ e_in, float* __restrict__ e_out, float* __restrict__ drho_out,
                    float* __restrict__ u_out, float* __restrict__ kap_out, unsigned* __restrict__ status) {

@@ -1,15 +1,17 @@
-"""Writes tgv64_re<Re>_oracle.npz: the FP64 oracle's moment fields of the
+"""Writes tgv64_<case>_oracle.npz: the FP64 oracle's moment fields of the
 3-D Taylor-Green vortex at Ma 0.3 (diatomic gas, eta_B/eta = 0.6, Pr = 0.71,
-b = 0) on a 64^3 box of each BCC sublattice.
+b = 0) on a 64^3 box of each BCC sublattice, after 1000 steps.
 
-Two cases of the 512^3 Taylor-Green vortex at Ma 0.3, Re 1600, copied to 64^3:
-  --re 200 --steps 1000   the same lattice viscosity as the 512^3 run
-                          (nu = u0 L / Re with L eight times smaller), i.e.
-                          the same relaxation times and the same per-step
-                          rounding regime of the stored populations;
-  --re 1600 --steps 200   the same Reynolds number; on 64^3 the method itself
-                          breaks down between steps 250 and 300 (the oracle's
-                          state turns non-finite), so it is compared earlier.
+The 512^3 Taylor-Green vortex at Ma 0.3, Re 1600 copied to 64^3 with the same
+lattice viscosity (nu = u0 L / Re with L eight times smaller, i.e. Re 200 on
+64^3), hence the same relaxation times (tau = 0.060, tau1 = 0.075) and the
+same per-step rounding regime of the stored populations. With these
+relaxation times the conservative form of the rotational energy breaks down
+(a mode grows from round-off by e every ~20 steps; the oracle's state turns
+non-finite near step 850), while the paper's own theta_R solver stays stable.
+Two cases:
+  --re 200 --mode paper          the 512^3 relaxation times, paper's solver
+  --re 100 --mode conservative   twice the viscosity, the default solver
 
 The reduced-storage test (tests/test_gpu_tgv64.py) compares the GPU path's
 FP32, FP16-deviation and BF16-deviation storage runs of the same setups with
@@ -24,8 +26,8 @@ deviation's own scale): rho - 1, u (3 components), theta_T - theta0,
 E_R - delta theta0 / 2 at each step of STEPS; the oracle's FP64 totals M, J, E
 at step 0 and at those steps; the parameters.
 
-    python tests/golden/make_tgv64_oracle.py --re 200 --steps 1000
-    python tests/golden/make_tgv64_oracle.py --re 1600 --steps 200
+    python tests/golden/make_tgv64_oracle.py --re 200 --mode paper
+    python tests/golden/make_tgv64_oracle.py --re 100 --mode conservative
 """
 import argparse
 import os
@@ -46,9 +48,10 @@ MA, LAM, PR, GAMMA = 0.3, 0.6, 0.71, 1.4
 ZSTRIDE = 4  # stored z planes: 0, 4, 8, ...
 
 
-def setup(n, re):
+def setup(n, re, rot_mode):
     """Fields and oracle parameters of the n^3 Taylor-Green vortex at Ma 0.3
-    and Reynolds number re: u0 = Ma c_s, L = n/(2 pi), nu = u0 L / re."""
+    and Reynolds number re: u0 = Ma c_s, L = n/(2 pi), nu = u0 L / re;
+    rot_mode 0 = conservative rotational energy, 1 = the paper's solver."""
     t0 = PM.THETA0
     u0 = MA * np.sqrt(GAMMA * t0)
     nu = u0 * (n / (2.0 * np.pi)) / re
@@ -57,8 +60,9 @@ def setup(n, re):
     f = I.taylor_green(n, t0, u0)
     thmax = float(np.max((3 * f["T"] + d * f["R"]) / (3 + d)))
     nsub = PM.nsub_for(d, tau, tau1, kr, thmax, 3)
-    P = O.make_params(d, tau, tau1, b, kr, 1.0, nsub, 0)
-    return f, P, dict(delta=d, tau=tau, tau1=tau1, b=b, k_r=kr, nsub=nsub, nu=nu, u0=u0)
+    P = O.make_params(d, tau, tau1, b, kr, 1.0, nsub, 0, rot_mode=rot_mode)
+    return f, P, dict(delta=d, tau=tau, tau1=tau1, b=b, k_r=kr, nsub=nsub, nu=nu, u0=u0,
+                      rot_mode=rot_mode)
 
 
 def sample(a, n):
@@ -79,13 +83,14 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--n", type=int, default=64)
     ap.add_argument("--re", type=float, default=200.0)
+    ap.add_argument("--mode", choices=["paper", "conservative"], default="paper")
     ap.add_argument("--steps", default="1000", help="comma-separated steps to store")
     ap.add_argument("--out", default=None)
     a = ap.parse_args()
-    out_path = a.out or os.path.join(HERE, "tgv%d_re%d_oracle.npz" % (a.n, int(a.re)))
+    out_path = a.out or os.path.join(HERE, "tgv%d_re%d_%s_oracle.npz" % (a.n, int(a.re), a.mode))
     steps = sorted(int(s) for s in a.steps.split(","))
     O.build()
-    f, P, prm = setup(a.n, a.re)
+    f, P, prm = setup(a.n, a.re, 1 if a.mode == "paper" else 0)
     S = O.State(P, a.n, a.n, a.n).init_fields(f["rho"], f["u"], f["T"], f["R"])
     out = {"n": np.int64(a.n), "re": np.float64(a.re), "zstride": np.int64(ZSTRIDE),
            "steps": np.array(steps, dtype=np.int64)}
