@@ -184,10 +184,6 @@ static void free_all(rpk_lattice* L) {
   if (!L) return;
   for (cudaEvent_t ev : L->events) cudaEventDestroy(ev);
   L->events.clear();
-  for (cudaStream_t st : L->io)
-    if (st) cudaStreamDestroy(st);
-  for (cudaEvent_t ev : L->io_ev)
-    if (ev) cudaEventDestroy(ev);
   void* ptrs[] = {L->pop[0], L->pop[1], L->e,       L->e_star, L->e_a,    L->e_b,
                   L->vbuf,   L->thbuf,  L->drho,    L->kap,    L->u[0],   L->u[1],
                   L->ghost,  L->status, L->diag_partial, L->diag_out, L->stage, L->wrho};
@@ -369,42 +365,6 @@ rpk_status rpk_set_rot_mode(rpk_lattice* L, int mode) {
   return RPK_OK;
 }
 
-// Host <-> device copies of several arrays, each split into equal parts over
-// the lattice's I/O streams, which start after the work queued on L->stream
-// and which L->stream waits for.
-struct CopyJob {
-  void* dst;
-  const void* src;
-  size_t bytes;
-};
-
-static rpk_status copy_spread(rpk_lattice* L, const CopyJob* jobs, int njobs, cudaMemcpyKind kind) {
-  constexpr int S = rpk_lattice::kIoStreams;
-  if (!L->io_ready) {
-    for (int k = 0; k < S; ++k) RPK_CUDA(cudaStreamCreateWithFlags(&L->io[k], cudaStreamNonBlocking));
-    for (int k = 0; k <= S; ++k) RPK_CUDA(cudaEventCreateWithFlags(&L->io_ev[k], cudaEventDisableTiming));
-    L->io_ready = true;
-  }
-  RPK_CUDA(cudaEventRecord(L->io_ev[S], L->stream));
-  for (int k = 0; k < S; ++k) RPK_CUDA(cudaStreamWaitEvent(L->io[k], L->io_ev[S], 0));
-  for (int j = 0; j < njobs; ++j) {
-    if (!jobs[j].bytes) continue;
-    const size_t part = (jobs[j].bytes / S + 7) & ~(size_t)7;
-    for (int k = 0; k < S; ++k) {
-      const size_t off = part * k;
-      if (off >= jobs[j].bytes) break;
-      const size_t len = std::min(part, jobs[j].bytes - off);
-      RPK_CUDA(cudaMemcpyAsync(static_cast<char*>(jobs[j].dst) + off,
-                               static_cast<const char*>(jobs[j].src) + off, len, kind, L->io[k]));
-    }
-  }
-  for (int k = 0; k < S; ++k) {
-    RPK_CUDA(cudaEventRecord(L->io_ev[k], L->io[k]));
-    RPK_CUDA(cudaStreamWaitEvent(L->stream, L->io_ev[k], 0));
-  }
-  return RPK_OK;
-}
-
 static rpk_status ensure_stage(rpk_lattice* L) {
   if (L->stage) return RPK_OK;
   const size_t bytes = sizeof(double) * 7 * (size_t)L->npts;
@@ -432,10 +392,10 @@ rpk_status rpk_init_fields(rpk_lattice* L, const double* rho, const double* u,
     rpk_status st = ensure_stage(L);
     if (st != RPK_OK) return st;
     double* s = L->stage;
-    const size_t b = n * sizeof(double);
-    const CopyJob jobs[4] = {{s, rho, b}, {s + n, u, 3 * b}, {s + 4 * n, T, b}, {s + 5 * n, R, b}};
-    st = copy_spread(L, jobs, 4, cudaMemcpyHostToDevice);
-    if (st != RPK_OK) return st;
+    RPK_CUDA(cudaMemcpyAsync(s, rho, n * sizeof(double), cudaMemcpyHostToDevice, L->stream));
+    RPK_CUDA(cudaMemcpyAsync(s + n, u, 3 * n * sizeof(double), cudaMemcpyHostToDevice, L->stream));
+    RPK_CUDA(cudaMemcpyAsync(s + 4 * n, T, n * sizeof(double), cudaMemcpyHostToDevice, L->stream));
+    RPK_CUDA(cudaMemcpyAsync(s + 5 * n, R, n * sizeof(double), cudaMemcpyHostToDevice, L->stream));
     drho = s;
     du = s + n;
     dT = s + 4 * n;
@@ -520,10 +480,11 @@ rpk_status rpk_read_moments(rpk_lattice* L, double* rho, double* u, double* T, d
   if (st != RPK_OK) return st;
   if (!on_device) {
     const size_t b = n * sizeof(double);
-    const CopyJob jobs[5] = {{rho, o_rho, rho ? b : 0}, {u, o_u, u ? 3 * b : 0}, {T, o_T, T ? b : 0},
-                             {R, o_R, R ? b : 0}, {E, o_E, E ? b : 0}};
-    st = copy_spread(L, jobs, 5, cudaMemcpyDeviceToHost);
-    if (st != RPK_OK) return st;
+    if (rho) RPK_CUDA(cudaMemcpyAsync(rho, o_rho, b, cudaMemcpyDeviceToHost, L->stream));
+    if (u) RPK_CUDA(cudaMemcpyAsync(u, o_u, 3 * b, cudaMemcpyDeviceToHost, L->stream));
+    if (T) RPK_CUDA(cudaMemcpyAsync(T, o_T, b, cudaMemcpyDeviceToHost, L->stream));
+    if (R) RPK_CUDA(cudaMemcpyAsync(R, o_R, b, cudaMemcpyDeviceToHost, L->stream));
+    if (E) RPK_CUDA(cudaMemcpyAsync(E, o_E, b, cudaMemcpyDeviceToHost, L->stream));
   }
   unsigned flags = 0;
   st = read_status(L, &flags);

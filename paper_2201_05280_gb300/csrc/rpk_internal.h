@@ -47,12 +47,6 @@ struct rpk_lattice {
   double* diag_partial = nullptr;
   double* diag_out = nullptr;
   double* stage = nullptr;          // 7 x npts doubles for host I/O, lazy
-  // host I/O: each copy is split over kIoStreams streams (more copy engines
-  // on the host link), ordered after and before the lattice's stream
-  static constexpr int kIoStreams = 4;
-  cudaStream_t io[kIoStreams] = {};
-  cudaEvent_t io_ev[kIoStreams + 1] = {};
-  bool io_ready = false;
   int64_t steps = 0;
   size_t bytes_held = 0;
   // kernel timing: event pairs recorded around each kernel class

@@ -177,14 +177,17 @@ __global__ void __launch_bounds__(kThreads) k_conv(ConvArgs P) {
 // 5 taps. One persistent CTA per SM keeps the layer's BF16 weights in shared
 // memory (A: 128 x 640, K-major) and walks over tiles of 128 output positions
 // of one sequence. Three roles run concurrently on double buffers:
-//   producers (warps 4-7) stage the tile's 132 input rows (positions
-//     q0 - 2 .. q0 + 129, activation applied, BF16) into B[i % 2];
-//   one issuing thread (warp 4, lane 0) waits for B[i % 2] and for the
+//   producers (warps 8-15) stage the tile's 132 input rows (positions
+//     q0 - 2 .. q0 + 129, activation applied, BF16) into B[i % 2], every
+//     load of the tile in flight at once (9 per thread);
+//   one issuing thread (warp 8, lane 0) waits for B[i % 2] and for the
 //     accumulator i % 2 to be free, issues 40 MMAs (M 128, N 128, K 16) into
 //     TMEM columns 128 (i % 2) .. + 127 and commits to two mbarriers (B free,
 //     accumulator full);
-//   the epilogue (warps 0-3, TMEM lane = output channel) reads the
-//     accumulator, applies bias, mask and residual as k_conv does, and frees it.
+//   the epilogue (warps 0-7; TMEM lane = output channel, lane quadrant
+//     warp % 4, warps 0-3 the first 64 columns and warps 4-7 the last 64)
+//     reads the accumulator, applies bias, mask and residual as k_conv does,
+//     and frees it.
 // The operand of tap t is the staged tile seen from row t (forward) or 4 - t
 // (input gradient): in the interleaved no-swizzle layout (rows 16 bytes apart
 // inside each 8-column chunk) a row shift is a start-address offset.
@@ -198,7 +201,9 @@ constexpr uint32_t TC_B_BYTES = (TC_KC / 8) * TC_B_LBO;    // 33792 per buffer
 constexpr uint32_t TC_BAR_OFF = TC_A_BYTES + 2 * TC_B_BYTES;
 constexpr uint32_t TC_SMEM = TC_BAR_OFF + 128;             // 8 mbarriers + TMEM address
 static_assert(TC_SMEM <= 227 * 1024, "tensor-core tiles exceed shared memory");
-constexpr int TC_THREADS = 256;
+constexpr int TC_THREADS = 512;
+constexpr int TC_EPI = 256;                                // epilogue threads (warps 0-7)
+constexpr int TC_PROD = TC_THREADS - TC_EPI;               // producer threads (warps 8-15)
 constexpr int TC_COLS = 2 * TC_N;                          // two accumulators
 constexpr long long TC_WAIT_LIMIT = 1ll << 22;             // mbarrier polls before giving up
 
@@ -279,10 +284,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv_tc(TcArgs P) {
   }
   if (tid == 0) {
     for (int b = 0; b < 2; ++b) {
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bars + b)), "r"(128) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bars + b)), "r"(TC_PROD) : "memory");
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bars + 2 + b)), "r"(1) : "memory");
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bars + 4 + b)), "r"(1) : "memory");
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bars + 6 + b)), "r"(128) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bars + 6 + b)), "r"(TC_EPI) : "memory");
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -301,9 +306,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv_tc(TcArgs P) {
   const uint32_t bar0 = smem_u32(bars);
   bool ok = true;
 
-  if (warp >= 4) {
+  if (tid >= TC_EPI) {
     // producers, and the issuing thread
-    const int ptid = tid - 128;
+    const int ptid = tid - TC_EPI;
     for (int i = 0, tile = blockIdx.x; tile < P.ntiles && ok; ++i, tile += gridDim.x) {
       const int b = i & 1;
       if (i >= 2) ok = __all_sync(0xffffffffu, mbar_wait(bar0 + 8 * (2 + b), ((i >> 1) - 1) & 1));
@@ -311,14 +316,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv_tc(TcArgs P) {
       int q0, cnt, lo, len;
       tc_tile(P, tile, q0, cnt, lo, len);
       unsigned char* dst = sB + b * TC_B_BYTES;
-      // 2112 (row, chunk) elements, 17 per thread: loads of a batch of 4 are
-      // issued before any is converted
-      constexpr int kElems = TC_ROWS * (TC_KC / 8), kBatch = 4;
-      for (int e0 = ptid; e0 < kElems; e0 += 128 * kBatch) {
+      // 2112 (row, chunk) elements, at most 9 per thread: all loads of a
+      // thread are issued before any is converted
+      constexpr int kElems = TC_ROWS * (TC_KC / 8);
+      constexpr int kBatch = (kElems + TC_PROD - 1) / TC_PROD;
+      for (int e0 = ptid; e0 < kElems; e0 += TC_PROD * kBatch) {
         float4 f[kBatch][2];
 #pragma unroll
         for (int u = 0; u < kBatch; ++u) {
-          const int e = e0 + u * 128;
+          const int e = e0 + u * TC_PROD;
           const int r = e % TC_ROWS, c = e / TC_ROWS;
           const int q = q0 - 2 + r;
           f[u][0] = f[u][1] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -330,7 +336,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv_tc(TcArgs P) {
         }
 #pragma unroll
         for (int u = 0; u < kBatch; ++u) {
-          const int e = e0 + u * 128;
+          const int e = e0 + u * TC_PROD;
           if (e >= kElems) break;
           const int r = e % TC_ROWS, c = e / TC_ROWS;
           float4 f0 = f[u][0], f1 = f[u][1];
@@ -344,7 +350,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv_tc(TcArgs P) {
         }
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      mbar_arrive(bar0 + 8 * b);  // B full (128 arrivals)
+      mbar_arrive(bar0 + 8 * b);  // B full (TC_PROD arrivals)
       if (ptid == 0) {
         // the issuing thread: B staged by all producers, accumulator free
         bool go = mbar_wait(bar0 + 8 * b, (i >> 1) & 1);
@@ -382,8 +388,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv_tc(TcArgs P) {
       __syncwarp();
     }
   } else {
-    // epilogue: TMEM lane = output channel m
-    const int m = warp * 32 + lane;
+    // epilogue: TMEM lane = output channel m; this warp's half of the columns
+    const int quad = warp & 3, half = warp >> 2;
+    const int m = quad * 32 + lane;
     const float bm = P.bias ? P.bias[m] : 0.f;
     for (int i = 0, tile = blockIdx.x; tile < P.ntiles; ++i, tile += gridDim.x) {
       const int b = i & 1;
@@ -396,7 +403,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv_tc(TcArgs P) {
       int q0, cnt, lo, len;
       tc_tile(P, tile, q0, cnt, lo, len);
 #pragma unroll 1
-      for (int j = 0; j < TC_N / 32; ++j) {
+      for (int j = half * (TC_N / 64); j < (half + 1) * (TC_N / 64); ++j) {
         uint32_t v[32];
         asm volatile(
             "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
@@ -406,7 +413,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv_tc(TcArgs P) {
               "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]),
               "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]),
               "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
-            : "r"(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(b * TC_N + j * 32)));
+            : "r"(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(b * TC_N + j * 32)));
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
         // all loads of the chunk first (out may alias res: each element is read
         // and then written by this thread), then the stores
@@ -429,7 +436,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv_tc(TcArgs P) {
         }
       }
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-      mbar_arrive(bar0 + 8 * (6 + b));  // accumulator free (128 arrivals)
+      mbar_arrive(bar0 + 8 * (6 + b));  // accumulator free (TC_EPI arrivals)
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
