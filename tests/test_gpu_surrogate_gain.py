@@ -1,9 +1,10 @@
 """What the trained surrogate gains over the method without it.
 
-A network of the surrogate's architecture (width 64, 2 residual blocks) is
-trained on the GPU by the library's own forward, backward and Adam kernels on
-the batched LBM's snapshots of 96 tubes of the shock-tube sweep (lengths
-300-800 cells), then evaluated on 24 held-out tubes of another seed:
+The surrogate's network (width 128, 6 residual blocks, 0.99 M parameters) is
+trained on the GPU by the library's own forward, backward and Adam kernels
+(6000 Adam steps of 32 crops) on the batched LBM's snapshots of 96 tubes of
+the shock-tube sweep (lengths 300-800 cells), then evaluated on 24 held-out
+tubes of another seed:
 
 1. One window (32 steps) from the LBM's own state, every window of every tube
    (the rollout with a spot check in every window records the network's
@@ -30,6 +31,7 @@ pytestmark = pytest.mark.gpu
 
 T0 = 0.2948964908710633
 TRAIN_STEPS = 6000
+WIDTH, BLOCKS = 128, 6
 
 
 @pytest.fixture(scope="module")
@@ -43,9 +45,9 @@ def trained():
     tubes, cond = SG.make_tubes(specs, f, T0)
     data = SG.TrainingSet(tubes, cond, f, diffusion="implicit")
     cfg = SG.default_config(T0)
-    net = rpk.Net(SG.CIN, SG.COUT, 64, 2, seed=5)
-    untrained = rpk.Net(SG.CIN, SG.COUT, 64, 2, seed=5)
-    hist = SG.train(net, cfg, data, TRAIN_STEPS, batch=16, crop_len=512,
+    net = rpk.Net(SG.CIN, SG.COUT, WIDTH, BLOCKS, seed=5)
+    untrained = rpk.Net(SG.CIN, SG.COUT, WIDTH, BLOCKS, seed=5)
+    hist = SG.train(net, cfg, data, TRAIN_STEPS, batch=32, crop_len=512,
                     noise=[3e-4, 3e-4, 1e-4, 1e-4], seed=5)
     torch.cuda.synchronize()
     del data
@@ -56,7 +58,7 @@ def trained():
 
 
 def _zero_net():
-    net = rpk.Net(SG.CIN, SG.COUT, 64, 2, seed=5)
+    net = rpk.Net(SG.CIN, SG.COUT, WIDTH, BLOCKS, seed=5)
     net.set_params(np.zeros(net.num_params, dtype=np.float32))
     return net
 
@@ -98,7 +100,7 @@ def test_one_window_error_beats_the_method_without_a_network(trained):
     assert med["trained"] <= 0.3 * med["untrained"]
 
 
-@pytest.mark.parametrize("spot_every,l1_tol", [(4, 1e-2), (8, 3e-2)])
+@pytest.mark.parametrize("spot_every,l1_tol", [(4, 1e-2), (2, 1e-2)])
 def test_rollout_saves_lbm_steps(trained, spot_every, l1_tol):
     net, untrained, tubes, cond, blk0, hist = trained
     ref, offs = _plain_lbm(tubes, blk0)
