@@ -19,6 +19,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <random>
@@ -291,12 +292,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv_tc(TcArgs P) {
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  // weights: chunk c (k = 8c .. 8c + 7) of row m at c * TC_A_LBO + m * 16
+  // weights: chunk c (k = 8c .. 8c + 7) of row m at c * TC_A_LBO + m * 16,
+  // copied global -> shared asynchronously (every thread's 20 copies in flight
+  // at once, no register round trip)
   for (int e = tid; e < TC_M * (TC_K / 8); e += TC_THREADS) {
     const int m = e % TC_M, c = e / TC_M;
-    const uint4 v = *reinterpret_cast<const uint4*>(P.A + (int64_t)m * TC_K + 8 * c);
-    *reinterpret_cast<uint4*>(sA + c * TC_A_LBO + m * 16) = v;
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(sA + c * TC_A_LBO + m * 16)),
+                 "l"(P.A + (int64_t)m * TC_K + 8 * c)
+                 : "memory");
   }
+  asm volatile("cp.async.wait_all;" ::: "memory");
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
@@ -716,7 +721,13 @@ rpk_status conv(rpk_net* N, const __nv_bfloat16* A, int M, int taps, int Kc, int
 
 rpk_status conv_dw(rpk_net* N, const float* dY, int M, const float* X, int Kc, int taps,
                    int relu_in, float* dW, int64_t nq, int seq_len) {
-  const int qchunk = 2048;
+  // positions per block: enough blocks for about four per SM over the
+  // (output x input) tiles, between 128 and 2048 positions, a multiple of BK
+  const int64_t tiles = (int64_t)((taps * Kc + BN - 1) / BN) * ((M + BM - 1) / BM);
+  const int64_t want = std::max<int64_t>(1, 4 * (int64_t)std::max(N->nsm, 1) / std::max<int64_t>(tiles, 1));
+  int64_t qc = (nq + want - 1) / want;
+  qc = std::min<int64_t>(2048, std::max<int64_t>(128, (qc + BK - 1) / BK * BK));
+  const int qchunk = (int)qc;
   DwArgs P{dY, X, dW, M, Kc, taps, relu_in, (int)nq, seq_len, qchunk};
   const dim3 grid((unsigned)((taps * Kc + BN - 1) / BN), (unsigned)((M + BM - 1) / BM),
                   (unsigned)((nq + qchunk - 1) / qchunk));

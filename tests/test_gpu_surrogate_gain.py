@@ -17,8 +17,11 @@ tubes of another seed:
    error of each tube against the plain LBM. The zero network is handed to the
    LBM at its first spot check and saves nothing.
 
-Measured on GB300: see the printed values; the bars below are set
-from them with margin.
+Measured on GB300: one-window median error 0.18% trained, 1.2% untrained,
+3.5% without a network; the rollout ran 0.65 (every 4th window checked) and
+0.73 (every 2nd) of the plain LBM's steps with final errors of median 0.52% /
+0.56%, max 2.6%, where the zero network saves nothing. The bars below leave
+about a factor of two.
 """
 import numpy as np
 import pytest
@@ -95,7 +98,7 @@ def test_one_window_error_beats_the_method_without_a_network(trained):
           "training loss %.3e -> %.3e" % (e_tr.size, med, np.percentile(e_tr, 90),
                                           np.mean(hist[:20]), np.mean(hist[-100:])))
     assert e_tr.size == e_0.size > 50
-    assert med["trained"] <= 1e-2
+    assert med["trained"] <= 5e-3
     assert med["trained"] <= 0.2 * med["no network"]
     assert med["trained"] <= 0.3 * med["untrained"]
 
@@ -122,4 +125,8 @@ def test_rollout_saves_lbm_steps(trained, spot_every, l1_tol):
     print("spot every %d, l1_tol %g: LBM steps / plain LBM steps, median and max final L1 vs plain "
           "LBM, network windows kept: %s" % (spot_every, l1_tol, res))
     assert res["no network"][0] >= 1.0 and res["no network"][3] == 0
-    assert res["trained"][0] <= res["no network"][0]
+    # the trained network saves LBM steps at a median final error below 1%
+    assert res["trained"][0] <= 0.85
+    assert res["trained"][3] > 0
+    assert res["trained"][1] <= 1e-2
+    assert res["trained"][2] <= 5e-2
