@@ -262,6 +262,40 @@ def run_reference(args, rank):
     return 0
 
 
+def batch_line(rpk, ntubes, diffusion):
+    """One graph-captured persistent launch of ntubes tubes of the sweep
+    (autotuned): MLUPS, milliseconds and the roofline of the populations'
+    traffic (41 x 4 B read and written per point update)."""
+    import torch
+    specs, f = I.tube_sweep(ntubes, THETA0)
+    cs = rpk.sound_speed(GAS["gamma"])
+    tubes = []
+    for sp in specs:
+        nu = sp["kn"] * cs * sp["nx"]
+        eta, etaB, kap = rpk.gas_from_nondim(GAS["gamma"], nu, sp["lam"], sp["pr"])
+        rr = rpk.map_gas(GAS["gamma"], eta, etaB, kap, 0.0)
+        tubes.append({"nx": sp["nx"], "nsteps": sp["nsteps"], "relax": rr, "res": sp["res"]})
+    stream = torch.cuda.Stream()
+    bt = rpk.Batch(tubes, precision="f32", save_every=32, stream=stream)
+    bt.set_diffusion(diffusion)
+    bt.init_fields(f["rho"], f["u"], f["T"], f["R"])
+    tune = bt.autotune()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    bt.run()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    bt.close()
+    updates = sum(2 * t["nx"] * t["nsteps"] for t in tubes)
+    gbs = updates * 41 * 2 * 4 / (ms * 1e-3) / 1e9
+    return {"workload": "%d quasi-1-D shock tubes of the sweep, %s rotational diffusion" % (ntubes, diffusion),
+            "value": updates / (ms * 1e-3) / 1e6, "unit": "MLUPS", "ms": ms, "autotune": tune,
+            "population_gbs": gbs, "frac": gbs / load_peaks()[0], "gpu_launches": 1}
+
+
 def run_batch(args):
     """Batched shock-tube sweep: --tubes quasi-1-D tubes, lengths U[500, 4000],
     pressure ratio U[2, 20] (right state on the left isentrope), Kn log-U[1e-3,
@@ -480,6 +514,10 @@ def main():
     ap.add_argument("--cpu-n", type=int, default=24, help="oracle sample box for cpu_baseline")
     ap.add_argument("--cpu-steps", type=int, default=100)
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the 16-bit storage runs and the batched sweep added to the line")
+    ap.add_argument("--extra-tubes", type=int, default=1024,
+                    help="tubes of the batched sweep added to the lattice line")
     ap.add_argument("--mode", default="lattice", choices=["lattice", "batch", "surrogate"],
                     help="lattice: the 3-D step (default); batch: the shock-tube sweep; "
                          "surrogate: learned surrogate vs plain batched LBM")
@@ -595,6 +633,36 @@ def main():
                "note": "per job of K steps: fields uploaded once from pinned host memory, "
                        "moments read back once; bytes per step = job bytes / K"}
 
+    # the same workload with 16-bit deviation storage, and a batched sweep:
+    # short runs in the same process, so that the line carries them too
+    extras = None
+    if not args.no_extras and world == 1:
+        extras = {"storage": {}, "batch": None}
+        for prec in ("f16dev", "bf16dev"):
+            if prec == args.precision:
+                continue
+            lx = rpk.Lattice(n, n, n, precision=prec, stream=stream)
+            lx.set_relax(r["delta"], r["tau"], r["tau1"], r["b"], r["k_r"])
+            lx.init_fields(f["rho"], f["u"], f["T"], f["R"])
+            lx.step(args.warmup)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            lx.step(args.steps)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            xms = e0.elapsed_time(e1)
+            st = lx.diagnostics(check=False)["status"]
+            lx.close()
+            sb = algorithmic_bytes_per_point(prec)["step"]
+            gbs = sb * npts * args.steps / (xms * 1e-3) / 1e9
+            extras["storage"][prec] = {"value": job_mlups(1, npts, args.steps, xms), "unit": "MLUPS",
+                                       "ms_per_step": xms / args.steps, "step_bytes_per_point": sb,
+                                       "step_gbs": gbs, "step_frac": gbs / load_peaks()[0],
+                                       "device_status": st}
+        torch.cuda.empty_cache()
+        extras["batch"] = batch_line(rpk, args.extra_tubes, "implicit")
+        torch.cuda.empty_cache()
+
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
@@ -644,7 +712,7 @@ def main():
                              "single_thread": {"value": cpu_mlups, "cores": 1,
                                                "sample": "one %d^3 box x %d steps, %.1f s" %
                                                          (args.cpu_n, args.cpu_steps, cpu_dt)}},
-            "e2e": e2e, "gpu_launches": launches,
+            "e2e": e2e, "gpu_launches": launches, "extras": extras,
             "clocks": clk.summary(),
             "device_status": diag["status"]}
     print(json.dumps(line))

@@ -196,9 +196,12 @@ constexpr int TC_M = 128, TC_N = 128, TC_KC = 128, TC_TAPS = 5;
 constexpr int TC_ROWS = TC_N + TC_TAPS - 1;                // 132 staged rows
 constexpr int TC_K = TC_TAPS * TC_KC;                      // 640
 constexpr uint32_t TC_A_LBO = TC_M * 16;                   // bytes between 8-wide k chunks of A
-constexpr uint32_t TC_B_LBO = TC_ROWS * 16;                // bytes between 8-wide k chunks of B
+// bytes between 8-wide k chunks of B: one row more than staged, so that the
+// producers' 16-byte stores of one row's consecutive chunks fall in distinct
+// shared-memory banks (2128 / 4 = 532 = 20 mod 32)
+constexpr uint32_t TC_B_LBO = (TC_ROWS + 1) * 16;
 constexpr uint32_t TC_A_BYTES = (TC_K / 8) * TC_A_LBO;     // 163840
-constexpr uint32_t TC_B_BYTES = (TC_KC / 8) * TC_B_LBO;    // 33792 per buffer
+constexpr uint32_t TC_B_BYTES = (TC_KC / 8) * TC_B_LBO;    // 34048 per buffer
 constexpr uint32_t TC_BAR_OFF = TC_A_BYTES + 2 * TC_B_BYTES;
 constexpr uint32_t TC_SMEM = TC_BAR_OFF + 128;             // 8 mbarriers + TMEM address
 static_assert(TC_SMEM <= 227 * 1024, "tensor-core tiles exceed shared memory");
@@ -322,7 +325,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv_tc(TcArgs P) {
       tc_tile(P, tile, q0, cnt, lo, len);
       unsigned char* dst = sB + b * TC_B_BYTES;
       // 2112 (row, chunk) elements, at most 9 per thread: all loads of a
-      // thread are issued before any is converted
+      // thread are issued before any is converted; consecutive threads take
+      // consecutive 32-byte chunks of a row (coalesced rows of 512 bytes)
       constexpr int kElems = TC_ROWS * (TC_KC / 8);
       constexpr int kBatch = (kElems + TC_PROD - 1) / TC_PROD;
       for (int e0 = ptid; e0 < kElems; e0 += TC_PROD * kBatch) {
@@ -330,7 +334,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv_tc(TcArgs P) {
 #pragma unroll
         for (int u = 0; u < kBatch; ++u) {
           const int e = e0 + u * TC_PROD;
-          const int r = e % TC_ROWS, c = e / TC_ROWS;
+          const int r = e / (TC_KC / 8), c = e % (TC_KC / 8);
           const int q = q0 - 2 + r;
           f[u][0] = f[u][1] = make_float4(0.f, 0.f, 0.f, 0.f);
           if (e < kElems && q >= lo && q < lo + len) {
@@ -343,7 +347,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv_tc(TcArgs P) {
         for (int u = 0; u < kBatch; ++u) {
           const int e = e0 + u * TC_PROD;
           if (e >= kElems) break;
-          const int r = e % TC_ROWS, c = e / TC_ROWS;
+          const int r = e / (TC_KC / 8), c = e % (TC_KC / 8);
           float4 f0 = f[u][0], f1 = f[u][1];
           if (P.relu_in) {
             f0.x = fmaxf(f0.x, 0.f), f0.y = fmaxf(f0.y, 0.f), f0.z = fmaxf(f0.z, 0.f), f0.w = fmaxf(f0.w, 0.f);
