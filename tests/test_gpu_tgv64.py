@@ -37,8 +37,6 @@ STORED = {"rho": "drho", "u": "u", "T": "dT", "Erot": "dE"}
 CASES = {"re200_paper": "tgv64_re200_paper_oracle.npz",
          "re100_conservative": "tgv64_re100_conservative_oracle.npz"}
 
-# bounds per case and storage: (full scale, deviation scale) for rho, u, theta_T, E_R,
-# and (|dM|/M, |dE|/E) over the run
 # Bounds, about 3x the errors measured on GB300: (full scale, deviation scale)
 # for rho, u, theta_T, E_R, and |change of M|, |change of E| over the run minus
 # the oracle's own change. FP64: the stored oracle values are float32 (2^-24
