@@ -263,55 +263,7 @@ __global__ void __launch_bounds__(kThreads)
           __syncthreads();
           Real* ein = sE;
           Real* eout = sS;
-          int k = 1;
-          if constexpr (sizeof(Real) == 4) {
-            // FP32: up to kFH sub-steps per barrier. A thread takes chunks of
-            // kFC points of one sublattice line with kFH points of halo on each
-            // side in registers (beyond the line ends: the reservoir's theta_R
-            // and kappa_R, a = 0); after n <= kFH sub-steps the chunk itself is
-            // exact. Same expressions, in the same order, as the loop below.
-            constexpr int kFC = 8, kFH = 4, kFL = kFC + 2 * kFH;
-            const int cpl = (nx + kFC - 1) / kFC;  // chunks per line
-            for (; k < nsub;) {
-              const int nb = min(kFH, nsub - k);
-              for (int ch = tid; ch < 2 * cpl; ch += kThreads) {
-                const int s = ch >= cpl, x0 = (ch - s * cpl) * kFC, base = s * nx;
-                Real e[kFL], a[kFL], c[kFL], kap[kFL];
-#pragma unroll
-                for (int j = 0; j < kFL; ++j) {
-                  const int x = x0 - kFH + j;
-                  if (x < 0) {
-                    e[j] = Real(0), a[j] = Real(0), c[j] = thGl, kap[j] = gl[kGhKap];
-                  } else if (x >= nx) {
-                    e[j] = Real(0), a[j] = Real(0), c[j] = thGh, kap[j] = gh[kGhKap];
-                  } else {
-                    e[j] = ein[base + x], a[j] = sP[base + x], c[j] = sD[base + x], kap[j] = sK[base + x];
-                  }
-                }
-                for (int it = 0; it < nb; ++it) {
-                  Real th[kFL];
-#pragma unroll
-                  for (int j = 0; j < kFL; ++j) th[j] = a[j] * e[j] + c[j];
-#pragma unroll
-                  for (int j = 1; j < kFL - 1; ++j) {
-                    Real acc = Real(0);
-                    acc += Real(0.5) * (kap[j] + kap[j - 1]) * (th[j - 1] - th[j]);
-                    acc += Real(0.5) * (kap[j] + kap[j + 1]) * (th[j + 1] - th[j]);
-                    e[j] = e[j] + K.hsub * acc;
-                  }
-                }
-#pragma unroll
-                for (int j = kFH; j < kFH + kFC; ++j)
-                  if (x0 - kFH + j < nx) eout[base + x0 - kFH + j] = e[j];
-              }
-              __syncthreads();
-              Real* tmp = ein;
-              ein = eout;
-              eout = tmp;
-              k += nb;
-            }
-          }
-          for (; k < nsub; ++k) {
+          for (int k = 1; k < nsub; ++k) {
             for (int p = tid; p < np; p += kThreads) {
               const int s = p >= nx, x = p - s * nx;
               const Real ep = ein[p];
