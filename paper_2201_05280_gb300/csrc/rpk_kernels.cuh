@@ -649,6 +649,26 @@ __device__ __forceinline__ double warp_min(double v) {
   return v;
 }
 
+// Block reduction of the per-thread diagnostics (sums, and the minimum in
+// slot 6) into partial[blockIdx.x * kDiagVals + k].
+__device__ __forceinline__ void diag_block_reduce(const double (&acc)[kDiagVals - 1],
+                                                  double* __restrict__ partial) {
+  __shared__ double red[kDiagThreads / 32][kDiagVals];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < kDiagVals - 1; ++k) {
+    const double v = (k == 6) ? warp_min(acc[k]) : warp_sum(acc[k]);
+    if (lane == 0) red[wid][k] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < kDiagVals - 1) {
+    const int k = threadIdx.x;
+    double v = red[0][k];
+    for (int w = 1; w < kDiagThreads / 32; ++w) v = (k == 6) ? fmin(v, red[w][k]) : v + red[w][k];
+    partial[(int64_t)blockIdx.x * kDiagVals + k] = v;
+  }
+}
+
 template <typename Store, typename Real, bool kPull, int kBC>
 __global__ void __launch_bounds__(kDiagThreads, sizeof(Real) == 4 ? 4 : 1)
     k_diag(StepConst<Real> K, const Store* __restrict__ pin, const Real* __restrict__ e_in,
@@ -742,20 +762,76 @@ __global__ void __launch_bounds__(kDiagThreads, sizeof(Real) == 4 ? 4 : 1)
     });
     acc[5] += (double)Hp - 0.5 * (double)K.delta * (double)m.rho * log(t0 + (double)m.dR);
   }
-  __shared__ double red[kDiagThreads / 32][kDiagVals];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  diag_block_reduce(acc, partial);
+}
+
+// k_diag for two x-adjacent points per thread (periodic pull, conservative
+// form, FP32 arithmetic, nx even): the moments and targets in packed FP32x2
+// form, the logarithms and the FP64 accumulation per point. Thread t handles
+// pair t of the field planes (sublattice t / (n3/2)).
+template <typename Store>
+__global__ void __launch_bounds__(kDiagThreads, 3)
+    k_diag_pair(StepConst<float> K, const Store* __restrict__ pin, const float* __restrict__ e_in,
+                double* __restrict__ partial) {
+  using Word = typename PairIO<Store>::Word;
+  double acc[kDiagVals - 1] = {0, 0, 0, 0, 0, 0, INFINITY};
+  const int nxp = K.nx >> 1;
+  const int64_t n3p = K.n3 >> 1;
+  const double t0 = (double)K.theta0;
+  const float beta = K.beta, keep = 1.f - K.beta;
+  auto hterm = [](float w, float fw) {  // w (fw ln fw - fw), fw = f/w
+    return fw > 0.f ? w * (fw * __logf(fw) - fw) : NAN;
+  };
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < 2 * n3p;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int s = (int)(t / n3p);
+    const int64_t cp = t - (int64_t)s * n3p;
+    const int i = (int)(cp % nxp);
+    const int64_t row = cp / nxp;
+    const int y = (int)(row % K.ny), z = (int)(row / K.ny);
+    F2 h[kQ];
+    gather_pair<Store>(reinterpret_cast<const Word*>(pin), K, s, i, y, z, h);
+    Mom<F2> m;
+    raw_moments(h, m);
+    const F2 e(reinterpret_cast<const float2*>(e_in)[t]);
+    recover<float, false>(m, e, K);
+    Herm<F2> H;
+    mix_coeffs(m, K, H);
+    const float w0 = float(kWeightRest);
+    const F2 f0 = F2(1.f) + keep * h[0] + beta * H.e0;
+    float Hp[2] = {hterm(w0, f0.v.x), hterm(w0, f0.v.y)};
+    float gm[2] = {w0 * (1.f + h[0].v.x), w0 * (1.f + h[0].v.y)};
+    static_for<kPairs>([&](auto kc) {
+      constexpr int k = decltype(kc)::value;
+      constexpr Vel2 v = kPairVel2[k];
+      const float w = float(pair_weight(k));
+      const F2 ev = herm_even<v.x, v.y, v.z>(H), od = herm_odd<v.x, v.y, v.z>(H);
+      const F2 fp = F2(1.f) + keep * h[2 * k + 1] + beta * (ev + od);
+      const F2 fm = F2(1.f) + keep * h[2 * k + 2] + beta * (ev - od);
+      Hp[0] += hterm(w, fp.v.x) + hterm(w, fm.v.x);
+      Hp[1] += hterm(w, fp.v.y) + hterm(w, fm.v.y);
+      gm[0] = fminf(gm[0], fminf(w * (1.f + h[2 * k + 1].v.x), w * (1.f + h[2 * k + 2].v.x)));
+      gm[1] = fminf(gm[1], fminf(w * (1.f + h[2 * k + 1].v.y), w * (1.f + h[2 * k + 2].v.y)));
+    });
+    const float drho[2] = {m.drho.v.x, m.drho.v.y}, rho[2] = {m.rho.v.x, m.rho.v.y};
+    const float jx[2] = {m.j[0].v.x, m.j[0].v.y}, jy[2] = {m.j[1].v.x, m.j[1].v.y};
+    const float jz[2] = {m.j[2].v.x, m.j[2].v.y}, dR[2] = {m.dR.v.x, m.dR.v.y};
+    const float ev[2] = {e.v.x, e.v.y};
+    const float p0[2] = {m.dP[0].v.x, m.dP[0].v.y}, p1[2] = {m.dP[1].v.x, m.dP[1].v.y};
+    const float p2[2] = {m.dP[2].v.x, m.dP[2].v.y};
 #pragma unroll
-  for (int k = 0; k < kDiagVals - 1; ++k) {
-    const double v = (k == 6) ? warp_min(acc[k]) : warp_sum(acc[k]);
-    if (lane == 0) red[wid][k] = v;
+    for (int l = 0; l < 2; ++l) {
+      acc[0] += 1.0 + (double)drho[l];
+      acc[1] += (double)jx[l];
+      acc[2] += (double)jy[l];
+      acc[3] += (double)jz[l];
+      acc[4] += (1.5 * t0 + 0.5 * (double)K.delta * t0) +
+                (0.5 * ((double)p0[l] + (double)p1[l] + (double)p2[l]) + (double)ev[l]);
+      acc[5] += (double)Hp[l] - 0.5 * (double)K.delta * (double)rho[l] * log(t0 + (double)dR[l]);
+      acc[6] = fmin(acc[6], (double)gm[l]);
+    }
   }
-  __syncthreads();
-  if (threadIdx.x < kDiagVals - 1) {
-    const int k = threadIdx.x;
-    double v = red[0][k];
-    for (int w = 1; w < kDiagThreads / 32; ++w) v = (k == 6) ? fmin(v, red[w][k]) : v + red[w][k];
-    partial[(int64_t)blockIdx.x * kDiagVals + k] = v;
-  }
+  diag_block_reduce(acc, partial);
 }
 
 static __global__ void __launch_bounds__(1024) k_diag_final(const double* __restrict__ partial, int nblk,

@@ -314,6 +314,25 @@ rpk_status Ops<Store, Real>::diag(rpk_lattice* L, double out[8]) {
   const Real* wcol = static_cast<const Real*>(L->wrho);
   const bool res = L->grid.bc_x == RPK_BC_RESERVOIR;
   const int wm = wall_mask(L);
+  bool pair = false;
+  if constexpr (sizeof(Real) == 4) pair = !L->streamed && !wm && !res && !L->rot_mode && L->grid.nx % 2 == 0;
+  if (pair) {
+    if constexpr (sizeof(Real) == 4) {
+      // two points per thread (3 blocks per SM)
+      const int64_t pneed = (L->npts / 2 + kDiagThreads - 1) / kDiagThreads;
+      const int pblk = (int)std::max<int64_t>(1, std::min<int64_t>(std::min<int64_t>(kDiagBlocks, (int64_t)L->sms * 3), pneed));
+      k_diag_pair<Store><<<pblk, kDiagThreads, 0, L->stream>>>(K, pin, e, L->diag_partial);
+      rpk_status st0 = check_launch("k_diag_pair");
+      if (st0 != RPK_OK) return st0;
+      k_diag_final<<<1, 1024, 0, L->stream>>>(L->diag_partial, pblk, L->diag_out);
+      st0 = check_launch("k_diag_final");
+      if (st0 != RPK_OK) return st0;
+      RPK_CUDA(cudaMemcpyAsync(out, L->diag_out, kDiagVals * sizeof(double), cudaMemcpyDeviceToHost,
+                               L->stream));
+      RPK_CUDA(cudaStreamSynchronize(L->stream));
+      return RPK_OK;
+    }
+  }
   if (L->streamed) {
     k_diag<Store, Real, false, 0><<<nblk, kDiagThreads, 0, L->stream>>>(K, pin, e, gh, L->diag_partial, wcol);
   } else if (wm) {
