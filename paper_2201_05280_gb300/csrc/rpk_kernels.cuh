@@ -677,6 +677,7 @@ __global__ void __launch_bounds__(kDiagThreads, sizeof(Real) == 4 ? 4 : 1)
   double acc[kDiagVals - 1] = {0, 0, 0, 0, 0, 0, INFINITY};
   const int64_t npts = 2 * K.n3;
   const double t0 = (double)K.theta0;
+  [[maybe_unused]] int64_t npts_here = 0;  // points of this thread (FP32 arithmetic)
   for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < npts;
        p += (int64_t)gridDim.x * blockDim.x) {
     PointIdx P;
@@ -733,12 +734,20 @@ __global__ void __launch_bounds__(kDiagThreads, sizeof(Real) == 4 ? 4 : 1)
     const double Ee = K.paper ? 0.5 * (double)K.delta * ((double)m.rho * ((double)K.theta0 + (double)m.dR) -
                                                           (double)K.theta0)
                               : (double)e_in[p];
-    acc[0] += 1.0 + dm;
+    if constexpr (sizeof(Real) == 8) {
+      acc[0] += 1.0 + dm;
+      // sum g c^2/2 = 3 theta0/2 + sum w h c^2/2 ; Er = delta theta0/2 + e
+      acc[4] += (1.5 * t0 + 0.5 * (double)K.delta * t0) + (ek + Ee);
+    } else {
+      // the per-point constants (1 and 3 theta0/2 + delta theta0/2) are added
+      // once per thread below
+      acc[0] += dm;
+      acc[4] += ek + Ee;
+      ++npts_here;
+    }
     acc[1] += jx;
     acc[2] += jy;
     acc[3] += jz;
-    // sum g c^2/2 = 3 theta0/2 + sum w h c^2/2 ; Er = delta theta0/2 + e
-    acc[4] += (1.5 * t0 + 0.5 * (double)K.delta * t0) + (ek + Ee);
     acc[6] = fmin(acc[6], gmin);
     // H1 from f = (1 - beta*) g + beta* f^mix, per point in the arithmetic
     // precision of the path, accumulated in FP64
@@ -760,7 +769,14 @@ __global__ void __launch_bounds__(kDiagThreads, sizeof(Real) == 4 ? 4 : 1)
       Hp += hterm(w, Real(1) + keep * h[2 * k + 1] + beta * (ev + od));
       Hp += hterm(w, Real(1) + keep * h[2 * k + 2] + beta * (ev - od));
     });
-    acc[5] += (double)Hp - 0.5 * (double)K.delta * (double)m.rho * log(t0 + (double)m.dR);
+    if constexpr (sizeof(Real) == 8)
+      acc[5] += (double)Hp - 0.5 * (double)K.delta * (double)m.rho * log(t0 + (double)m.dR);
+    else  // FP32 arithmetic: the rotational term's logarithm in FP32 too
+      acc[5] += (double)(Hp - Real(0.5) * K.delta * m.rho * __logf(K.theta0 + m.dR));
+  }
+  if constexpr (sizeof(Real) == 4) {
+    acc[0] += (double)npts_here;
+    acc[4] += (double)npts_here * (1.5 * t0 + 0.5 * (double)K.delta * t0);
   }
   diag_block_reduce(acc, partial);
 }
@@ -778,6 +794,7 @@ __global__ void __launch_bounds__(kDiagThreads, 3)
   const int nxp = K.nx >> 1;
   const int64_t n3p = K.n3 >> 1;
   const double t0 = (double)K.theta0;
+  int64_t npts_here = 0;
   const float beta = K.beta, keep = 1.f - K.beta;
   auto hterm = [](float w, float fw) {  // w (fw ln fw - fw), fw = f/w
     return fw > 0.f ? w * (fw * __logf(fw) - fw) : NAN;
@@ -821,16 +838,19 @@ __global__ void __launch_bounds__(kDiagThreads, 3)
     const float p2[2] = {m.dP[2].v.x, m.dP[2].v.y};
 #pragma unroll
     for (int l = 0; l < 2; ++l) {
-      acc[0] += 1.0 + (double)drho[l];
+      acc[0] += (double)drho[l];
       acc[1] += (double)jx[l];
       acc[2] += (double)jy[l];
       acc[3] += (double)jz[l];
-      acc[4] += (1.5 * t0 + 0.5 * (double)K.delta * t0) +
-                (0.5 * ((double)p0[l] + (double)p1[l] + (double)p2[l]) + (double)ev[l]);
-      acc[5] += (double)Hp[l] - 0.5 * (double)K.delta * (double)rho[l] * log(t0 + (double)dR[l]);
+      acc[4] += 0.5 * ((double)p0[l] + (double)p1[l] + (double)p2[l]) + (double)ev[l];
+      acc[5] += (double)(Hp[l] - 0.5f * K.delta * rho[l] * __logf(K.theta0 + dR[l]));
       acc[6] = fmin(acc[6], (double)gm[l]);
     }
+    npts_here += 2;
   }
+  // the per-point constants: 1 (mass) and 3 theta0/2 + delta theta0/2 (energy)
+  acc[0] += (double)npts_here;
+  acc[4] += (double)npts_here * (1.5 * t0 + 0.5 * (double)K.delta * t0);
   diag_block_reduce(acc, partial);
 }
 
