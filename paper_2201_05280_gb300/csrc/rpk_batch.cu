@@ -98,50 +98,7 @@ __global__ void __launch_bounds__(kThreads)
       Store* pout = bufs[cur ^ 1];
       const bool snap = (t % save_every) == 0;
       float* sn = snaps + T->snap_off + (int64_t)(t / save_every) * 4 * np;
-      // 1. pull + collide + exchange of every point of the tube; FP32
-      //    arithmetic on an even tube: two x-adjacent points per thread in packed
-      //    FP32x2 form (the pairs next to the reservoirs gather point by point)
-      bool pairs = false;
-      if constexpr (sizeof(Real) == 4) pairs = !streamed && nx % 2 == 0 && nx >= 4;
-      if (pairs) {
-        if constexpr (sizeof(Real) == 4) {
-          using IO = PairIO<Store>;
-          using Word = typename IO::Word;
-          const int nxp = nx >> 1;
-          for (int j = tid; j < 2 * nxp; j += kThreads) {
-            const int s = j >= nxp, i = j - s * nxp, p0 = s * nx + 2 * i;
-            F2 h[kQ];
-            if (i > 0 && i < nxp - 1) {
-              gather_pair<Store>(reinterpret_cast<const Word*>(pin), K, s, i, 0, 0, h);
-            } else {
-              Real ha[kQ], hb[kQ];
-              gather<Store, Real, true, 1>(pin, ghost, K, tube_point(nx, p0), ha);
-              gather<Store, Real, true, 1>(pin, ghost, K, tube_point(nx, p0 + 1), hb);
-#pragma unroll
-              for (int q = 0; q < kQ; ++q) h[q] = F2(ha[q], hb[q]);
-            }
-            Mom<F2> m;
-            Word* out = reinterpret_cast<Word*>(pout) + (int64_t)(s * kQ) * nxp + i;
-            const F2 es = collide_emit<Real, false>(
-                K, h, F2(sE[p0], sE[p0 + 1]), [&](int q, F2 v) { out[(int64_t)q * nxp] = IO::from_f2(v); }, m);
-            const F2 ux = m.j[0] * m.inv_rho;
-            const F2 kap = K.kapc * m.rho * (K.theta0 + m.dth);
-            sS[p0] = es.v.x, sS[p0 + 1] = es.v.y;
-            sD[p0] = m.drho.v.x, sD[p0 + 1] = m.drho.v.y;
-            uc[p0] = ux.v.x, uc[p0 + 1] = ux.v.y;
-            sK[p0] = kap.v.x, sK[p0 + 1] = kap.v.y;
-            flag_moments2(m, K.theta0, status);
-            if (snap) {
-              const F2 th = K.theta0 + m.dT;
-              const F2 er = (Real(0.5) * K.delta) * m.rho * (K.theta0 + m.dR);
-              sn[p0] = 1.f + m.drho.v.x, sn[p0 + 1] = 1.f + m.drho.v.y;
-              sn[np + p0] = ux.v.x, sn[np + p0 + 1] = ux.v.y;
-              sn[2 * np + p0] = th.v.x, sn[2 * np + p0 + 1] = th.v.y;
-              sn[3 * np + p0] = er.v.x, sn[3 * np + p0 + 1] = er.v.y;
-            }
-          }
-        }
-      } else
+      // 1. pull + collide + exchange of every point of the tube
       for (int p = tid; p < np; p += kThreads) {
         const PointIdx P = tube_point(nx, p);
         Real h[kQ];

@@ -899,7 +899,7 @@ static __global__ void __launch_bounds__(256) k_check_fields(const double* __res
     if (!(r > 0.0) || !(t > 0.0) || !(q > 0.0) || !isfinite(r) || !isfinite(t) || !isfinite(q) ||
         !isfinite(ux) || !isfinite(uy) || !isfinite(uz))
       bad = 1;
-    v = fmax(v, (3.0 * t + delta * q) / (3.0 + delta));
+    v = fmax(v, 3.0 * t + delta * q);  // divided by 3 + delta once, below
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
@@ -908,7 +908,7 @@ static __global__ void __launch_bounds__(256) k_check_fields(const double* __res
   __syncthreads();
   if (threadIdx.x == 0) {
     for (int w = 1; w < 8; ++w) v = fmax(v, red[w]);
-    out[2 * blockIdx.x] = v;
+    out[2 * blockIdx.x] = v / (3.0 + delta);
     out[2 * blockIdx.x + 1] = bad_any ? 1.0 : 0.0;
   }
 }
