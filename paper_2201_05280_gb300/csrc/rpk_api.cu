@@ -378,6 +378,31 @@ static rpk_status ensure_stage(rpk_lattice* L) {
   return RPK_OK;
 }
 
+// Device address under which the current device reads or writes host memory
+// p directly (NVLink-C2C on Grace systems, PCIe elsewhere): pinned memory
+// through its mapped device pointer, pageable memory where the device has
+// pageable-memory access; false where it has no direct access.
+static bool host_view(const rpk_lattice* L, const void* p, void** out) {
+  cudaPointerAttributes a{};
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  if (a.type == cudaMemoryTypeHost && a.devicePointer) {
+    *out = a.devicePointer;
+    return true;
+  }
+  int pageable = 0;
+  if (a.type == cudaMemoryTypeUnregistered &&
+      cudaDeviceGetAttribute(&pageable, cudaDevAttrPageableMemoryAccess, L->device) == cudaSuccess &&
+      pageable) {
+    *out = const_cast<void*>(p);
+    return true;
+  }
+  cudaGetLastError();
+  return false;
+}
+
 rpk_status rpk_init_fields(rpk_lattice* L, const double* rho, const double* u,
                            const double* T, const double* R, int on_device) {
   if (!L || !rho || !u || !T || !R) return fail(RPK_ERR_ARG, "NULL argument");
@@ -388,33 +413,42 @@ rpk_status rpk_init_fields(rpk_lattice* L, const double* rho, const double* u,
   const int64_t n = L->npts;
   const double *drho = rho, *du = u, *dT = T, *dR = R;
   if (!on_device) {
-    // one copy per field into the staging buffer; checked on the device below
-    rpk_status st = ensure_stage(L);
-    if (st != RPK_OK) return st;
-    double* s = L->stage;
-    RPK_CUDA(cudaMemcpyAsync(s, rho, n * sizeof(double), cudaMemcpyHostToDevice, L->stream));
-    RPK_CUDA(cudaMemcpyAsync(s + n, u, 3 * n * sizeof(double), cudaMemcpyHostToDevice, L->stream));
-    RPK_CUDA(cudaMemcpyAsync(s + 4 * n, T, n * sizeof(double), cudaMemcpyHostToDevice, L->stream));
-    RPK_CUDA(cudaMemcpyAsync(s + 5 * n, R, n * sizeof(double), cudaMemcpyHostToDevice, L->stream));
-    drho = s;
-    du = s + n;
-    dT = s + 4 * n;
-    dR = s + 5 * n;
+    // host fields: read in place by the initialisation kernel where the device
+    // can reach them, otherwise one copy per field into the staging buffer
+    void* v[4];
+    if (host_view(L, rho, &v[0]) && host_view(L, u, &v[1]) && host_view(L, T, &v[2]) &&
+        host_view(L, R, &v[3])) {
+      drho = static_cast<const double*>(v[0]);
+      du = static_cast<const double*>(v[1]);
+      dT = static_cast<const double*>(v[2]);
+      dR = static_cast<const double*>(v[3]);
+    } else {
+      rpk_status st = ensure_stage(L);
+      if (st != RPK_OK) return st;
+      double* s = L->stage;
+      RPK_CUDA(cudaMemcpyAsync(s, rho, n * sizeof(double), cudaMemcpyHostToDevice, L->stream));
+      RPK_CUDA(cudaMemcpyAsync(s + n, u, 3 * n * sizeof(double), cudaMemcpyHostToDevice, L->stream));
+      RPK_CUDA(cudaMemcpyAsync(s + 4 * n, T, n * sizeof(double), cudaMemcpyHostToDevice, L->stream));
+      RPK_CUDA(cudaMemcpyAsync(s + 5 * n, R, n * sizeof(double), cudaMemcpyHostToDevice, L->stream));
+      drho = s;
+      du = s + n;
+      dT = s + 4 * n;
+      dR = s + 5 * n;
+    }
   }
-  // validation and the largest initial theta (for nsub = 0) in one device pass
-  const int nb = 256;
-  k_check_fields<<<nb, 256, 0, L->stream>>>(drho, du, dT, dR, n, L->relax.delta, L->diag_partial);
-  RPK_CUDA(cudaGetLastError());
-  std::vector<double> part(2 * nb);
-  RPK_CUDA(cudaMemcpyAsync(part.data(), L->diag_partial, 2 * nb * sizeof(double),
-                           cudaMemcpyDeviceToHost, L->stream));
+  // one pass: the initial state, the check of the inputs and the largest theta
+  L->init_ok = false;
+  rpk_status st = with_ops(L->grid.precision,
+                           [&](auto ops) { return decltype(ops)::init(L, drho, du, dT, dR); });
+  if (st != RPK_OK) return st;
+  unsigned long long check[2] = {0, 0};
+  RPK_CUDA(cudaMemcpyAsync(check, L->diag_out, sizeof(check), cudaMemcpyDeviceToHost, L->stream));
   RPK_CUDA(cudaStreamSynchronize(L->stream));
-  double tmax = -INFINITY;
-  for (int b = 0; b < nb; ++b) {
-    if (part[2 * b + 1] != 0.0)
-      return fail(RPK_ERR_PARAM, "fields need finite rho > 0, theta_T > 0, theta_R > 0 and finite u");
-    tmax = std::max(tmax, part[2 * b]);
-  }
+  if (check[1] != 0)
+    return fail(RPK_ERR_PARAM, "fields need finite rho > 0, theta_T > 0, theta_R > 0 and finite u");
+  double tmax;
+  std::memcpy(&tmax, &check[0], sizeof(double));
+  tmax /= 3.0 + L->relax.delta;
   if (!(tmax > 0.0) || !std::isfinite(tmax)) return fail(RPK_ERR_PARAM, "fields need theta > 0");
   // FTCS sub-steps from the largest initial theta when nsub = 0
   if (L->relax.nsub == 0) {
@@ -431,9 +465,6 @@ rpk_status rpk_init_fields(rpk_lattice* L, const double* rho, const double* u,
   } else {
     L->nsub = L->relax.nsub;
   }
-  rpk_status st = with_ops(L->grid.precision,
-                           [&](auto ops) { return decltype(ops)::init(L, drho, du, dT, dR); });
-  if (st != RPK_OK) return st;
   RPK_CUDA(cudaMemsetAsync(L->status, 0, sizeof(unsigned), L->stream));
   RPK_CUDA(cudaStreamSynchronize(L->stream));
   L->streamed = true;
@@ -464,21 +495,39 @@ rpk_status rpk_read_moments(rpk_lattice* L, double* rho, double* u, double* T, d
   RPK_CUDA(cudaSetDevice(L->device));
   const int64_t n = L->npts;
   double *o_rho = rho, *o_u = u, *o_T = T, *o_R = R, *o_E = E;
+  bool staged = false;
   if (!on_device) {
-    rpk_status st = ensure_stage(L);
-    if (st != RPK_OK) return st;
-    double* s = L->stage;
-    o_rho = rho ? s : nullptr;
-    o_u = u ? s + n : nullptr;
-    o_T = T ? s + 4 * n : nullptr;
-    o_R = R ? s + 5 * n : nullptr;
-    o_E = E ? s + 6 * n : nullptr;
+    // host outputs: written in place by the moments kernel where the device
+    // can reach them, otherwise through the staging buffer
+    double* outs[5] = {rho, u, T, R, E};
+    double* views[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    bool direct = true;
+    for (int k = 0; k < 5 && direct; ++k) {
+      void* v = nullptr;
+      if (outs[k]) {
+        direct = host_view(L, outs[k], &v);
+        views[k] = static_cast<double*>(v);
+      }
+    }
+    if (direct) {
+      o_rho = views[0], o_u = views[1], o_T = views[2], o_R = views[3], o_E = views[4];
+    } else {
+      rpk_status st = ensure_stage(L);
+      if (st != RPK_OK) return st;
+      double* s = L->stage;
+      o_rho = rho ? s : nullptr;
+      o_u = u ? s + n : nullptr;
+      o_T = T ? s + 4 * n : nullptr;
+      o_R = R ? s + 5 * n : nullptr;
+      o_E = E ? s + 6 * n : nullptr;
+      staged = true;
+    }
   }
   rpk_status st = with_ops(L->grid.precision, [&](auto ops) {
     return decltype(ops)::moments(L, o_rho, o_u, o_T, o_R, o_E);
   });
   if (st != RPK_OK) return st;
-  if (!on_device) {
+  if (staged) {
     const size_t b = n * sizeof(double);
     if (rho) RPK_CUDA(cudaMemcpyAsync(rho, o_rho, b, cudaMemcpyDeviceToHost, L->stream));
     if (u) RPK_CUDA(cudaMemcpyAsync(u, o_u, 3 * b, cudaMemcpyDeviceToHost, L->stream));

@@ -558,26 +558,54 @@ __device__ __forceinline__ void init_point(const StepConst<Real>& K, Real half_d
 }
 
 // Initial state of every point: writes its own slots (post-stream state), e,
-// and u(0) into both ring slots (the first step advects with u(0)).
+// and u(0) into both ring slots (the first step advects with u(0)). The same
+// pass checks the inputs: check[0] receives (as the bits of a non-negative
+// double, by atomic maximum) the largest 3 theta_T + delta theta_R, check[1]
+// a nonzero word where some rho, theta_T or theta_R is not finite and positive
+// or some velocity component is not finite. The inputs may be host memory the
+// device can read directly.
 template <typename Store, typename Real>
 __global__ void __launch_bounds__(128)
     k_init(StepConst<Real> K, Real half_dt_over_tau1, const double* __restrict__ rho_in,
            const double* __restrict__ u_in, const double* __restrict__ T_in,
            const double* __restrict__ R_in, Store* __restrict__ pout, Real* __restrict__ e_out,
-           Real* __restrict__ u0, Real* __restrict__ u1) {
+           Real* __restrict__ u0, Real* __restrict__ u1, unsigned long long* __restrict__ check) {
   PointIdx P;
-  if (!point_from_block(K, P)) return;
-  const int64_t npts = 2 * K.n3;
-  const int64_t p = (int64_t)P.s * K.n3 + P.cell;
-  const double ux = u_in[p], uy = u_in[npts + p], uz = u_in[2 * npts + p];
-  Real h[kQ], e;
-  init_point(K, half_dt_over_tau1, rho_in[p], ux, uy, uz, T_in[p], R_in[p], h, e);
-  Store* out = pout + (int64_t)(P.s * kQ) * K.n3 + P.cell;
+  const bool in = point_from_block(K, P);
+  double tv = 0.0;
+  bool bad = false;
+  if (in) {
+    const int64_t npts = 2 * K.n3;
+    const int64_t p = (int64_t)P.s * K.n3 + P.cell;
+    const double r = rho_in[p], T = T_in[p], R = R_in[p];
+    const double ux = u_in[p], uy = u_in[npts + p], uz = u_in[2 * npts + p];
+    bad = !(r > 0.0) || !(T > 0.0) || !(R > 0.0) || !isfinite(r) || !isfinite(T) || !isfinite(R) ||
+          !isfinite(ux) || !isfinite(uy) || !isfinite(uz);
+    if (!bad) {
+      tv = 3.0 * T + (double)K.delta * R;
+      Real h[kQ], e;
+      init_point(K, half_dt_over_tau1, r, ux, uy, uz, T, R, h, e);
+      Store* out = pout + (int64_t)(P.s * kQ) * K.n3 + P.cell;
 #pragma unroll
-  for (int q = 0; q < kQ; ++q) out[(int64_t)q * K.n3] = from_real<Store, Real>(h[q]);
-  e_out[p] = e;
-  u0[p] = Real(ux); u0[npts + p] = Real(uy); u0[2 * npts + p] = Real(uz);
-  u1[p] = Real(ux); u1[npts + p] = Real(uy); u1[2 * npts + p] = Real(uz);
+      for (int q = 0; q < kQ; ++q) out[(int64_t)q * K.n3] = from_real<Store, Real>(h[q]);
+      e_out[p] = e;
+      u0[p] = Real(ux); u0[npts + p] = Real(uy); u0[2 * npts + p] = Real(uz);
+      u1[p] = Real(ux); u1[npts + p] = Real(uy); u1[2 * npts + p] = Real(uz);
+    }
+  }
+  // positive doubles order like their bit patterns: a warp maximum, then one
+  // atomic per warp
+  unsigned long long bits = (unsigned long long)__double_as_longlong(tv);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long other = __shfl_xor_sync(0xffffffffu, bits, o);
+    bits = other > bits ? other : bits;
+  }
+  const unsigned any_bad = __any_sync(0xffffffffu, bad);
+  if ((threadIdx.x & 31) == 0) {
+    atomicMax(check, bits);
+    if (any_bad) atomicOr(check + 1, 1ull);
+  }
 }
 
 // Reservoir table: for the low (side 0) and high (side 1) x end, the h of the
@@ -873,43 +901,6 @@ static __global__ void __launch_bounds__(1024) k_diag_final(const double* __rest
     double v = red[0][k];
     for (int w = 1; w < (int)(blockDim.x / 32); ++w) v = (k == 6) ? fmin(v, red[w][k]) : v + red[w][k];
     out[k] = v;
-  }
-}
-
-// Checks the initial fields and finds the hottest point: per block, the
-// largest theta = (3 theta_T + delta theta_R)/(3 + delta) (eq. thetadef; for
-// nsub) and a flag that is 1 where some rho, theta_T or theta_R is not finite
-// and positive or some velocity component is not finite. out[2 b] = max theta,
-// out[2 b + 1] = flag of block b.
-static __global__ void __launch_bounds__(256) k_check_fields(const double* __restrict__ rho,
-                                                      const double* __restrict__ u,
-                                                      const double* __restrict__ T,
-                                                      const double* __restrict__ R, int64_t n,
-                                                      double delta, double* __restrict__ out) {
-  __shared__ double red[8];
-  __shared__ int bad_any;
-  if (threadIdx.x == 0) bad_any = 0;
-  __syncthreads();
-  double v = -INFINITY;
-  int bad = 0;
-  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n;
-       p += (int64_t)gridDim.x * blockDim.x) {
-    const double r = rho[p], t = T[p], q = R[p];
-    const double ux = u[p], uy = u[n + p], uz = u[2 * n + p];
-    if (!(r > 0.0) || !(t > 0.0) || !(q > 0.0) || !isfinite(r) || !isfinite(t) || !isfinite(q) ||
-        !isfinite(ux) || !isfinite(uy) || !isfinite(uz))
-      bad = 1;
-    v = fmax(v, 3.0 * t + delta * q);  // divided by 3 + delta once, below
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
-  if (bad) bad_any = 1;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    for (int w = 1; w < 8; ++w) v = fmax(v, red[w]);
-    out[2 * blockIdx.x] = v / (3.0 + delta);
-    out[2 * blockIdx.x + 1] = bad_any ? 1.0 : 0.0;
   }
 }
 

@@ -229,9 +229,11 @@ rpk_status Ops<Store, Real>::init(rpk_lattice* L, const double* rho, const doubl
   const StepConst<Real> K = make_const<Real>(L);
   const Real hdt = Real(0.5 * L->relax.dt / L->relax.tau1);
   L->cur = 0;
+  unsigned long long* check = reinterpret_cast<unsigned long long*>(L->diag_out);
+  RPK_CUDA(cudaMemsetAsync(check, 0, 2 * sizeof(unsigned long long), L->stream));
   k_init<Store, Real><<<point_grid(L, 128), 128, 0, L->stream>>>(
       K, hdt, rho, u, T, R, static_cast<Store*>(L->pop[0]), static_cast<Real*>(L->e),
-      static_cast<Real*>(L->u[0]), static_cast<Real*>(L->u[1]));
+      static_cast<Real*>(L->u[0]), static_cast<Real*>(L->u[1]), check);
   return check_launch("k_init");
 }
 
