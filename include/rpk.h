@@ -220,9 +220,8 @@ rpk_status rpk_set_x_walls(rpk_lattice* lat, const double* walls8);
 /* Initial state from hydrodynamic fields (layout above): rho > 0, u (3
  * planes), theta_T > 0, theta_R > 0. f = f^Eq(rho, u, theta_T I), then
  * g = f - (dt/2) Omega(f) and the auxiliary E_R (Sec. 5). Host arrays when
- * on_device = 0 (read in place by the device where it can reach them --
- * pinned memory, or pageable memory on systems with pageable-memory access
- * such as Grace -- otherwise copied through a staging buffer), device arrays
+ * on_device = 0 (pinned host memory is read in place by the device over the
+ * host link; pageable memory is copied through a staging buffer), device arrays
  * of this device when 1. The same device pass checks the inputs:
  * RPK_ERR_PARAM if some rho, theta_T, theta_R is not finite and positive or
  * some u is not finite, and then the lattice is left uninitialised (its
@@ -236,8 +235,8 @@ rpk_status rpk_step(rpk_lattice* lat, int64_t n);
 /* Hydrodynamic fields of the current state: rho, u (3 planes), theta_T and
  * theta_R of the physical distribution, and E_R = delta rho theta_R / 2. Any
  * output pointer may be NULL to skip it. Host arrays when on_device = 0
- * (written in place by the device where it can reach them, as in
- * rpk_init_fields, otherwise through the staging buffer), device arrays when
+ * (pinned memory written in place by the device, pageable memory through the
+ * staging buffer), device arrays when
  * 1. Synchronises the stream; returns RPK_ERR_NUMERIC if the device status
  * flags are set (the arrays are still written). */
 rpk_status rpk_read_moments(rpk_lattice* lat, double* rho, double* u, double* theta_T,
