@@ -115,7 +115,7 @@ __device__ __forceinline__ void flag_moments2(const Mom<F2>& m, float theta0, un
 
 // The pull-stream + collide + exchange step of k_collide for two x-adjacent
 // points per thread on a periodic grid with nx even, FP32 arithmetic in
-// packed FP32x2 form (same numbers as the one-point kernel's FP32 path, half
+// packed FP32x2 form (the one-point kernel's FP32 arithmetic to rounding, half
 // the arithmetic instructions; pair words halve the loads and stores).
 // Thread (blockIdx.x * blockDim.x + threadIdx.x) owns x0 = 2 * that index.
 template <typename Store>

@@ -1,0 +1,79 @@
+"""The step's kernel variants agree with each other point by point.
+
+The grid chooses among kernels for the same arithmetic of the step (Sec. 5):
+the collision with one point per thread (nx odd) or with two x-adjacent points
+per thread in packed FP32x2 form (nx even; pair words, straddled for odd x
+shifts), and the transport's one-point or four-point kernels (FP32 fields,
+nx % 4 == 0). A field of period p in x run on nx = p, 2p and 4p is the same
+problem, so the 2p and 4p runs must give the p-run's moments tiled. The
+packed and scalar forms round alike per operation but are not bit-identical
+(the scalar instantiation differs in the last bits of ~20% of the moments on
+random inputs), so the bound is FP32 rounding carried through the steps, and
+for 16-bit storage the odd flip of a stored value's last bit: measured on
+GB300, max|difference| / max(|field|, scale) over all fields is at most
+2.8e-9 (FP32), 7.5e-7 (FP16) and 1.2e-5 (BF16) after 6 steps. A wrong source column or a missed edge word
+moves a population by its whole deviation (~1e-2 of the field) and fails.
+p = 45 gives rows of 45 and 90 pair columns, p = 21 a row shorter than a
+block, p = 1 the one-pair row (every x neighbour is the point itself).
+"""
+import numpy as np
+import pytest
+
+import paper_2201_05280_gb300 as rpk
+import rpk_inputs as I
+
+pytestmark = pytest.mark.gpu
+
+T0 = 0.2948964908710633
+RELAX = dict(delta=2.0, tau=0.6, tau1=0.8, b=0.3, k_r=0.9, nsub=2)
+KEYS = ("rho", "u", "T", "R", "Erot")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    from paper_2201_05280_gb300 import build as B
+    B.build()
+    import torch
+    assert torch.cuda.is_available()
+    torch.cuda.set_device(0)
+
+
+def _run(f, nx, ny, nz, prec, nsteps):
+    lat = rpk.Lattice(nx, ny, nz, precision=prec).set_relax(**RELAX)
+    lat.init_fields(f["rho"], f["u"], f["T"], f["R"]).step(nsteps)
+    out = lat.read_moments()
+    lat.close()
+    return out
+
+
+def _tile(m, p, ny, nz, reps):
+    t = I.tile({"rho": m["rho"], "u": m["u"], "T": m["T"], "R": m["R"]}, p, ny, nz, (reps, 1, 1))
+    t["Erot"] = I.tile({"rho": m["Erot"], "u": m["u"], "T": m["T"], "R": m["R"]}, p, ny, nz,
+                       (reps, 1, 1))["rho"]
+    return t
+
+
+# max|difference| / max(max|field|, scale): FP32 rounding, 16-bit last-bit flips
+BOUNDS = {"f32": 1e-7, "f16dev": 1e-5, "bf16dev": 1e-4}
+SCALE = {"rho": 1.0, "u": float(np.sqrt(1.4 * T0)), "T": T0, "R": T0, "Erot": T0}
+
+
+@pytest.mark.parametrize("prec", ["f32", "f16dev", "bf16dev"])
+@pytest.mark.parametrize("p,ny,nz", [(45, 5, 3), (21, 4, 2), (1, 3, 2)])
+def test_collide_and_transport_variants_agree(prec, p, ny, nz):
+    nsteps = 6
+    f = I.random_smooth(p, ny, nz, T0, seed=23)
+    ref = _run(f, p, ny, nz, prec, nsteps)
+    worst = {}
+    for reps in (2, 4):
+        got = _run(I.tile(f, p, ny, nz, (reps, 1, 1)), reps * p, ny, nz, prec, nsteps)
+        want = _tile(ref, p, ny, nz, reps)
+        for k in KEYS:
+            a = np.asarray(got[k]).reshape(-1)
+            b = np.asarray(want[k]).reshape(-1)
+            assert a.shape == b.shape, (k, a.shape, b.shape)
+            err = float(np.abs(a - b).max() / max(np.abs(b).max(), SCALE[k]))
+            worst[(reps, k)] = err
+    print("variants %s p %d: %s" % (prec, p, {"%d%s" % kk: "%.1e" % v for kk, v in worst.items()}))
+    bad = {kk: v for kk, v in worst.items() if not v <= BOUNDS[prec]}
+    assert not bad, (prec, p, bad)
