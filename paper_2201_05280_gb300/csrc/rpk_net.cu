@@ -177,18 +177,24 @@ __global__ void __launch_bounds__(kThreads) k_conv(ConvArgs P) {
 // Tensor-core (tcgen05) path of the residual-block convolutions: Co = Ci = 128,
 // 5 taps. One persistent CTA per SM keeps the layer's BF16 weights in shared
 // memory (A: 128 x 640, K-major) and walks over tiles of 128 output positions
-// of one sequence. Three roles run concurrently on double buffers:
-//   producers (warps 8-15) stage the tile's 132 input rows (positions
-//     q0 - 2 .. q0 + 129, activation applied, BF16) into B[i % 2], every
-//     load of the tile in flight at once (9 per thread);
-//   one issuing thread (warp 8, lane 0) waits for B[i % 2] and for the
-//     accumulator i % 2 to be free, issues 40 MMAs (M 128, N 128, K 16) into
-//     TMEM columns 128 (i % 2) .. + 127 and commits to two mbarriers (B free,
-//     accumulator full);
+// of one sequence. Three roles run concurrently:
+//   producers (warps 8-15) load tile i's 132 input rows (positions q0 - 2 ..
+//     q0 + 129, every load in flight at once, 9 per thread) into registers
+//     while the MMAs of tile i - 1 still read the single input buffer B, then
+//     wait for B to be free and store the rows (activation applied, BF16);
+//   one issuing thread (warp 8, lane 0) waits for B and for the accumulator
+//     i % 2 to be free, issues 40 MMAs (M 128, N 128, K 16) into TMEM columns
+//     128 (i % 2) .. + 127 and commits to two mbarriers (B free, accumulator
+//     full);
 //   the epilogue (warps 0-7; TMEM lane = output channel, lane quadrant
-//     warp % 4, warps 0-3 the first 64 columns and warps 4-7 the last 64)
-//     reads the accumulator, applies bias, mask and residual as k_conv does,
-//     and frees it.
+//     warp % 4) writes the tile as four quarters of 32 positions through two
+//     16 KB staging buffers in the output's own layout: the residual rows of
+//     the next quarter are bulk-copied into the other buffer (cp.async.bulk,
+//     completion on an mbarrier) while each thread adds its accumulator
+//     column, bias and mask to its elements of this one, and one thread
+//     bulk-copies the quarter to the output rows. The epilogue's global
+//     traffic is then two bulk copies per quarter instead of 64 loads and 64
+//     stores per thread, whose latency had set the tile period.
 // The operand of tap t is the staged tile seen from row t (forward) or 4 - t
 // (input gradient): in the interleaved no-swizzle layout (rows 16 bytes apart
 // inside each 8-column chunk) a row shift is a start-address offset.
@@ -201,10 +207,15 @@ constexpr uint32_t TC_A_LBO = TC_M * 16;                   // bytes between 8-wi
 // shared-memory banks (2128 / 4 = 532 = 20 mod 32)
 constexpr uint32_t TC_B_LBO = (TC_ROWS + 1) * 16;
 constexpr uint32_t TC_A_BYTES = (TC_K / 8) * TC_A_LBO;     // 163840
-constexpr uint32_t TC_B_BYTES = (TC_KC / 8) * TC_B_LBO;    // 34048 per buffer
-constexpr uint32_t TC_BAR_OFF = TC_A_BYTES + 2 * TC_B_BYTES;
+constexpr uint32_t TC_B_BYTES = (TC_KC / 8) * TC_B_LBO;    // 34048
+constexpr int TC_QTR = TC_N / 4;                           // positions per staged quarter tile
+constexpr uint32_t TC_SQ_BYTES = TC_QTR * TC_M * 4;        // 16384: FP32 rows of a quarter tile
+constexpr uint32_t TC_S_BYTES = 2 * TC_SQ_BYTES;           // two staging buffers
+constexpr uint32_t TC_S_OFF = TC_A_BYTES + TC_B_BYTES;
+constexpr uint32_t TC_BAR_OFF = TC_S_OFF + TC_S_BYTES;
 constexpr uint32_t TC_SMEM = TC_BAR_OFF + 128;             // 8 mbarriers + TMEM address
 static_assert(TC_SMEM <= 227 * 1024, "tensor-core tiles exceed shared memory");
+static_assert(TC_S_OFF % 128 == 0, "the staging buffer is a bulk-copy operand");
 constexpr int TC_THREADS = 512;
 constexpr int TC_EPI = 256;                                // epilogue threads (warps 0-7)
 constexpr int TC_PROD = TC_THREADS - TC_EPI;               // producer threads (warps 8-15)
@@ -270,12 +281,51 @@ __device__ __forceinline__ void tc_tile(const TcArgs& P, int tile, int& q0, int&
   }
 }
 
+// Barrier 1 among the 256 epilogue threads (the producers never use it).
+__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, %0;" ::"n"(TC_EPI) : "memory"); }
+
+// The same barrier, returning whether p holds in every epilogue thread: the
+// epilogue warps then leave their loops together and no warp waits at a
+// barrier that another has left.
+// 16 consecutive accumulator columns of this thread's TMEM lane (32x32b shape)
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+        "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+        "=r"(v[14]), "=r"(v[15])
+      : "r"(taddr));
+}
+
+__device__ __forceinline__ bool epi_all(bool p) {
+  int r;
+  asm volatile(
+      "{\n .reg .pred pi, po;\n setp.ne.b32 pi, %1, 0;\n bar.red.and.pred po, 1, %2, pi;\n"
+      " selp.b32 %0, 1, 0, po;\n}\n"
+      : "=r"(r)
+      : "r"((int)p), "n"(TC_EPI)
+      : "memory");
+  return r != 0;
+}
+
+// Bulk copy of the residual rows of quarter q of a tile (positions q0 + 32 q ..)
+// into a staging buffer, completing with its byte count on the mbarrier bar.
+__device__ __forceinline__ void qtr_load(const TcArgs& P, uint32_t bar, uint32_t dst, int q0, int cnt, int q) {
+  const int rows = min(TC_QTR, cnt - q * TC_QTR);
+  const uint32_t bytes = (uint32_t)rows * TC_M * 4;
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(P.res + (int64_t)(q0 + q * TC_QTR) * TC_M), "r"(bytes), "r"(bar)
+               : "memory");
+}
+
 __global__ void __launch_bounds__(TC_THREADS, 1) k_conv_tc(TcArgs P) {
   extern __shared__ __align__(1024) unsigned char tc_smem[];
   unsigned char* sA = tc_smem;
   unsigned char* sB = tc_smem + TC_A_BYTES;
+  float* sS = reinterpret_cast<float*>(tc_smem + TC_S_OFF);
   uint64_t* bars = reinterpret_cast<uint64_t*>(tc_smem + TC_BAR_OFF);
-  // bars: 0-1 B full, 2-3 B free, 4-5 accumulator full, 6-7 accumulator free
+  // bars: 0 B full, 1 B free, 2-3 accumulator full, 4-5 accumulator free, 6-7 residual in S[0], S[1]
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tc_smem + TC_BAR_OFF + 64);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
@@ -287,12 +337,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv_tc(TcArgs P) {
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   if (tid == 0) {
-    for (int b = 0; b < 2; ++b) {
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bars + b)), "r"(TC_PROD) : "memory");
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bars + 2 + b)), "r"(1) : "memory");
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bars + 4 + b)), "r"(1) : "memory");
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bars + 6 + b)), "r"(TC_EPI) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bars)), "r"(TC_PROD) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bars + 1)), "r"(1) : "memory");
+    for (int a = 0; a < 2; ++a) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bars + 2 + a)), "r"(1) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bars + 4 + a)), "r"(TC_EPI) : "memory");
     }
+    for (int q = 0; q < 2; ++q)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bars + 6 + q)), "r"(1) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   // weights: chunk c (k = 8c .. 8c + 7) of row m at c * TC_A_LBO + m * 16,
@@ -310,64 +362,62 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv_tc(TcArgs P) {
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tmem_slot;
-  const uint32_t a_base = smem_u32(sA), b_base = smem_u32(sB);
+  const uint32_t a_base = smem_u32(sA), b_base = smem_u32(sB), s_base = smem_u32(sS);
   const uint32_t bar0 = smem_u32(bars);
   bool ok = true;
 
   if (tid >= TC_EPI) {
     // producers, and the issuing thread
     const int ptid = tid - TC_EPI;
+    // 2112 (row, 8-channel chunk) elements, at most 9 per thread; consecutive
+    // threads take consecutive 32-byte chunks of a row (coalesced 512-byte rows)
+    constexpr int kElems = TC_ROWS * (TC_KC / 8);
+    constexpr int kBatch = (kElems + TC_PROD - 1) / TC_PROD;
+    static_assert(kBatch * TC_PROD >= kElems, "one batch of loads covers the tile");
     for (int i = 0, tile = blockIdx.x; tile < P.ntiles && ok; ++i, tile += gridDim.x) {
-      const int b = i & 1;
-      if (i >= 2) ok = __all_sync(0xffffffffu, mbar_wait(bar0 + 8 * (2 + b), ((i >> 1) - 1) & 1));
-      if (!ok) break;
       int q0, cnt, lo, len;
       tc_tile(P, tile, q0, cnt, lo, len);
-      unsigned char* dst = sB + b * TC_B_BYTES;
-      // 2112 (row, chunk) elements, at most 9 per thread: all loads of a
-      // thread are issued before any is converted; consecutive threads take
-      // consecutive 32-byte chunks of a row (coalesced rows of 512 bytes)
-      constexpr int kElems = TC_ROWS * (TC_KC / 8);
-      constexpr int kBatch = (kElems + TC_PROD - 1) / TC_PROD;
-      for (int e0 = ptid; e0 < kElems; e0 += TC_PROD * kBatch) {
-        float4 f[kBatch][2];
+      // every load of tile i is issued while the MMAs of tile i - 1 still read B
+      float4 f[kBatch][2];
 #pragma unroll
-        for (int u = 0; u < kBatch; ++u) {
-          const int e = e0 + u * TC_PROD;
-          const int r = e / (TC_KC / 8), c = e % (TC_KC / 8);
-          const int q = q0 - 2 + r;
-          f[u][0] = f[u][1] = make_float4(0.f, 0.f, 0.f, 0.f);
-          if (e < kElems && q >= lo && q < lo + len) {
-            const float4* src = reinterpret_cast<const float4*>(P.X + (int64_t)q * TC_KC + 8 * c);
-            f[u][0] = src[0];
-            f[u][1] = src[1];
-          }
-        }
-#pragma unroll
-        for (int u = 0; u < kBatch; ++u) {
-          const int e = e0 + u * TC_PROD;
-          if (e >= kElems) break;
-          const int r = e / (TC_KC / 8), c = e % (TC_KC / 8);
-          float4 f0 = f[u][0], f1 = f[u][1];
-          if (P.relu_in) {
-            f0.x = fmaxf(f0.x, 0.f), f0.y = fmaxf(f0.y, 0.f), f0.z = fmaxf(f0.z, 0.f), f0.w = fmaxf(f0.w, 0.f);
-            f1.x = fmaxf(f1.x, 0.f), f1.y = fmaxf(f1.y, 0.f), f1.z = fmaxf(f1.z, 0.f), f1.w = fmaxf(f1.w, 0.f);
-          }
-          *reinterpret_cast<uint4*>(dst + c * TC_B_LBO + r * 16) =
-              make_uint4(pack_bf16(f0.x, f0.y), pack_bf16(f0.z, f0.w), pack_bf16(f1.x, f1.y),
-                         pack_bf16(f1.z, f1.w));
+      for (int u = 0; u < kBatch; ++u) {
+        const int e = ptid + u * TC_PROD;
+        const int r = e / (TC_KC / 8), c = e % (TC_KC / 8);
+        const int q = q0 - 2 + r;
+        f[u][0] = f[u][1] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (e < kElems && q >= lo && q < lo + len) {
+          const float4* src = reinterpret_cast<const float4*>(P.X + (int64_t)q * TC_KC + 8 * c);
+          f[u][0] = src[0];
+          f[u][1] = src[1];
         }
       }
+      // B free: the MMAs of tile i - 1 have completed
+      if (i >= 1) ok = __all_sync(0xffffffffu, mbar_wait(bar0 + 8, (i - 1) & 1));
+      if (!ok) break;
+#pragma unroll
+      for (int u = 0; u < kBatch; ++u) {
+        const int e = ptid + u * TC_PROD;
+        if (e >= kElems) break;
+        const int r = e / (TC_KC / 8), c = e % (TC_KC / 8);
+        float4 f0 = f[u][0], f1 = f[u][1];
+        if (P.relu_in) {
+          f0.x = fmaxf(f0.x, 0.f), f0.y = fmaxf(f0.y, 0.f), f0.z = fmaxf(f0.z, 0.f), f0.w = fmaxf(f0.w, 0.f);
+          f1.x = fmaxf(f1.x, 0.f), f1.y = fmaxf(f1.y, 0.f), f1.z = fmaxf(f1.z, 0.f), f1.w = fmaxf(f1.w, 0.f);
+        }
+        *reinterpret_cast<uint4*>(sB + c * TC_B_LBO + r * 16) =
+            make_uint4(pack_bf16(f0.x, f0.y), pack_bf16(f0.z, f0.w), pack_bf16(f1.x, f1.y),
+                       pack_bf16(f1.z, f1.w));
+      }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      mbar_arrive(bar0 + 8 * b);  // B full (TC_PROD arrivals)
+      mbar_arrive(bar0);  // B full (TC_PROD arrivals)
       if (ptid == 0) {
-        // the issuing thread: B staged by all producers, accumulator free
-        bool go = mbar_wait(bar0 + 8 * b, (i >> 1) & 1);
-        if (go && i >= 2) go = mbar_wait(bar0 + 8 * (6 + b), ((i >> 1) - 1) & 1);
+        // the issuing thread: B staged by all producers, accumulator i % 2 free
+        const int acc = i & 1;
+        bool go = mbar_wait(bar0, i & 1);
+        if (go && i >= 2) go = mbar_wait(bar0 + 8 * (4 + acc), ((i >> 1) - 1) & 1);
         if (go) {
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-          const uint32_t bb = b_base + (uint32_t)b * TC_B_BYTES;
-          const uint32_t d = tmem + (uint32_t)(b * TC_N);
+          const uint32_t d = tmem + (uint32_t)(acc * TC_N);
 #pragma unroll 1
           for (int t = 0; t < TC_TAPS; ++t) {
             const int row0 = P.sgn > 0 ? t : TC_TAPS - 1 - t;
@@ -375,20 +425,20 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv_tc(TcArgs P) {
             for (int s = 0; s < TC_KC / 16; ++s) {
               const uint64_t ad =
                   tc_desc(a_base + (uint32_t)(t * (TC_KC / 8) + 2 * s) * TC_A_LBO, TC_A_LBO, 128);
-              const uint64_t bd = tc_desc(bb + (uint32_t)(2 * s) * TC_B_LBO + (uint32_t)row0 * 16, TC_B_LBO, 128);
-              const uint32_t acc = (t | s) ? 1u : 0u;
+              const uint64_t bd = tc_desc(b_base + (uint32_t)(2 * s) * TC_B_LBO + (uint32_t)row0 * 16, TC_B_LBO, 128);
+              const uint32_t accum = (t | s) ? 1u : 0u;
               asm volatile(
                   "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
                   " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
-                  "l"(ad), "l"(bd), "r"(TC_IDESC), "r"(acc)
+                  "l"(ad), "l"(bd), "r"(TC_IDESC), "r"(accum)
                   : "memory");
             }
           }
           asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                           bar0 + 8 * (2 + b))
+                           bar0 + 8)
                        : "memory");
           asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                           bar0 + 8 * (4 + b))
+                           bar0 + 8 * (2 + acc))
                        : "memory");
         } else {
           atomicOr(P.error, 1u);
@@ -397,56 +447,86 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv_tc(TcArgs P) {
       __syncwarp();
     }
   } else {
-    // epilogue: TMEM lane = output channel m; this warp's half of the columns
-    const int quad = warp & 3, half = warp >> 2;
+    // epilogue: TMEM lane = output channel m; a tile is written as four
+    // quarters of 32 positions through two 16 KB staging buffers (quarter q in
+    // S[q % 2]); warps 0-3 take positions 0-15 of a quarter, warps 4-7 16-31.
+    // With a residual, the rows of quarter q + 1 are bulk-loaded into the other
+    // buffer while quarter q is computed; every quarter leaves as one bulk store.
+    const int quad = warp & 3, sub = warp >> 2;
     const int m = quad * 32 + lane;
     const float bm = P.bias ? P.bias[m] : 0.f;
+    const uint32_t rbar = bar0 + 8 * 6;  // 6: residual in S[0], 7: residual in S[1]
+    int rphase[2] = {0, 0};
     for (int i = 0, tile = blockIdx.x; tile < P.ntiles; ++i, tile += gridDim.x) {
-      const int b = i & 1;
-      ok = __all_sync(0xffffffffu, mbar_wait(bar0 + 8 * (4 + b), (i >> 1) & 1));
-      if (!ok) {
-        if (lane == 0) atomicOr(P.error, 1u);
-        break;
-      }
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const int acc = i & 1;
       int q0, cnt, lo, len;
       tc_tile(P, tile, q0, cnt, lo, len);
-#pragma unroll 1
-      for (int j = half * (TC_N / 64); j < (half + 1) * (TC_N / 64); ++j) {
-        uint32_t v[32];
-        asm volatile(
-            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
-            "%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
-              "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
-              "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]),
-              "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]),
-              "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
-            : "r"(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(b * TC_N + j * 32)));
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-        // all loads of the chunk first (out may alias res: each element is read
-        // and then written by this thread), then the stores
-        float add[32];
-        uint32_t drop = 0;  // bit k: masked out
-#pragma unroll
-        for (int k = 0; k < 32; ++k) {
-          const int n = j * 32 + k;
-          const int64_t o = (int64_t)(q0 + n) * TC_M + m;
-          add[k] = (P.res && n < cnt) ? P.res[o] : 0.f;
-          if (P.mask && n < cnt && !(P.mask[o] > 0.f)) drop |= 1u << k;
+      const int nq = (cnt + TC_QTR - 1) / TC_QTR;  // quarters holding positions
+      if (tid == 0) {
+        // both buffers are free once every earlier bulk store has read them out
+        asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+        if (P.res)
+          for (int q = 0; q < 2 && q < nq; ++q) qtr_load(P, rbar + 8 * q, s_base + q * TC_SQ_BYTES, q0, cnt, q);
+      }
+      ok = epi_all(mbar_wait(bar0 + 8 * (2 + acc), (i >> 1) & 1));
+      if (!ok) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      for (int q = 0; q < nq && ok; ++q) {
+        const int buf = q & 1;
+        const int rows = min(TC_QTR, cnt - q * TC_QTR);
+        const int64_t qq = (int64_t)(q0 + q * TC_QTR);
+        float* S = sS + buf * (TC_QTR * TC_M);
+        if (P.res) {
+          ok = epi_all(mbar_wait(rbar + 8 * buf, rphase[buf] & 1));
+          ++rphase[buf];
+          if (!ok) break;
+          if (tid == 0 && q >= 1 && q + 1 < nq) {
+            // the store of quarter q - 1 has read S[1 - buf] before the next rows land there
+            asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+            qtr_load(P, rbar + 8 * (1 - buf), s_base + (1 - buf) * TC_SQ_BYTES, q0, cnt, q + 1);
+          }
+        } else {
+          // the store of quarter q - 2 has read S[buf] (the latest one may still be reading the other)
+          if (tid == 0) asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+          epi_sync();
         }
+        uint32_t v[16];
+        tmem_ld16(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(acc * TC_N + q * TC_QTR + sub * 16), v);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        uint32_t drop = 0;  // bit k: masked out
+        if (P.mask) {
 #pragma unroll
-        for (int k = 0; k < 32; ++k) {
-          const int n = j * 32 + k;
-          if (n < cnt) {
-            const float val = ((drop >> k) & 1u) ? 0.f : __uint_as_float(v[k]) + bm;
-            P.out[(int64_t)(q0 + n) * TC_M + m] = val + add[k];
+          for (int k = 0; k < 16; ++k) {
+            const int r = sub * 16 + k;
+            if (r < rows && !(P.mask[(qq + r) * TC_M + m] > 0.f)) drop |= 1u << k;
           }
         }
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+          const int r = sub * 16 + k;
+          if (r < rows) {
+            float* sp = S + r * TC_M + m;
+            float val = ((drop >> k) & 1u) ? 0.f : __uint_as_float(v[k]) + bm;
+            if (P.res) val += *sp;
+            *sp = val;
+          }
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        epi_sync();
+        if (tid == 0) {
+          asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(P.out + qq * TC_M),
+                       "r"(s_base + buf * TC_SQ_BYTES), "r"((uint32_t)rows * TC_M * 4)
+                       : "memory");
+          asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+        }
       }
+      if (!ok) break;
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-      mbar_arrive(bar0 + 8 * (6 + b));  // accumulator free (TC_EPI arrivals)
+      mbar_arrive(bar0 + 8 * (4 + acc));  // accumulator free (TC_EPI arrivals)
     }
+    if (!ok && tid == 0) atomicOr(P.error, 1u);
+    // the output is written and S read out before the CTA ends
+    if (tid == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
@@ -701,7 +781,9 @@ rpk_status refresh_bf16(rpk_net* N) {
 rpk_status conv(rpk_net* N, const __nv_bfloat16* A, int M, int taps, int Kc, int sgn,
                 const float* X, int relu_in, float* out, const float* bias, const float* res,
                 const float* mask, int64_t nq, int seq_len, const int2* qseq = nullptr) {
-  const bool aligned = (((uintptr_t)A | (uintptr_t)X) & 15) == 0;
+  // 16-byte operands: the weights and inputs for cp.async, the output and
+  // residual rows for the epilogue's bulk copies
+  const bool aligned = (((uintptr_t)A | (uintptr_t)X | (uintptr_t)out | (uintptr_t)res) & 15) == 0;
   if (N->tc && M == TC_M && Kc == TC_KC && taps == TC_TAPS && aligned && nq > 0) {
     TcArgs T{A, X, out, bias, res, mask, nullptr, 0, seq_len, 0, sgn, relu_in, N->tc_error};
     if (qseq) {
