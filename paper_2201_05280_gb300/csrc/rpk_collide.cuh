@@ -118,11 +118,14 @@ __device__ __forceinline__ void flag_moments2(const Mom<F2>& m, float theta0, un
 // packed FP32x2 form (the one-point kernel's FP32 arithmetic to rounding, half
 // the arithmetic instructions; pair words halve the loads and stores).
 // Thread (blockIdx.x * blockDim.x + threadIdx.x) owns x0 = 2 * that index.
-template <typename Store>
+// kPaper: the paper's theta_R solver (the state holds theta_R - theta0; the
+// time-t theta_T(f) - theta0 goes to tt_out), as in k_collide.
+template <typename Store, bool kPaper = false>
 __global__ void __launch_bounds__(128, sizeof(Store) == 4 ? 3 : 4)
     k_collide_pair(StepConst<float> K, const Store* __restrict__ pin, Store* __restrict__ pout,
                    const float* __restrict__ e_in, float* __restrict__ e_out, float* __restrict__ drho_out,
-                   float* __restrict__ u_out, float* __restrict__ kap_out, unsigned* __restrict__ status) {
+                   float* __restrict__ u_out, float* __restrict__ kap_out, unsigned* __restrict__ status,
+                   float* __restrict__ tt_out) {
   using IO = PairIO<Store>;
   using Word = typename IO::Word;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -137,7 +140,7 @@ __global__ void __launch_bounds__(128, sizeof(Store) == 4 ? 3 : 4)
   gather_pair<Store>(reinterpret_cast<const Word*>(pin), K, s, i, y, z, h);
   Mom<F2> m;
   Word* out = reinterpret_cast<Word*>(pout) + (int64_t)(s * kQ) * n3p + cellp;
-  const F2 es = collide_emit<float, false>(
+  const F2 es = collide_emit<float, kPaper>(
       K, h, F2(reinterpret_cast<const float2*>(e_in)[pp]),
       [&](int q, F2 v) { out[(int64_t)q * n3p] = IO::from_f2(v); }, m);
   reinterpret_cast<float2*>(e_out)[pp] = es.v;
@@ -147,6 +150,7 @@ __global__ void __launch_bounds__(128, sizeof(Store) == 4 ? 3 : 4)
   u2[K.n3 + pp] = (m.j[1] * m.inv_rho).v;
   u2[2 * K.n3 + pp] = (m.j[2] * m.inv_rho).v;
   reinterpret_cast<float2*>(kap_out)[pp] = (K.kapc * m.rho * (K.theta0 + m.dth)).v;
+  if constexpr (kPaper) reinterpret_cast<float2*>(tt_out)[pp] = m.dT.v;
   flag_moments2(m, K.theta0, status);
 }
 

@@ -97,6 +97,18 @@ static rpk_status collide_launch(rpk_lattice* L, const StepConst<Real>& K) {
   Real* ucur = static_cast<Real*>(L->u[L->steps & 1]);
   const Real* wcol = static_cast<const Real*>(L->wrho);
   if (L->rot_mode) {
+    if constexpr (kPull && kBC == 0 && sizeof(Real) == 4) {
+      if (L->grid.nx % 2 == 0) {
+        // two x-adjacent points per thread, packed FP32x2 arithmetic
+        const dim3 grid((unsigned)((L->grid.nx / 2 + 127) / 128), (unsigned)L->grid.ny,
+                        (unsigned)(2 * L->grid.nz));
+        k_collide_pair<Store, true><<<grid, 128, 0, L->stream>>>(
+            K, pin, pout, static_cast<const Real*>(L->e), static_cast<Real*>(L->e_star),
+            static_cast<Real*>(L->drho), ucur, static_cast<Real*>(L->kap), L->status,
+            static_cast<Real*>(L->thbuf));
+        return check_launch("k_collide_pair");
+      }
+    }
     k_collide<Store, Real, kPull, kBC, true><<<point_grid(L, 128), 128, 0, L->stream>>>(
         K, pin, pout, static_cast<const Real*>(L->e), static_cast<Real*>(L->e_star),
         static_cast<Real*>(L->drho), ucur, static_cast<Real*>(L->kap),
@@ -108,9 +120,9 @@ static rpk_status collide_launch(rpk_lattice* L, const StepConst<Real>& K) {
       // two x-adjacent points per thread, packed FP32x2 arithmetic
       const dim3 grid((unsigned)((L->grid.nx / 2 + 127) / 128), (unsigned)L->grid.ny,
                       (unsigned)(2 * L->grid.nz));
-      k_collide_pair<Store><<<grid, 128, 0, L->stream>>>(
+      k_collide_pair<Store, false><<<grid, 128, 0, L->stream>>>(
           K, pin, pout, static_cast<const Real*>(L->e), static_cast<Real*>(L->e_star),
-          static_cast<Real*>(L->drho), ucur, static_cast<Real*>(L->kap), L->status);
+          static_cast<Real*>(L->drho), ucur, static_cast<Real*>(L->kap), L->status, nullptr);
       return check_launch("k_collide_pair");
     }
   }

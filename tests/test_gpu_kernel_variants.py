@@ -3,8 +3,9 @@
 The grid chooses among kernels for the same arithmetic of the step (Sec. 5):
 the collision with one point per thread (nx odd) or with two x-adjacent points
 per thread in packed FP32x2 form (nx even; pair words, straddled for odd x
-shifts), and the transport's one-point or four-point kernels (FP32 fields,
-nx % 4 == 0). A field of period p in x run on nx = p, 2p and 4p is the same
+shifts), in the conservative rotational form and in the paper's theta_R
+solver, and the transport's one-point or four-point kernels (conservative
+form, FP32 fields, nx % 4 == 0). A field of period p in x run on nx = p, 2p and 4p is the same
 problem, so the 2p and 4p runs must give the p-run's moments tiled. The
 packed and scalar forms round alike per operation but are not bit-identical
 (the scalar instantiation differs in the last bits of ~20% of the moments on
@@ -38,8 +39,9 @@ def _gpu():
     torch.cuda.set_device(0)
 
 
-def _run(f, nx, ny, nz, prec, nsteps):
+def _run(f, nx, ny, nz, prec, nsteps, mode="conservative"):
     lat = rpk.Lattice(nx, ny, nz, precision=prec).set_relax(**RELAX)
+    lat.set_rot_mode(mode)
     lat.init_fields(f["rho"], f["u"], f["T"], f["R"]).step(nsteps)
     out = lat.read_moments()
     lat.close()
@@ -58,15 +60,16 @@ BOUNDS = {"f32": 1e-7, "f16dev": 1e-5, "bf16dev": 1e-4}
 SCALE = {"rho": 1.0, "u": float(np.sqrt(1.4 * T0)), "T": T0, "R": T0, "Erot": T0}
 
 
+@pytest.mark.parametrize("mode", ["conservative", "paper"])
 @pytest.mark.parametrize("prec", ["f32", "f16dev", "bf16dev"])
 @pytest.mark.parametrize("p,ny,nz", [(45, 5, 3), (21, 4, 2), (1, 3, 2)])
-def test_collide_and_transport_variants_agree(prec, p, ny, nz):
+def test_collide_and_transport_variants_agree(prec, p, ny, nz, mode):
     nsteps = 6
     f = I.random_smooth(p, ny, nz, T0, seed=23)
-    ref = _run(f, p, ny, nz, prec, nsteps)
+    ref = _run(f, p, ny, nz, prec, nsteps, mode)
     worst = {}
     for reps in (2, 4):
-        got = _run(I.tile(f, p, ny, nz, (reps, 1, 1)), reps * p, ny, nz, prec, nsteps)
+        got = _run(I.tile(f, p, ny, nz, (reps, 1, 1)), reps * p, ny, nz, prec, nsteps, mode)
         want = _tile(ref, p, ny, nz, reps)
         for k in KEYS:
             a = np.asarray(got[k]).reshape(-1)
@@ -74,6 +77,6 @@ def test_collide_and_transport_variants_agree(prec, p, ny, nz):
             assert a.shape == b.shape, (k, a.shape, b.shape)
             err = float(np.abs(a - b).max() / max(np.abs(b).max(), SCALE[k]))
             worst[(reps, k)] = err
-    print("variants %s p %d: %s" % (prec, p, {"%d%s" % kk: "%.1e" % v for kk, v in worst.items()}))
+    print("variants %s %s p %d: %s" % (mode, prec, p, {"%d%s" % kk: "%.1e" % v for kk, v in worst.items()}))
     bad = {kk: v for kk, v in worst.items() if not v <= BOUNDS[prec]}
-    assert not bad, (prec, p, bad)
+    assert not bad, (mode, prec, p, bad)
