@@ -450,6 +450,105 @@ static __global__ void __launch_bounds__(kTBX * kTBY)
   st4(e_next, p, r);
 }
 
+// Paper-mode transport passes with four x-adjacent points per thread (periodic
+// FP32 grid, nx a multiple of 4): k_pm_pred, k_pm_corr and k_pm_ftcs point by
+// point, in the same order of operations.
+static __global__ void __launch_bounds__(kTBX * kTBY)
+    k_pm_pred4(StepConst<float> K, const float* __restrict__ r, const float* __restrict__ ucur,
+               float* __restrict__ rp) {
+  Quad Q;
+  if (!quad_from_block(K, Q)) return;
+  const int64_t npts = 2 * K.n3, p = Q.p;
+  float r0[4], adv[4] = {0.f, 0.f, 0.f, 0.f};
+  un4(ld4(r, p), r0);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    float u[4], rq[4];
+    un4(ld4(ucur, a * npts + p), u);
+    if (a == 0) {
+#pragma unroll
+      for (int l = 0; l < 3; ++l) rq[l] = r0[l + 1];
+      rq[3] = r[p + Q.xp];
+    } else {
+      un4(ld4(r, p + (a == 1 ? Q.yp : Q.zp)), rq);
+    }
+#pragma unroll
+    for (int l = 0; l < 4; ++l) adv[l] += u[l] * (rq[l] - r0[l]);
+  }
+  float o[4];
+#pragma unroll
+  for (int l = 0; l < 4; ++l) o[l] = r0[l] - K.dt * adv[l];
+  st4(rp, p, o);
+}
+
+static __global__ void __launch_bounds__(kTBX * kTBY)
+    k_pm_corr4(StepConst<float> K, const float* __restrict__ r, const float* __restrict__ rp,
+               const float* __restrict__ ucur, float* __restrict__ rc) {
+  Quad Q;
+  if (!quad_from_block(K, Q)) return;
+  const int64_t npts = 2 * K.n3, p = Q.p;
+  float q0[4], adv[4] = {0.f, 0.f, 0.f, 0.f};
+  un4(ld4(rp, p), q0);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    float u[4], rq[4];
+    un4(ld4(ucur, a * npts + p), u);
+    if (a == 0) {
+      rq[0] = rp[p + Q.xm];
+#pragma unroll
+      for (int l = 1; l < 4; ++l) rq[l] = q0[l - 1];
+    } else {
+      un4(ld4(rp, p + (a == 1 ? Q.ym : Q.zm)), rq);
+    }
+#pragma unroll
+    for (int l = 0; l < 4; ++l) adv[l] += u[l] * (q0[l] - rq[l]);
+  }
+  float r0[4], o[4];
+  un4(ld4(r, p), r0);
+#pragma unroll
+  for (int l = 0; l < 4; ++l) o[l] = 0.5f * (r0[l] + q0[l] - K.dt * adv[l]);
+  st4(rc, p, o);
+}
+
+static __global__ void __launch_bounds__(kTBX * kTBY)
+    k_pm_ftcs4(StepConst<float> K, const float* __restrict__ r, const float* __restrict__ drho,
+               const float* __restrict__ kap, const float* __restrict__ tt, float* __restrict__ rn, int last) {
+  Quad Q;
+  if (!quad_from_block(K, Q)) return;
+  const int64_t p = Q.p;
+  float r0[4], lap[4] = {0.f, 0.f, 0.f, 0.f};
+  un4(ld4(r, p), r0);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    float rpl[4], rmi[4];
+    if (a == 0) {
+#pragma unroll
+      for (int l = 0; l < 3; ++l) rpl[l] = r0[l + 1];
+      rpl[3] = r[p + Q.xp];
+      rmi[0] = r[p + Q.xm];
+#pragma unroll
+      for (int l = 1; l < 4; ++l) rmi[l] = r0[l - 1];
+    } else {
+      un4(ld4(r, p + (a == 1 ? Q.yp : Q.zp)), rpl);
+      un4(ld4(r, p + (a == 1 ? Q.ym : Q.zm)), rmi);
+    }
+#pragma unroll
+    for (int l = 0; l < 4; ++l) lap[l] += rpl[l] - 2.0f * r0[l] + rmi[l];
+  }
+  float dr[4], kp[4], o[4];
+  un4(ld4(drho, p), dr);
+  un4(ld4(kap, p), kp);
+#pragma unroll
+  for (int l = 0; l < 4; ++l) o[l] = r0[l] + K.hsub * 2.0f * kp[l] / ((1.0f + dr[l]) * K.delta) * lap[l];
+  if (last) {
+    float t[4];
+    un4(ld4(tt, p), t);
+#pragma unroll
+    for (int l = 0; l < 4; ++l) o[l] = K.ra_keep * o[l] + K.ra_t * t[l];
+  }
+  st4(rn, p, o);
+}
+
 // ---------------------------------------------------------------------------
 // Paper mode of the rotational solver (Sec. 5): after the collision has done
 // step 1 (first backward-Euler half step, stored in es), three passes on

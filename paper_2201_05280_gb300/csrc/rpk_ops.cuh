@@ -154,6 +154,23 @@ static rpk_status transport_launch(rpk_lattice* L, const StepConst<Real>& K) {
   if (L->rot_mode) {
     // paper mode: MacCormack on theta_R, FTCS sub-steps, the last with the
     // second relaxation half step (th holds the time-t theta_T)
+    if constexpr (kBC == 0 && sizeof(Real) == 4) {
+      if (L->grid.nx % 4 == 0) {
+        // periodic FP32 grid, nx a multiple of 4: four x-adjacent points per thread
+        const dim3 qgrid((unsigned)((L->grid.nx / 4 + kTBX - 1) / kTBX),
+                         (unsigned)((L->grid.ny + kTBY - 1) / kTBY), (unsigned)(2 * L->grid.nz));
+        k_pm_pred4<<<qgrid, tb, 0, L->stream>>>(K, es, ucur, ea);
+        k_pm_corr4<<<qgrid, tb, 0, L->stream>>>(K, es, ea, ucur, eb);
+        const Real* src = eb;
+        for (int k = 0; k < L->nsub; ++k) {
+          Real* dst = (k == L->nsub - 1) ? e : (src == eb ? ea : eb);
+          k_pm_ftcs4<<<qgrid, tb, 0, L->stream>>>(K, src, drho, kap, th, dst, k == L->nsub - 1);
+          src = dst;
+        }
+        RPK_CUDA(timing_end(L, RPK_KC_TRANSPORT, 2 + L->nsub));
+        return check_launch("rotational transport (paper mode)");
+      }
+    }
     k_pm_pred<Real, kBC><<<tgrid, tb, 0, L->stream>>>(K, es, ucur, ea, gh);
     k_pm_corr<Real, kBC><<<tgrid, tb, 0, L->stream>>>(K, es, ea, ucur, eb, gh);
     const Real* src = eb;

@@ -4,8 +4,8 @@ The grid chooses among kernels for the same arithmetic of the step (Sec. 5):
 the collision with one point per thread (nx odd) or with two x-adjacent points
 per thread in packed FP32x2 form (nx even; pair words, straddled for odd x
 shifts), in the conservative rotational form and in the paper's theta_R
-solver, and the transport's one-point or four-point kernels (conservative
-form, FP32 fields, nx % 4 == 0). A field of period p in x run on nx = p, 2p and 4p is the same
+solver, and the transport's one-point or four-point kernels (both forms,
+FP32 fields, nx % 4 == 0). A field of period p in x run on nx = p, 2p and 4p is the same
 problem, so the 2p and 4p runs must give the p-run's moments tiled. The
 packed and scalar forms round alike per operation but are not bit-identical
 (the scalar instantiation differs in the last bits of ~20% of the moments on
