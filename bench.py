@@ -39,7 +39,7 @@ FALLBACK_HBM_GBS = 6800.0
 FALLBACK_BF16_TFLOPS = 1900.0  # burst; about 1700 sustained
 
 
-def algorithmic_bytes_per_point(prec):
+def algorithmic_bytes_per_point(prec, rot_mode="conservative"):
     """Bytes one point must move per step (rows a1-a8 of the hot path):
     41 populations read + 41 written, plus the moment/rotational fields
     (read rho, u, theta, E_R: 24 B; write 24 B) in the field precision."""
@@ -47,7 +47,8 @@ def algorithmic_bytes_per_point(prec):
     fb = 8 if prec == "f64" else 4
     return {"step": 41 * 2 * sb + 12 * fb,
             # collide kernel alone: populations, e in, and e*, rho, u (3), kappa out
-            "collide": 41 * 2 * sb + 7 * fb}
+            # (the paper's theta_R solver also writes theta_T for its last half step)
+            "collide": 41 * 2 * sb + (8 if rot_mode == "paper" else 7) * fb}
 
 
 def load_peaks():
@@ -540,6 +541,9 @@ def main():
     ap.add_argument("--anchor", type=int, default=0)
     ap.add_argument("--workload", default="waves", choices=["waves", "tgv"],
                     help="decaying wave field (default) or Taylor-Green vortex Ma 0.3 Re 1600")
+    ap.add_argument("--rot-mode", default="conservative", choices=["conservative", "paper"],
+                    help="rotational-energy solver: the conservative form (default) or the "
+                         "paper's theta_R solver")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -579,6 +583,7 @@ def main():
     stream = torch.cuda.Stream()
     lat = rpk.Lattice(n, n, n, precision=args.precision, stream=stream)
     lat.set_relax(r["delta"], r["tau"], r["tau1"], r["b"], r["k_r"])
+    lat.set_rot_mode(args.rot_mode)
     lat.init_fields(f["rho"], f["u"], f["T"], f["R"])
     nsub = lat.info()["nsub"]
     npts = lat.npts
@@ -615,6 +620,7 @@ def main():
                               ("Erot", npts))}
         lat2 = rpk.Lattice(n, n, n, precision=args.precision, stream=stream)
         lat2.set_relax(r["delta"], r["tau"], r["tau1"], r["b"], r["k_r"])
+        lat2.set_rot_mode(args.rot_mode)
         lat2.init_fields(pin["rho"], pin["u"], pin["T"], pin["R"])  # warm the staging path
         lat2.step(3)
         lat2.read_moments(outs)
@@ -643,6 +649,7 @@ def main():
                 continue
             lx = rpk.Lattice(n, n, n, precision=prec, stream=stream)
             lx.set_relax(r["delta"], r["tau"], r["tau1"], r["b"], r["k_r"])
+            lx.set_rot_mode(args.rot_mode)
             lx.init_fields(f["rho"], f["u"], f["T"], f["R"])
             lx.step(args.warmup)
             torch.cuda.synchronize()
@@ -668,12 +675,13 @@ def main():
             dist.destroy_process_group()
         return 0
 
-    ab = algorithmic_bytes_per_point(args.precision)
+    ab = algorithmic_bytes_per_point(args.precision, args.rot_mode)
     peak, peak_src = load_peaks()
     coll_ms, coll_n = ktimes["collide"]
     coll_avg_s = coll_ms / max(coll_n, 1) * 1e-3
     achieved = ab["collide"] * npts / coll_avg_s / 1e9
-    traffic = ncu_traffic(args.precision)
+    # the committed capture is of the conservative form's collide kernel
+    traffic = ncu_traffic(args.precision) if args.rot_mode == "conservative" else None
     step_gbs = ab["step"] * npts * args.steps / (ms * 1e-3) / 1e9
     roofline = {"bound": "hbm", "kernel": "k_collide_pair (pull-stream + collide + exchange, two points per thread)"
                 if args.n % 2 == 0 else "k_collide (pull-stream + collide + exchange)",
@@ -701,6 +709,7 @@ def main():
                                     if args.workload == "waves" else
                                     "3-D Taylor-Green vortex %d^3, Ma 0.3, Re 1600, %s" % (n, args.precision)),
                        "grid": [n, n, n], "points": npts, "gas": gas, "nsub": nsub,
+                       "rotational_form": args.rot_mode,
                        "l2": "inputs larger than L2 (%.1f GB of populations)" %
                              (2 * 41 * npts * STORE_BYTES[args.precision] / 1e9),
                        "parallelism": "replicas x%d" % world},

@@ -19,6 +19,9 @@ def test_algorithmic_bytes_per_point():
     assert bench.algorithmic_bytes_per_point("f16dev")["step"] == 212
     assert bench.algorithmic_bytes_per_point("bf16dev")["step"] == 212
     assert bench.algorithmic_bytes_per_point("f64")["step"] == 752
+    # the paper's theta_R solver writes theta_T(f) from the collision as well
+    assert bench.algorithmic_bytes_per_point("f32", "paper") == {"step": 376, "collide": 360}
+    assert bench.algorithmic_bytes_per_point("f16dev", "paper")["collide"] == 196
 
 
 def test_committed_collide_capture_matches_the_sources():
