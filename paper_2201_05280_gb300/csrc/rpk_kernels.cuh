@@ -908,11 +908,12 @@ __global__ void __launch_bounds__(kDiagThreads, sizeof(Real) == 4 ? 4 : 1)
   diag_block_reduce(acc, partial);
 }
 
-// k_diag for two x-adjacent points per thread (periodic pull, conservative
-// form, FP32 arithmetic, nx even): the moments and targets in packed FP32x2
-// form, the logarithms and the FP64 accumulation per point. Thread t handles
-// pair t of the field planes (sublattice t / (n3/2)).
-template <typename Store>
+// k_diag for two x-adjacent points per thread (periodic pull, FP32
+// arithmetic, nx even; kPaper: the state holds theta_R as in the paper's
+// solver): the moments and targets in packed FP32x2 form, the logarithms and
+// the FP64 accumulation per point. Thread t handles pair t of the field planes
+// (sublattice t / (n3/2)).
+template <typename Store, bool kPaper>
 __global__ void __launch_bounds__(kDiagThreads, 3)
     k_diag_pair(StepConst<float> K, const Store* __restrict__ pin, const float* __restrict__ e_in,
                 double* __restrict__ partial) {
@@ -938,7 +939,7 @@ __global__ void __launch_bounds__(kDiagThreads, 3)
     Mom<F2> m;
     raw_moments(h, m);
     const F2 e(reinterpret_cast<const float2*>(e_in)[t]);
-    recover<float, false>(m, e, K);
+    recover<float, kPaper>(m, e, K);
     Herm<F2> H;
     mix_coeffs(m, K, H);
     const float w0 = float(kWeightRest);
@@ -969,7 +970,10 @@ __global__ void __launch_bounds__(kDiagThreads, 3)
       acc[1] += (double)jx[l];
       acc[2] += (double)jy[l];
       acc[3] += (double)jz[l];
-      acc[4] += 0.5 * ((double)p0[l] + (double)p1[l] + (double)p2[l]) + (double)ev[l];
+      // paper mode holds theta_R: its energy density delta rho theta_R / 2 (deviation)
+      const double Ee = kPaper ? 0.5 * (double)K.delta * ((double)rho[l] * (t0 + (double)dR[l]) - t0)
+                               : (double)ev[l];
+      acc[4] += 0.5 * ((double)p0[l] + (double)p1[l] + (double)p2[l]) + Ee;
       acc[5] += (double)(Hp[l] - 0.5f * K.delta * rho[l] * __logf(K.theta0 + dR[l]));
       acc[6] = fmin(acc[6], (double)gm[l]);
     }

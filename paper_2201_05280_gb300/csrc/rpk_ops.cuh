@@ -346,13 +346,16 @@ rpk_status Ops<Store, Real>::diag(rpk_lattice* L, double out[8]) {
   const bool res = L->grid.bc_x == RPK_BC_RESERVOIR;
   const int wm = wall_mask(L);
   bool pair = false;
-  if constexpr (sizeof(Real) == 4) pair = !L->streamed && !wm && !res && !L->rot_mode && L->grid.nx % 2 == 0;
+  if constexpr (sizeof(Real) == 4) pair = !L->streamed && !wm && !res && L->grid.nx % 2 == 0;
   if (pair) {
     if constexpr (sizeof(Real) == 4) {
       // two points per thread (3 blocks per SM)
       const int64_t pneed = (L->npts / 2 + kDiagThreads - 1) / kDiagThreads;
       const int pblk = (int)std::max<int64_t>(1, std::min<int64_t>(std::min<int64_t>(kDiagBlocks, (int64_t)L->sms * 3), pneed));
-      k_diag_pair<Store><<<pblk, kDiagThreads, 0, L->stream>>>(K, pin, e, L->diag_partial);
+      if (L->rot_mode)
+        k_diag_pair<Store, true><<<pblk, kDiagThreads, 0, L->stream>>>(K, pin, e, L->diag_partial);
+      else
+        k_diag_pair<Store, false><<<pblk, kDiagThreads, 0, L->stream>>>(K, pin, e, L->diag_partial);
       rpk_status st0 = check_launch("k_diag_pair");
       if (st0 != RPK_OK) return st0;
       k_diag_final<<<1, 1024, 0, L->stream>>>(L->diag_partial, pblk, L->diag_out);

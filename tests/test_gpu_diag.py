@@ -6,9 +6,10 @@ form) and are accumulated across points in FP64; H1 uses FP32 logarithms. The
 state itself differs from the oracle's by FP32 rounding (~1e-7 relative after
 a few steps of a smooth flow), so M, J and E agree to ~1e-7 of M and E, H1 to
 ~1e-6 and min g to ~1e-6 of its own size. nx even runs the two-points-per-thread
-kernel, nx odd the one-point kernel; both are held to the same bars, and the
-16-bit storages (whose states differ from the oracle's by their rounding) to
-looser ones.
+kernel, nx odd the one-point kernel, in both rotational forms (the paper's
+solver holds theta_R, whose energy density delta rho theta_R / 2 enters E);
+all are held to the same bars, and the 16-bit storages (whose states differ
+from the oracle's by their rounding) to looser ones.
 """
 import numpy as np
 import pytest
@@ -35,17 +36,19 @@ def _gpu():
     torch.cuda.set_device(0)
 
 
+@pytest.mark.parametrize("mode", ["conservative", "paper"])
 @pytest.mark.parametrize("prec", ["f32", "f16dev", "bf16dev"])
 @pytest.mark.parametrize("nx", [40, 41])
-def test_fp32_diagnostics_against_oracle(prec, nx):
+def test_fp32_diagnostics_against_oracle(prec, nx, mode):
     ny, nz, nsteps = 6, 4, 5
     f = I.random_smooth(nx, ny, nz, T0, seed=19)
     lat = rpk.Lattice(nx, ny, nz, precision=prec).set_relax(**RELAX)
+    lat.set_rot_mode(mode)
     lat.init_fields(f["rho"], f["u"], f["T"], f["R"]).step(nsteps)
     d = lat.diagnostics()
     lat.close()
     P = O.make_params(RELAX["delta"], RELAX["tau"], RELAX["tau1"], RELAX["b"], RELAX["k_r"], 1.0,
-                      RELAX["nsub"], 0)
+                      RELAX["nsub"], 0, rot_mode=1 if mode == "paper" else 0)
     ref = O.State(P, nx, ny, nz).init_fields(f["rho"], f["u"], f["T"], f["R"]).step(nsteps).diag()
     cons, h1, gmin = BARS[prec]
     errs = {"M": abs(d["M"] - ref["M"]) / ref["M"],
@@ -53,7 +56,7 @@ def test_fp32_diagnostics_against_oracle(prec, nx):
             "E": abs(d["E"] - ref["E"]) / ref["E"],
             "H1": abs(d["H1"] - ref["H1"]) / abs(ref["H1"]),
             "min_g": abs(d["min_g"] - ref["min_g"]) / abs(ref["min_g"])}
-    print("diagnostics %s nx %d: %s" % (prec, nx, {k: "%.2e" % v for k, v in errs.items()}))
+    print("diagnostics %s %s nx %d: %s" % (mode, prec, nx, {k: "%.2e" % v for k, v in errs.items()}))
     assert d["status"] == 0
     assert errs["M"] <= cons and errs["J"] <= cons and errs["E"] <= cons, errs
     assert errs["H1"] <= h1, errs
