@@ -14,21 +14,21 @@ namespace rpk {
 // hands the 41 relaxed populations to emit(q, value) in the order q = 0, 1, 2,
 // ..., returns the moments in m and the exchanged auxiliary rotational energy
 // (paper mode: theta_R after the first backward-Euler half step).
-template <typename Real, bool kPaper = false, typename V, typename Emit>
-__device__ __forceinline__ V collide_emit(const StepConst<Real>& K, const V (&h)[kQ], V e, Emit&& emit,
-                                          Mom<V>& m) {
-  raw_moments(h, m);
+// The part after the raw moments: hq(q) gives population q's h for the
+// relaxation (the array itself, or a conversion of its stored word).
+template <typename Real, bool kPaper = false, typename V, typename HQ, typename Emit>
+__device__ __forceinline__ V collide_relax(const StepConst<Real>& K, Mom<V>& m, V e, HQ&& hq, Emit&& emit) {
   recover<Real, kPaper>(m, e, K);
   Herm<V> H;
   mix_coeffs(m, K, H);
-  emit(0, fmad(K.c_keep, h[0], K.c_relax * H.e0));
+  emit(0, fmad(K.c_keep, hq(0), K.c_relax * H.e0));
   static_for<kPairs>([&](auto kc) {
     constexpr int k = decltype(kc)::value;
     constexpr Vel2 v = kPairVel2[k];
     const V ev = herm_even<v.x, v.y, v.z>(H);
     const V od = herm_odd<v.x, v.y, v.z>(H);
-    emit(2 * k + 1, fmad(K.c_keep, h[2 * k + 1], K.c_relax * (ev + od)));
-    emit(2 * k + 2, fmad(K.c_keep, h[2 * k + 2], K.c_relax * (ev - od)));
+    emit(2 * k + 1, fmad(K.c_keep, hq(2 * k + 1), K.c_relax * (ev + od)));
+    emit(2 * k + 2, fmad(K.c_keep, hq(2 * k + 2), K.c_relax * (ev - od)));
   });
   // conservative form: the exchanged auxiliary energy; paper mode: theta_R after
   // the first backward-Euler half step with the time-t theta_T (Sec. 5, step 1)
@@ -36,6 +36,13 @@ __device__ __forceinline__ V collide_emit(const StepConst<Real>& K, const V (&h)
     return fmad(K.ra_keep, m.dR, K.ra_t * m.dT);
   else
     return fmad(K.exc * m.rho, m.dth - m.dR, e);
+}
+
+template <typename Real, bool kPaper = false, typename V, typename Emit>
+__device__ __forceinline__ V collide_emit(const StepConst<Real>& K, const V (&h)[kQ], V e, Emit&& emit,
+                                          Mom<V>& m) {
+  raw_moments(h, m);
+  return collide_relax<Real, kPaper>(K, m, e, [&](int q) { return h[q]; }, emit);
 }
 
 // One point: the populations go to out[q * n3].
@@ -143,6 +150,54 @@ __global__ void __launch_bounds__(128, sizeof(Store) == 4 ? 3 : 4)
   const F2 es = collide_emit<float, kPaper>(
       K, h, F2(reinterpret_cast<const float2*>(e_in)[pp]),
       [&](int q, F2 v) { out[(int64_t)q * n3p] = IO::from_f2(v); }, m);
+  reinterpret_cast<float2*>(e_out)[pp] = es.v;
+  reinterpret_cast<float2*>(drho_out)[pp] = m.drho.v;
+  float2* u2 = reinterpret_cast<float2*>(u_out);
+  u2[pp] = (m.j[0] * m.inv_rho).v;
+  u2[K.n3 + pp] = (m.j[1] * m.inv_rho).v;
+  u2[2 * K.n3 + pp] = (m.j[2] * m.inv_rho).v;
+  reinterpret_cast<float2*>(kap_out)[pp] = (K.kapc * m.rho * (K.theta0 + m.dth)).v;
+  if constexpr (kPaper) reinterpret_cast<float2*>(tt_out)[pp] = m.dT.v;
+  flag_moments2(m, K.theta0, status);
+}
+
+// FP16 storage: k_collide_pair holding the 41 pair words (one register
+// each) instead of their 82 FP32 values between the moments and the
+// relaxation, which converts each word again where it is used (one cvt per
+// value). Fewer live registers give 5 blocks per SM instead of 4: 10.06
+// against 10.46 ms per 512^3 launch in the conservative form. The paper's
+// solver (11.53 against 10.86 ms) and BF16 storage (11.18 against 10.13 ms,
+// its conversion being two integer operations) keep k_collide_pair.
+template <typename Store, bool kPaper = false>
+__global__ void __launch_bounds__(128, 5)
+    k_collide_pair_w(StepConst<float> K, const Store* __restrict__ pin, Store* __restrict__ pout,
+                     const float* __restrict__ e_in, float* __restrict__ e_out, float* __restrict__ drho_out,
+                     float* __restrict__ u_out, float* __restrict__ kap_out, unsigned* __restrict__ status,
+                     float* __restrict__ tt_out) {
+  static_assert(std::is_same<Store, __half>::value, "the word-holding collision serves FP16 storage");
+  using IO = PairIO<Store>;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (K.nx >> 1)) return;
+  const int y = blockIdx.y;
+  const int s = blockIdx.z / K.nz;
+  const int z = blockIdx.z - s * K.nz;
+  const int64_t n3p = K.n3 >> 1;
+  const int64_t cellp = ((((int64_t)z * K.ny + y) * K.nx) >> 1) + i;
+  const int64_t pp = (int64_t)s * n3p + cellp;
+  unsigned hw[kQ];
+  gather_pair_words<Store>(reinterpret_cast<const unsigned*>(pin), K, s, i, y, z, hw);
+  Mom<F2> m;
+  {
+    F2 h[kQ];
+#pragma unroll
+    for (int q = 0; q < kQ; ++q) h[q] = IO::to_f2(hw[q]);
+    raw_moments(h, m);
+  }
+  unsigned* out = reinterpret_cast<unsigned*>(pout) + (int64_t)(s * kQ) * n3p + cellp;
+  const F2 es = collide_relax<float, kPaper>(
+      K, m, F2(reinterpret_cast<const float2*>(e_in)[pp]),
+      [&](int q) { return word_to_f2_here<Store>(hw[q]); },
+      [&](int q, F2 v) { out[(int64_t)q * n3p] = IO::from_f2(v); });
   reinterpret_cast<float2*>(e_out)[pp] = es.v;
   reinterpret_cast<float2*>(drho_out)[pp] = m.drho.v;
   float2* u2 = reinterpret_cast<float2*>(u_out);

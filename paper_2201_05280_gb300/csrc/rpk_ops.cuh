@@ -4,6 +4,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <type_traits>
 
 #include "rpk_internal.h"
 #include "rpk_kernels.cuh"
@@ -120,9 +121,15 @@ static rpk_status collide_launch(rpk_lattice* L, const StepConst<Real>& K) {
       // two x-adjacent points per thread, packed FP32x2 arithmetic
       const dim3 grid((unsigned)((L->grid.nx / 2 + 127) / 128), (unsigned)L->grid.ny,
                       (unsigned)(2 * L->grid.nz));
-      k_collide_pair<Store, false><<<grid, 128, 0, L->stream>>>(
-          K, pin, pout, static_cast<const Real*>(L->e), static_cast<Real*>(L->e_star),
-          static_cast<Real*>(L->drho), ucur, static_cast<Real*>(L->kap), L->status, nullptr);
+      // FP16 storage holds the pair words, not their FP32 values, across the collision
+      if constexpr (std::is_same<Store, __half>::value)
+        k_collide_pair_w<Store, false><<<grid, 128, 0, L->stream>>>(
+            K, pin, pout, static_cast<const Real*>(L->e), static_cast<Real*>(L->e_star),
+            static_cast<Real*>(L->drho), ucur, static_cast<Real*>(L->kap), L->status, nullptr);
+      else
+        k_collide_pair<Store, false><<<grid, 128, 0, L->stream>>>(
+            K, pin, pout, static_cast<const Real*>(L->e), static_cast<Real*>(L->e_star),
+            static_cast<Real*>(L->drho), ucur, static_cast<Real*>(L->kap), L->status, nullptr);
       return check_launch("k_collide_pair");
     }
   }
