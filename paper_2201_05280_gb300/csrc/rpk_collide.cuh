@@ -164,12 +164,13 @@ __global__ void __launch_bounds__(128, sizeof(Store) == 4 ? 3 : 4)
 // FP16 storage: k_collide_pair holding the 41 pair words (one register
 // each) instead of their 82 FP32 values between the moments and the
 // relaxation, which converts each word again where it is used (one cvt per
-// value). Fewer live registers give 5 blocks per SM instead of 4: 10.06
-// against 10.46 ms per 512^3 launch in the conservative form. The paper's
-// solver (11.53 against 10.86 ms) and BF16 storage (11.18 against 10.13 ms,
-// its conversion being two integer operations) keep k_collide_pair.
+// value). Fewer live registers fit more blocks per SM: per 512^3 launch 10.06
+// against 10.46 ms in the conservative form (5 blocks per SM), 10.24 against
+// 10.88 ms in the paper's solver (4 blocks; 11.53 ms with 5). BF16 storage
+// keeps k_collide_pair (11.18 against 10.13 ms: its conversion is two
+// integer operations).
 template <typename Store, bool kPaper = false>
-__global__ void __launch_bounds__(128, 5)
+__global__ void __launch_bounds__(128, kPaper ? 4 : 5)
     k_collide_pair_w(StepConst<float> K, const Store* __restrict__ pin, Store* __restrict__ pout,
                      const float* __restrict__ e_in, float* __restrict__ e_out, float* __restrict__ drho_out,
                      float* __restrict__ u_out, float* __restrict__ kap_out, unsigned* __restrict__ status,

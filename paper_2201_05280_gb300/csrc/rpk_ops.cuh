@@ -103,10 +103,16 @@ static rpk_status collide_launch(rpk_lattice* L, const StepConst<Real>& K) {
         // two x-adjacent points per thread, packed FP32x2 arithmetic
         const dim3 grid((unsigned)((L->grid.nx / 2 + 127) / 128), (unsigned)L->grid.ny,
                         (unsigned)(2 * L->grid.nz));
-        k_collide_pair<Store, true><<<grid, 128, 0, L->stream>>>(
-            K, pin, pout, static_cast<const Real*>(L->e), static_cast<Real*>(L->e_star),
-            static_cast<Real*>(L->drho), ucur, static_cast<Real*>(L->kap), L->status,
-            static_cast<Real*>(L->thbuf));
+        if constexpr (std::is_same<Store, __half>::value)
+          k_collide_pair_w<Store, true><<<grid, 128, 0, L->stream>>>(
+              K, pin, pout, static_cast<const Real*>(L->e), static_cast<Real*>(L->e_star),
+              static_cast<Real*>(L->drho), ucur, static_cast<Real*>(L->kap), L->status,
+              static_cast<Real*>(L->thbuf));
+        else
+          k_collide_pair<Store, true><<<grid, 128, 0, L->stream>>>(
+              K, pin, pout, static_cast<const Real*>(L->e), static_cast<Real*>(L->e_star),
+              static_cast<Real*>(L->drho), ucur, static_cast<Real*>(L->kap), L->status,
+              static_cast<Real*>(L->thbuf));
         return check_launch("k_collide_pair");
       }
     }
