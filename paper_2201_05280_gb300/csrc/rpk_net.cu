@@ -456,7 +456,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv_tc(TcArgs P) {
     const int m = quad * 32 + lane;
     const float bm = P.bias ? P.bias[m] : 0.f;
     const uint32_t rbar = bar0 + 8 * 6;  // 6: residual in S[0], 7: residual in S[1]
-    int rphase[2] = {0, 0};
+    int rphase[2] = {0, 0};  // residual copies waited for, per buffer (every thread)
+    int rissued[2] = {0, 0};  // residual copies issued, per buffer (thread 0)
     for (int i = 0, tile = blockIdx.x; tile < P.ntiles; ++i, tile += gridDim.x) {
       const int acc = i & 1;
       int q0, cnt, lo, len;
@@ -466,7 +467,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv_tc(TcArgs P) {
         // both buffers are free once every earlier bulk store has read them out
         asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
         if (P.res)
-          for (int q = 0; q < 2 && q < nq; ++q) qtr_load(P, rbar + 8 * q, s_base + q * TC_SQ_BYTES, q0, cnt, q);
+          for (int q = 0; q < 2 && q < nq; ++q) {
+            qtr_load(P, rbar + 8 * q, s_base + q * TC_SQ_BYTES, q0, cnt, q);
+            ++rissued[q];
+          }
       }
       ok = epi_all(mbar_wait(bar0 + 8 * (2 + acc), (i >> 1) & 1));
       if (!ok) break;
@@ -478,12 +482,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv_tc(TcArgs P) {
         float* S = sS + buf * (TC_QTR * TC_M);
         if (P.res) {
           ok = epi_all(mbar_wait(rbar + 8 * buf, rphase[buf] & 1));
-          ++rphase[buf];
           if (!ok) break;
+          ++rphase[buf];
           if (tid == 0 && q >= 1 && q + 1 < nq) {
             // the store of quarter q - 1 has read S[1 - buf] before the next rows land there
             asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
             qtr_load(P, rbar + 8 * (1 - buf), s_base + (1 - buf) * TC_SQ_BYTES, q0, cnt, q + 1);
+            ++rissued[1 - buf];
           }
         } else {
           // the store of quarter q - 2 has read S[buf] (the latest one may still be reading the other)
@@ -524,7 +529,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv_tc(TcArgs P) {
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       mbar_arrive(bar0 + 8 * (4 + acc));  // accumulator free (TC_EPI arrivals)
     }
-    if (!ok && tid == 0) atomicOr(P.error, 1u);
+    if (!ok && tid == 0) {
+      atomicOr(P.error, 1u);
+      // after a wait that gave up, let residual copies still in flight land
+      // (bounded waits) before the CTA's shared memory is released
+      for (int b = 0; b < 2; ++b)
+        for (; rphase[b] < rissued[b]; ++rphase[b]) mbar_wait(rbar + 8 * b, rphase[b] & 1);
+    }
     // the output is written and S read out before the CTA ends
     if (tid == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
   }
