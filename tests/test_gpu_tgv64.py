@@ -18,7 +18,7 @@ two scales: the full field (max|oracle|; c_s for u) and the deviation
 (max|oracle - rest state|: rho = 1, u = 0, theta0, delta theta0 / 2). The
 relative change of the FP64 totals M and E over the run is compared with the
 oracle's own change (the paper's solver does not conserve E to round-off).
-Bounds are about 3x the errors measured on GB300 (listed in the design doc).
+Bounds are about 3x the errors measured on GB300.
 """
 import os
 
